@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of fgemm mod p on GB300: effective GOPS = 2mnk/s, bit-exact.
+
+Workload (one step = one full fgemm call: conversion to channel planes, the
+tensor-core products and the fused reduction mod p):
+  n = m = k = 8192, p = 2147483647 (largest prime below 2^31), alpha and beta
+  uniform in [0, p), A, B, C uniform residues (seeded, synthetic).  The three
+  inputs hold 768 MiB, more than the 129 MB L2, so no flush is needed between
+  steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+Multi-GPU: one process per GPU (torchrun); every rank runs its own instance
+(weak scaling, no collective on the data path); value = all ranks' work / max
+time over ranks.  The reference arm times the CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fgemm mod p effective GOPS (2mnk/s) n=8192 bit-exact; p50/p99 serve latency"
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "rns_gemm_n8192_p2147483647.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_cs_0601133_gb300", "csrc", "rns_gemm.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--p", type=int, default=2147483647)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n, p):
+    return "fgemm m=n=k=%d p=%d alpha,beta uniform in [0,p), uniform residues" % (n, p)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["bf16_tflops_sustained"]), "measured bf16 cuBLAS, sustained"
+    except Exception:
+        return 1700.0, "fallback bf16, sustained"
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the tensor-core kernel from the committed ncu
+    summary, or None if the summary is absent or the kernel changed since."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+        src_hash = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        m_h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+        m_t = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+        if m_h and m_t and m_h.group(1) == src_hash:
+            return float(m_t.group(1))
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(A, B, C, p, alpha, beta, rows):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.fgemm(A[:rows], B, p, alpha, beta, C[:rows])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(A, B, C, p, alpha, beta, target_s=12.0):
+    import oracle
+    n, k = A.shape[0], A.shape[1]
+    ncols = B.shape[1]
+    rows = 4
+    t = oracle_sample(A, B, C, p, alpha, beta, rows)
+    rows = int(max(4, min(n, rows * target_s / max(t, 1e-3))))
+    t = oracle_sample(A, B, C, p, alpha, beta, rows)
+    gops = 2.0 * rows * ncols * k / t / 1e9
+    return {"value": gops, "unit": "GOPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d of %d rows of C (full k=%d, n=%d), %.1f s" % (rows, n, k, ncols, t)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_cs_0601133_gb300 import workloads as W
+    import oracle
+    A, B, C, alpha, beta = W.square_problem(args.n, args.p)
+    # rows per step: about 5 s of CPU work per step
+    t = oracle_sample(A, B, C, args.p, alpha, beta, 4)
+    rows = int(max(2, min(args.n, 4 * 5.0 / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(A, B, C, args.p, alpha, beta, rows)
+    times = [oracle_sample(A, B, C, args.p, alpha, beta, rows) for _ in range(args.steps)]
+    tstep = sum(times) / len(times)
+    value = 2.0 * rows * args.n * args.n / tstep / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tstep * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args.n, args.p), "n": args.n, "p": args.p},
+        "cpu_baseline": {"value": value, "unit": "GOPS", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": "each step: %d of %d rows of C with the full inner dimension" % (rows, args.n)},
+        "e2e": {"value": value, "unit": "GOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_own(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n, p = args.n, args.p
+
+    A, B, C, alpha, beta = W.square_problem(n, p)
+    dA = torch.from_numpy(A.view(np.int32)).to(dev)
+    dB = torch.from_numpy(B.view(np.int32)).to(dev)
+    dC = torch.from_numpy(C.view(np.int32)).to(dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ff.fgemm(dA, dB, p, alpha, beta, dC)
+    torch.cuda.synchronize()
+    if ff.last_device_error() != 0:
+        raise RuntimeError("device error word set during warm-up")
+
+    sampler = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ff.profile_enable(True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ff.fgemm(dA, dB, p, alpha, beta, dC)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ff.profile_enable(False)
+    clocks = sampler.stop()
+    kernels = ff.profile_read()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    if ff.last_device_error() != 0:
+        raise RuntimeError("device error word set during the timed region")
+    flop_step = 2.0 * n * n * n
+    value = world * args.steps * flop_step / (ms / 1e3) / 1e9
+
+    plan = ff.fgemm_plan(n, n, n, p)
+    launches = sum(v[0] for v in kernels.values())
+    gl, gms = kernels.get("rns_gemm", (0, 0.0))
+    peak, peak_src = measured_peak()
+    roofline = None
+    if gl:
+        avg_s = gms / gl / 1e3
+        achieved = plan["mma_flops"] / avg_s / 1e12
+        traffic = ncu_traffic()
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic,
+                    "kernel": "rns_gemm_kernel", "peak_source": peak_src,
+                    "algorithmic": "2*m*n*k_padded*channels = %.4g tensor FLOP per launch (%d channels)"
+                                   % (plan["mma_flops"], plan["channels"]),
+                    "avg_launch_ms": gms / gl}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world)
+
+    if rank == 0:
+        base = None
+        if world == 1 and not args.no_cpu_baseline:
+            base = cpu_baseline(A, B, C, p, alpha, beta)
+        line = {
+            "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": workload_name(n, p), "n": n, "p": p, "alpha": alpha, "beta": beta,
+                       "channels": plan["channels"], "moduli": plan["moduli"],
+                       "l2": "inputs 768 MiB > 129 MB L2: no flush between steps",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "cpu_baseline": base,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "kernels_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kernels.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world):
+    """Same metric through the public API with host buffers: every step copies
+    A, B, C from pinned host memory, runs fgemm and reads C back."""
+    n, p = args.n, args.p
+    hA = torch.from_numpy(A.view(np.int32)).pin_memory()
+    hB = torch.from_numpy(B.view(np.int32)).pin_memory()
+    hC = torch.from_numpy(C.view(np.int32)).pin_memory()
+    hOut = torch.empty_like(hC).pin_memory()
+    dA = torch.empty(hA.shape, dtype=torch.int32, device=dev)
+    dB = torch.empty(hB.shape, dtype=torch.int32, device=dev)
+    dC = torch.empty(hC.shape, dtype=torch.int32, device=dev)
+
+    def step():
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        dC.copy_(hC, non_blocking=True)
+        ff.fgemm(dA, dB, p, alpha, beta, dC)
+        hOut.copy_(dC, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return {"value": world * args.steps * 2.0 * n ** 3 / (ms / 1e3) / 1e9, "unit": "GOPS",
+            "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
+            "ms_per_step": ms / args.steps}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_own(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,137 @@
+/*
+ * ffgpu -- exact dense linear algebra over Z/pZ on one GB300 GPU (sm_103a).
+ *
+ * C ABI of the library libffgpu.so.  Plain pointers and sizes only.
+ *
+ * The operations follow Dumas, Giorgi and Pernet, "Dense linear algebra over
+ * word-size prime fields: the FFLAS and FFPACK packages":
+ *   fgemm  (section 3):   C <- alpha*A*B + beta*C over Z/pZ;
+ *   ftrsm  (section 4):   B <- alpha*op(T)^{-1}*B (left) or alpha*B*op(T)^{-1} (right).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major; lda, ldb, ldc, ldt are leading dimensions in
+ *     elements (ld >= number of columns).  A is m x k, B is k x n, C is m x n.
+ *   - Matrix pointers are DEVICE pointers owned by the caller; the library
+ *     never frees them.  Elements are uint32 words; any word is accepted and
+ *     taken mod p, as are alpha and beta.  Outputs are canonical residues in
+ *     [0, p).
+ *   - 2 <= p <= 2^31 - 1.  p need not be prime for fgemm.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Every call is asynchronous on that stream; argument errors are
+ *     returned synchronously and nothing is enqueued.  A failure inside a
+ *     kernel (a bounded wait that ran out) is recorded in a device error word
+ *     read by ffgpu_last_device_error().
+ *   - m, n or k may be 0: k = 0 gives C <- beta*C mod p; m = 0 or n = 0 is a
+ *     no-op.  C must not overlap A or B.
+ *   - Workspace: calls without an explicit workspace use a pool the library
+ *     keeps per (device, stream), grown with stream-ordered allocation.  Two
+ *     calls on the same stream are ordered and share it; calls on different
+ *     streams use different pools.
+ */
+#ifndef FFGPU_H
+#define FFGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FFGPU_API __attribute__((visibility("default")))
+#else
+#define FFGPU_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FFGPU_OK = 0,
+    FFGPU_ERR_INVALID = -1,       /* bad argument (shape, ld, null pointer, p out of range) */
+    FFGPU_ERR_UNSUPPORTED_P = -2, /* p outside [2, 2^31-1] */
+    FFGPU_ERR_NOMEM = -3,         /* workspace allocation failed or caller workspace too small */
+    FFGPU_ERR_CUDA = -4,          /* a CUDA runtime call failed (launch, copy, no device) */
+    FFGPU_ERR_TIMEOUT = -5,       /* a kernel's bounded wait ran out; its results are invalid */
+    FFGPU_ERR_BUDGET = -6         /* request exceeds a configured memory budget */
+} ffgpu_status;
+
+/* Human-readable name of a status code (static storage). */
+FFGPU_API const char* ffgpu_status_string(ffgpu_status s);
+
+/* Library version: major*10000 + minor*100 + patch. */
+FFGPU_API int ffgpu_version(void);
+
+/*
+ * fgemm (section 3, the problem statement; eqs. 1-2 for the delayed
+ * reduction that the kernel restates for its accumulator):
+ *     C <- (alpha * A * B + beta * C) mod p.
+ * A: m x k (lda), B: k x n (ldb), C: m x n (ldc), all device memory.
+ * Path: residues are mapped to a residue number system of small moduli
+ * (<= 256, bf16-exact), one tensor-core product per modulus with the
+ * accumulator reduced in place before it can lose exactness, and a fused
+ * epilogue that reconstructs the value mod p and applies alpha and beta.
+ * Bit-exact: the result is the unique canonical residue.
+ */
+FFGPU_API ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                         const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                         uint32_t beta, uint32_t* C, int64_t ldc, void* stream);
+
+/* Bytes of device workspace ffgpu_fgemm_ws needs for this problem. */
+FFGPU_API ffgpu_status ffgpu_fgemm_workspace_size(int64_t m, int64_t n, int64_t k, uint32_t p,
+                                        size_t* bytes);
+
+/*
+ * ffgpu_fgemm with a caller-owned device workspace of at least
+ * ffgpu_fgemm_workspace_size() bytes (256-byte aligned).  The workspace must
+ * not be used by anything else until the call has completed on `stream`.
+ * Kernel errors are reported through the device error word of `stream`'s pool.
+ */
+FFGPU_API ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                            const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                            uint32_t beta, uint32_t* C, int64_t ldc,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/* Description of how ffgpu_fgemm computes a problem (for benchmarks and tests). */
+typedef struct {
+    int32_t mode;         /* 1 = single modulus p (p <= 256); 2 = residue number system */
+    int32_t channels;     /* number of moduli, i.e. tensor-core products per output tile */
+    uint32_t moduli[16];  /* the moduli in use */
+    int32_t k_chunk;      /* inner-dimension length summed between in-place reductions */
+    int32_t k_slices;     /* > 1 when k is split into several launches */
+    int32_t tile_m, tile_n, tile_k;
+    double mma_flops;     /* 2*m*n*k*channels: tensor-core operations issued */
+} ffgpu_plan_info;
+
+FFGPU_API ffgpu_status ffgpu_fgemm_plan(int64_t m, int64_t n, int64_t k, uint32_t p, ffgpu_plan_info* out);
+
+/*
+ * Synchronizes `stream`, returns FFGPU_ERR_TIMEOUT if a kernel launched on it
+ * since the last call recorded a failure (and clears the record), FFGPU_OK
+ * otherwise, or FFGPU_ERR_CUDA if the stream reports a CUDA error.
+ */
+FFGPU_API ffgpu_status ffgpu_last_device_error(void* stream);
+
+/*
+ * Kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by two CUDA events recorded on its launching stream.
+ * ffgpu_profile_read synchronizes those events, sums their durations per
+ * kernel name into out[0..cap) (sorted by name), sets *count to the number of
+ * distinct kernels, and clears the record.  Off by default; costs two event
+ * records per launch when on.
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} ffgpu_kernel_time;
+
+FFGPU_API ffgpu_status ffgpu_profile_enable(int on);
+FFGPU_API ffgpu_status ffgpu_profile_read(ffgpu_kernel_time* out, int cap, int* count);
+
+/* Frees every workspace pool of the calling process (synchronizes the device). */
+FFGPU_API ffgpu_status ffgpu_release_workspaces(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFGPU_H */

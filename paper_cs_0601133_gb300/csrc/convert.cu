@@ -1,0 +1,175 @@
+// Conversion of uint32 words into bf16 channel planes, and small elementwise
+// kernels mod p.  All of them are HBM-bound.
+//
+// The conversion is the "few conversions" step the paper keeps out of the
+// product (section 1 and section 2.1.2: a residue is embedded in Z, here as a
+// centred representative, eq. 2): x -> x mod p -> centred x~ in
+// (-p/2, p/2] -> for each modulus m_c the balanced residue of x~ mod m_c in
+// [-m_c/2, m_c/2), written as an exact bf16.  With a single modulus (p <= 256)
+// the plane holds x~ itself.  Rows are padded with zeros to a multiple of 64
+// columns so every tensor-core tile sees whole 128-byte rows.
+#include <cuda_bf16.h>
+
+#include "devutil.cuh"
+#include "internal.h"
+
+namespace ffgpu {
+
+namespace {
+
+__device__ __forceinline__ unsigned short bf16_bits_of_int(int v) {
+    // |v| <= 256: exact in bf16
+    const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
+    return *reinterpret_cast<const unsigned short*>(&b);
+}
+
+// Residues of 8 words in every channel, packed 8 x bf16 per channel and
+// stored at dst[c * stride16].
+__device__ __forceinline__ void residues8(const ConvertParams& cp, const uint32_t (&x)[8],
+                                          uint4* __restrict__ dst, size_t stride16) {
+    uint32_t xr[8];
+    bool neg[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        xr[e] = mod_u64(x[e], cp.p, cp.mu);
+        neg[e] = xr[e] > cp.half_p;
+    }
+    if (cp.direct) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int v0 = neg[2 * i] ? (int)xr[2 * i] - (int)cp.p : (int)xr[2 * i];
+            const int v1 = neg[2 * i + 1] ? (int)xr[2 * i + 1] - (int)cp.p : (int)xr[2 * i + 1];
+            w[i] = (uint32_t)bf16_bits_of_int(v0) | ((uint32_t)bf16_bits_of_int(v1) << 16);
+        }
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        return;
+    }
+#pragma unroll 1
+    for (int c = 0; c < cp.nch; ++c) {
+        const uint32_t m = cp.mod[c], pm = cp.pmod[c];
+        const unsigned long long mg = cp.magic[c];
+        const int halfm = (int)(m - 1) / 2;
+        unsigned short h[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            // floor(xr / m) exactly: xr < 2^31, m <= 256, magic = ceil(2^40 / m)
+            const uint32_t q = (uint32_t)(((unsigned long long)xr[e] * mg) >> 40);
+            int r = (int)(xr[e] - q * m);
+            if (neg[e]) {  // x~ = xr - p
+                r -= (int)pm;
+                if (r < 0) r += (int)m;
+            }
+            if (r > halfm) r -= (int)m;
+            h[e] = bf16_bits_of_int(r);
+        }
+        dst[(size_t)c * stride16] = make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
+                            (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
+    }
+}
+
+// X: rows x cols (ldx) -> planes[c][rows][colsp], colsp a multiple of 64.
+__global__ void __launch_bounds__(256) convert_rows_kernel(const uint32_t* __restrict__ X, long long ldx,
+                                                           int rows, int cols, int colsp,
+                                                           const __grid_constant__ ConvertParams cp,
+                                                           uint4* __restrict__ planes, int vec_ok) {
+    const long long gpr = colsp / 8;
+    const long long total = (long long)rows * gpr;
+    const size_t plane16 = (size_t)rows * colsp / 8;  // plane size in 16-byte units
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(g / gpr);
+        const int c0 = (int)(g - (long long)r * gpr) * 8;
+        const uint32_t* src = X + (long long)r * ldx + c0;
+        uint32_t x[8];
+        if (vec_ok && c0 + 8 <= cols) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(src));
+            const uint4 b = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = (c0 + e < cols) ? __ldg(src + e) : 0u;
+        }
+        residues8(cp, x, planes + ((size_t)r * colsp + c0) / 8, plane16);
+    }
+}
+
+// X: rows x cols (ldx), rows = inner dimension -> planes[c][cols][rowsp]
+// (transposed, so the inner dimension is contiguous), through a 64 x 64 tile.
+__global__ void __launch_bounds__(256) convert_transpose_kernel(const uint32_t* __restrict__ X,
+                                                                long long ldx, int rows, int cols,
+                                                                int rowsp,
+                                                                const __grid_constant__ ConvertParams cp,
+                                                                uint4* __restrict__ planes) {
+    __shared__ uint32_t tile[64][65];
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int rr = idx >> 6, cc = idx & 63;
+        const int gr = r0 + rr, gc = c0 + cc;
+        tile[rr][cc] = (gr < rows && gc < cols) ? __ldg(X + (long long)gr * ldx + gc) : 0u;
+    }
+    __syncthreads();
+    const size_t plane16 = (size_t)cols * rowsp / 8;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        const int w = threadIdx.x + 256 * it;
+        const int cl = w >> 3, g = w & 7;
+        const int gc = c0 + cl;
+        if (gc >= cols) continue;
+        uint32_t x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = tile[g * 8 + e][cl];
+        residues8(cp, x, planes + ((size_t)gc * rowsp + r0 + g * 8) / 8, plane16);
+    }
+}
+
+__global__ void __launch_bounds__(256) scale_kernel(uint32_t* C, long long ldc, int m, int n, uint32_t p,
+                                                    uint32_t beta, unsigned long long mu) {
+    const long long total = (long long)m * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / n), c = (int)(i - (long long)r * n);
+        uint32_t* ptr = C + (long long)r * ldc + c;
+        *ptr = mod_u64((unsigned long long)beta * (*ptr), p, mu);
+    }
+}
+
+int grid_for(long long work, int per_block) {
+    long long g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > 152 * 16) g = 152 * 16;
+    return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_convert_rows(const uint32_t* X, long long ldx, int rows, int cols, int colsp,
+                                const ConvertParams& cp, void* planes, cudaStream_t s) {
+    if (rows == 0 || colsp == 0) return cudaSuccess;
+    const int vec_ok = ((reinterpret_cast<uintptr_t>(X) & 15) == 0) && (ldx % 4 == 0);
+    const long long work = (long long)rows * (colsp / 8);
+    convert_rows_kernel<<<grid_for(work, 256), 256, 0, s>>>(X, ldx, rows, cols, colsp, cp,
+                                                             static_cast<uint4*>(planes), vec_ok);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows, int cols, int rowsp,
+                                     const ConvertParams& cp, void* planes, cudaStream_t s) {
+    if (cols == 0 || rowsp == 0) return cudaSuccess;
+    dim3 grid((cols + 63) / 64, rowsp / 64);
+    convert_transpose_kernel<<<grid, 256, 0, s>>>(X, ldx, rows, cols, rowsp, cp,
+                                                   static_cast<uint4*>(planes));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, uint32_t beta,
+                         unsigned long long mu, cudaStream_t s) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    scale_kernel<<<grid_for((long long)m * n, 256), 256, 0, s>>>(C, ldc, m, n, p, beta, mu);
+    return cudaGetLastError();
+}
+
+}  // namespace ffgpu

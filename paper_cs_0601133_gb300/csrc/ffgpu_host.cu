@@ -1,0 +1,482 @@
+// Host side of libffgpu: the C ABI, argument checks, the plan (which moduli,
+// how the inner dimension is split), per-stream workspace pools, TMA
+// descriptors and the launch sequence.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace ffgpu {
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// Plan
+// ---------------------------------------------------------------------------
+
+static uint32_t inv_small(uint32_t a, uint32_t m) {
+    // inverse of a mod m for m <= 256 (a coprime to m), by exhaustive search
+    a %= m;
+    for (uint32_t x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return 0;
+}
+
+// Largest inner length that c channels can sum exactly: 4 * k * h^2 <= M with
+// h = floor(p/2), the largest magnitude of a centred residue.  The factor 4
+// keeps |sum| <= M/4, the margin the reconstruction's rounding step needs.
+static u128 moduli_product(int c) {
+    u128 M = 1;
+    for (int i = 0; i < c; ++i) M *= kModuli[i];
+    return M;
+}
+
+static int64_t k_capacity(uint32_t p, int c) {
+    const u128 h = p / 2;
+    const u128 cap = moduli_product(c) / (4 * h * h);
+    return cap > (u128)INT64_MAX ? INT64_MAX : (int64_t)cap;
+}
+
+// Plan for one launch summing `k` products.
+static void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
+    std::memset(&pl, 0, sizeof(pl));
+    pl.p = p;
+    if (p <= 256) {
+        pl.mode = 1;
+        pl.nch = 1;
+        pl.mod[0] = p;
+        pl.k_slice = INT64_MAX;
+        return;
+    }
+    pl.mode = 2;
+    pl.k_slice = k_capacity(p, kMaxChannels);
+    const int64_t ks = std::min<int64_t>(std::max<int64_t>(k, 1), pl.k_slice);
+    int c = 1;
+    while (c < kMaxChannels && k_capacity(p, c) < ks) ++c;
+    pl.nch = c;
+    const u128 M = moduli_product(c);
+    for (int i = 0; i < c; ++i) {
+        const uint32_t m = kModuli[i];
+        const u128 Mi = M / m;
+        pl.mod[i] = m;
+        pl.u[i] = inv_small((uint32_t)(Mi % m), m);
+        pl.W[i] = (uint32_t)(Mi % p);
+    }
+    pl.negMp = (uint32_t)((p - (uint32_t)(M % p)) % p);
+}
+
+static unsigned long long barrett_mu(uint32_t p) { return ~0ull / p; }
+
+// ---------------------------------------------------------------------------
+// Kernel timing
+// ---------------------------------------------------------------------------
+struct ProfEntry {
+    std::string name;
+    cudaEvent_t start, stop;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfEntry> g_prof;
+
+bool profiling_on() { return g_prof_on; }
+
+void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.push_back(ProfEntry{name, start, stop});
+}
+
+// ---------------------------------------------------------------------------
+// Devices, pools, descriptors
+// ---------------------------------------------------------------------------
+
+struct Pool {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int* err = nullptr;
+};
+
+static std::mutex g_mu;
+static std::map<std::pair<int, cudaStream_t>, Pool> g_pools;
+static std::map<int, int> g_sms;
+
+static int sm_count(int dev) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_sms.find(dev);
+    if (it != g_sms.end()) return it->second;
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    g_sms[dev] = v;
+    return v;
+}
+
+// Pool of (current device, stream); allocates the error word on first use and
+// grows the buffer to `need` bytes with stream-ordered allocation.
+static ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Pool& pl = g_pools[std::make_pair(dev, s)];
+    if (!pl.err) {
+        if (cudaMalloc(&pl.err, 256) != cudaSuccess) {
+            pl.err = nullptr;
+            return FFGPU_ERR_NOMEM;
+        }
+        if (cudaMemset(pl.err, 0, 256) != cudaSuccess) return FFGPU_ERR_CUDA;
+    }
+    if (need > pl.bytes) {
+        if (pl.ptr) {
+            cudaFreeAsync(pl.ptr, s);
+            pl.ptr = nullptr;
+            pl.bytes = 0;
+        }
+        const size_t want = (need + (size_t(1) << 21) - 1) & ~((size_t(1) << 21) - 1);
+        if (cudaMallocAsync(&pl.ptr, want, s) != cudaSuccess) {
+            cudaGetLastError();
+            pl.ptr = nullptr;
+            return FFGPU_ERR_NOMEM;
+        }
+        pl.bytes = want;
+    }
+    *out = &pl;
+    return FFGPU_OK;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D map over channel planes [nch][rows][kp] of bf16, box 64 x box_rows x 1,
+// 128-byte swizzle (the layout the tensor-core descriptors expect).
+static bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uint64_t nch,
+                          uint32_t box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {kp, rows, nch};
+    cuuint64_t strides[2] = {kp * 2, rows * kp * 2};
+    cuuint32_t box[3] = {64, box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t slots, planesA, planesB, total;
+};
+
+static Layout layout_for(int64_t m, int64_t n, int64_t kp, int nch, int grid) {
+    Layout L;
+    L.slots = 0;
+    L.planesA = align256(size_t(grid) * kSlotBytesPerCta);
+    L.planesB = L.planesA + align256(size_t(nch) * m * kp * 2);
+    L.total = L.planesB + align256(size_t(nch) * n * kp * 2);
+    return L;
+}
+
+static int64_t round64(int64_t x) { return (x + 63) / 64 * 64; }
+
+static int grid_for_tiles(int64_t m, int64_t n, int dev_sms) {
+    const int64_t tiles = ((m + kTileM - 1) / kTileM) * ((n + kTileN - 1) / kTileN);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dev_sms));
+}
+
+static ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
+                               const void* B, int64_t ldb, const void* C, int64_t ldc) {
+    if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
+    if (m < 0 || n < 0 || k < 0) return FFGPU_ERR_INVALID;
+    if (m > INT32_MAX / 2 || n > INT32_MAX / 2 || k > INT32_MAX / 2) return FFGPU_ERR_INVALID;
+    if (m == 0 || n == 0) return FFGPU_OK;
+    if (!C || ldc < n) return FFGPU_ERR_INVALID;
+    if (k > 0 && (!A || !B || lda < k || ldb < n)) return FFGPU_ERR_INVALID;
+    return FFGPU_OK;
+}
+
+// Workspace bytes for the largest launch of a problem.
+static size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
+    if (m == 0 || n == 0 || k == 0) return 0;
+    RnsPlan pl;
+    make_plan(p, k, pl);
+    const int64_t ks = std::min<int64_t>(k, pl.k_slice);
+    return layout_for(m, n, round64(ks), pl.nch, grid_for_tiles(m, n, sms)).total;
+}
+
+// The launch sequence: per slice of the inner dimension, convert A and B to
+// channel planes and run the tensor-core kernel (beta applies to the first
+// slice only; later slices accumulate with beta = 1).
+static ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                              const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                              uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                              int* err, cudaStream_t s) {
+    const unsigned long long mu = barrett_mu(p);
+    const uint32_t al = alpha % p;
+    uint32_t be = beta % p;
+    if (k == 0)
+        return timed_launch("scale_mod_p", s, [&] { return launch_scale(C, ldc, (int)m, (int)n, p, be, mu, s); }) ==
+                       cudaSuccess
+                   ? FFGPU_OK
+                   : FFGPU_ERR_CUDA;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int grid = grid_for_tiles(m, n, sm_count(dev));
+    RnsPlan pl0;
+    make_plan(p, k, pl0);
+    const int64_t kslice = std::min<int64_t>(k, pl0.k_slice);
+    for (int64_t k0 = 0; k0 < k; k0 += kslice) {
+        const int64_t ks = std::min<int64_t>(kslice, k - k0);
+        RnsPlan pl;
+        make_plan(p, ks, pl);
+        const int64_t kp = round64(ks);
+        const Layout L = layout_for(m, n, kp, pl.nch, grid);
+        if (L.total > ws_bytes) return FFGPU_ERR_NOMEM;
+        unsigned char* wsb = static_cast<unsigned char*>(ws);
+
+        ConvertParams cp;
+        std::memset(&cp, 0, sizeof(cp));
+        cp.p = p;
+        cp.half_p = p / 2;
+        cp.mu = mu;
+        cp.nch = pl.nch;
+        cp.direct = pl.mode == 1;
+        for (int c = 0; c < pl.nch; ++c) {
+            cp.mod[c] = pl.mod[c];
+            cp.pmod[c] = p % pl.mod[c];
+            cp.magic[c] = ((1ull << 40) + pl.mod[c] - 1) / pl.mod[c];
+        }
+        if (timed_launch("convert_rows", s, [&] {
+                return launch_convert_rows(A + k0, lda, (int)m, (int)ks, (int)kp, cp, wsb + L.planesA, s);
+            }) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+        if (timed_launch("convert_transpose", s, [&] {
+                return launch_convert_transpose(B + k0 * ldb, ldb, (int)ks, (int)n, (int)kp, cp, wsb + L.planesB,
+                                                s);
+            }) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+
+        CUtensorMap mapA, mapB;
+        if (!encode_planes(&mapA, wsb + L.planesA, kp, m, pl.nch, kTileM) ||
+            !encode_planes(&mapB, wsb + L.planesB, kp, n, pl.nch, kTileN))
+            return FFGPU_ERR_CUDA;
+
+        RnsGemmParams P;
+        std::memset(&P, 0, sizeof(P));
+        P.m = (int)m;
+        P.n = (int)n;
+        P.ksteps = (int)(kp / kTileK);
+        P.tiles_m = (int)((m + kTileM - 1) / kTileM);
+        P.tiles_n = (int)((n + kTileN - 1) / kTileN);
+        P.num_tiles = P.tiles_m * P.tiles_n;
+        P.nch = pl.nch;
+        P.direct = pl.mode == 1;
+        P.p = p;
+        P.alpha = al;
+        P.beta = be;
+        P.mu = mu;
+        P.C = C;
+        P.ldc = ldc;
+        P.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
+        P.slots = wsb + L.slots;
+        P.err = err;
+        for (int c = 0; c < pl.nch; ++c) {
+            P.modf[c] = (float)pl.mod[c];
+            P.inv_m[c] = 1.0f / (float)pl.mod[c];
+            P.modu[c] = pl.mod[c];
+            P.u[c] = pl.u[c];
+            P.W[c] = pl.W[c];
+        }
+        P.negMp = pl.negMp;
+        if (timed_launch("rns_gemm", s, [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+        be = 1;  // later slices accumulate onto the partial result
+    }
+    return FFGPU_OK;
+}
+
+}  // namespace ffgpu
+
+using namespace ffgpu;
+
+extern "C" {
+
+const char* ffgpu_status_string(ffgpu_status s) {
+    switch (s) {
+        case FFGPU_OK: return "FFGPU_OK";
+        case FFGPU_ERR_INVALID: return "FFGPU_ERR_INVALID";
+        case FFGPU_ERR_UNSUPPORTED_P: return "FFGPU_ERR_UNSUPPORTED_P";
+        case FFGPU_ERR_NOMEM: return "FFGPU_ERR_NOMEM";
+        case FFGPU_ERR_CUDA: return "FFGPU_ERR_CUDA";
+        case FFGPU_ERR_TIMEOUT: return "FFGPU_ERR_TIMEOUT";
+        case FFGPU_ERR_BUDGET: return "FFGPU_ERR_BUDGET";
+    }
+    return "FFGPU_UNKNOWN_STATUS";
+}
+
+int ffgpu_version(void) { return 100; }
+
+ffgpu_status ffgpu_fgemm_workspace_size(int64_t m, int64_t n, int64_t k, uint32_t p, size_t* bytes) {
+    if (!bytes) return FFGPU_ERR_INVALID;
+    const ffgpu_status st = check_args(m, n, k, p, (const void*)1, std::max<int64_t>(k, 1), (const void*)1,
+                                       std::max<int64_t>(n, 1), (const void*)1, std::max<int64_t>(n, 1));
+    if (st != FFGPU_OK) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        *bytes = fgemm_ws_bytes(m, n, k, p, 256);
+        return FFGPU_OK;
+    }
+    *bytes = fgemm_ws_bytes(m, n, k, p, sm_count(dev));
+    return FFGPU_OK;
+}
+
+ffgpu_status ffgpu_fgemm_plan(int64_t m, int64_t n, int64_t k, uint32_t p, ffgpu_plan_info* out) {
+    if (!out) return FFGPU_ERR_INVALID;
+    if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
+    if (m < 0 || n < 0 || k < 0) return FFGPU_ERR_INVALID;
+    std::memset(out, 0, sizeof(*out));
+    RnsPlan pl;
+    make_plan(p, std::max<int64_t>(k, 1), pl);
+    const int64_t ks = std::min<int64_t>(std::max<int64_t>(k, 1), pl.k_slice);
+    out->mode = pl.mode;
+    out->channels = pl.nch;
+    for (int c = 0; c < pl.nch; ++c) out->moduli[c] = pl.mod[c];
+    out->k_chunk = kChunkSteps * kTileK;
+    out->k_slices = (int32_t)((std::max<int64_t>(k, 1) + ks - 1) / ks);
+    out->tile_m = kTileM;
+    out->tile_n = kTileN;
+    out->tile_k = kTileK;
+    out->mma_flops = 2.0 * (double)m * (double)n * (double)round64(k) * (double)pl.nch;
+    return FFGPU_OK;
+}
+
+ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                            const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                            uint32_t beta, uint32_t* C, int64_t ldc, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
+    if (st != FFGPU_OK || m == 0 || n == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Pool* pool = nullptr;
+    st = pool_get(s, 0, &pool);
+    if (st != FFGPU_OK) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (workspace_bytes < fgemm_ws_bytes(m, n, k, p, sm_count(dev))) return FFGPU_ERR_NOMEM;
+    if (workspace_bytes && (reinterpret_cast<uintptr_t>(workspace) & 255)) return FFGPU_ERR_INVALID;
+    return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, workspace, workspace_bytes,
+                     pool->err, s);
+}
+
+ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                         const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta,
+                         uint32_t* C, int64_t ldc, void* stream) {
+    ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
+    if (st != FFGPU_OK || m == 0 || n == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    const size_t need = fgemm_ws_bytes(m, n, k, p, sm_count(dev));
+    Pool* pool = nullptr;
+    st = pool_get(s, need, &pool);
+    if (st != FFGPU_OK) return st;
+    return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, pool->ptr, pool->bytes, pool->err,
+                     s);
+}
+
+ffgpu_status ffgpu_last_device_error(void* stream) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return FFGPU_ERR_CUDA;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    int* err = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_pools.find(std::make_pair(dev, s));
+        if (it == g_pools.end() || !it->second.err) return FFGPU_OK;
+        err = it->second.err;
+    }
+    int v = 0;
+    if (cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFGPU_ERR_CUDA;
+    if (v != 0) {
+        cudaMemset(err, 0, sizeof(int));
+        return FFGPU_ERR_TIMEOUT;
+    }
+    return FFGPU_OK;
+}
+
+ffgpu_status ffgpu_profile_enable(int on) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = on != 0;
+    return FFGPU_OK;
+}
+
+ffgpu_status ffgpu_profile_read(ffgpu_kernel_time* out, int cap, int* count) {
+    if (cap < 0 || (cap > 0 && !out) || !count) return FFGPU_ERR_INVALID;
+    std::vector<ProfEntry> entries;
+    {
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        entries.swap(g_prof);
+    }
+    std::map<std::string, std::pair<int64_t, double>> acc;
+    ffgpu_status st = FFGPU_OK;
+    for (auto& e : entries) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(e.stop) != cudaSuccess || cudaEventElapsedTime(&ms, e.start, e.stop) != cudaSuccess) {
+            cudaGetLastError();
+            st = FFGPU_ERR_CUDA;
+        }
+        auto& a = acc[e.name];
+        a.first += 1;
+        a.second += ms;
+        cudaEventDestroy(e.start);
+        cudaEventDestroy(e.stop);
+    }
+    int i = 0;
+    for (auto& kv : acc) {
+        if (i < cap) {
+            std::memset(&out[i], 0, sizeof(out[i]));
+            std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.first;
+            out[i].total_ms = kv.second.second;
+        }
+        ++i;
+    }
+    *count = i;
+    return st;
+}
+
+ffgpu_status ffgpu_release_workspaces(void) {
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return FFGPU_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : g_pools) {
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+        if (kv.second.err) cudaFree(kv.second.err);
+    }
+    g_pools.clear();
+    return FFGPU_OK;
+}
+
+}  // extern "C"

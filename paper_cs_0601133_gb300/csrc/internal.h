@@ -1,0 +1,112 @@
+// Internal declarations shared by the CUDA translation units of libffgpu.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ffgpu.h"
+
+namespace ffgpu {
+
+// ---------------------------------------------------------------------------
+// Residue number system.  Moduli <= 256 whose balanced residues (|r| <= 128)
+// are exact bfloat16 values; pairwise coprime; in decreasing order so that the
+// first c of them give the largest product for c channels.
+// ---------------------------------------------------------------------------
+constexpr int kMaxChannels = 12;
+constexpr uint32_t kModuli[kMaxChannels] = {256, 255, 253, 251, 247, 241,
+                                            239, 233, 229, 227, 223, 211};
+
+// Tile of the tensor-core kernel.
+constexpr int kTileM = 128;
+constexpr int kTileN = 256;
+constexpr int kTileK = 64;       // one 128-byte swizzle row of bf16
+constexpr int kChunkSteps = 8;   // 8 x 64 = 512 products summed between in-place reductions
+constexpr int kStages = 4;
+
+// Error codes written to the device error word.
+enum DevErr : int {
+    kDevOk = 0,
+    kDevTimeoutProducer = 1,
+    kDevTimeoutMma = 2,
+    kDevTimeoutEpilogue = 3,
+    kDevTimeoutDrain = 4,
+};
+
+struct RnsPlan {
+    int mode;        // 1 = direct (modulus p itself), 2 = RNS
+    int nch;         // channels
+    uint32_t p;
+    uint32_t mod[kMaxChannels];
+    uint32_t u[kMaxChannels];      // (M/m_c)^{-1} mod m_c
+    uint32_t W[kMaxChannels];      // (M/m_c) mod p
+    uint32_t negMp;                // (p - (M mod p)) mod p
+    int64_t k_slice;               // largest inner length one launch may sum
+};
+
+// Parameters of the tensor-core kernel (passed by value).
+struct RnsGemmParams {
+    int m, n;
+    int ksteps;          // kp / 64
+    int tiles_m, tiles_n, num_tiles;
+    int nch;
+    int direct;
+    uint32_t p;
+    uint32_t alpha, beta;          // reduced mod p
+    unsigned long long mu;         // floor((2^64-1)/p)
+    uint32_t* C;
+    long long ldc;
+    int vec_ok;                    // 16-byte vector access to C is legal
+    unsigned char* slots;          // per-CTA residue slots
+    int* err;                      // device error word
+    float modf[kMaxChannels];
+    float inv_m[kMaxChannels];
+    uint32_t modu[kMaxChannels];
+    uint32_t u[kMaxChannels];
+    uint32_t W[kMaxChannels];
+    uint32_t negMp;
+};
+
+constexpr size_t kSlotBytesPerCta = size_t(kMaxChannels) * kTileM * kTileN;
+
+// Conversion parameters: uint32 words -> bf16 channel planes.
+struct ConvertParams {
+    uint32_t p;
+    uint32_t half_p;                 // floor(p/2): residues above it are centred to x - p
+    unsigned long long mu;           // floor((2^64-1)/p)
+    int nch;
+    int direct;
+    uint32_t mod[kMaxChannels];
+    uint32_t pmod[kMaxChannels];     // p mod m_c
+    unsigned long long magic[kMaxChannels];  // ceil(2^40 / m_c)
+};
+
+// host launchers (implemented in the .cu files)
+cudaError_t launch_convert_rows(const uint32_t* X, long long ldx, int rows, int cols, int colsp,
+                                const ConvertParams& cp, void* planes, cudaStream_t s);
+cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows, int cols, int rowsp,
+                                     const ConvertParams& cp, void* planes, cudaStream_t s);
+cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, uint32_t beta,
+                         unsigned long long mu, cudaStream_t s);
+cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
+                            const RnsGemmParams& prm, int grid, cudaStream_t s);
+size_t rns_gemm_smem_bytes();
+
+// Kernel timing (ffgpu_profile_*): brackets a launch with events on `s`.
+bool profiling_on();
+void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop);
+
+template <class F>
+cudaError_t timed_launch(const char* name, cudaStream_t s, F&& launch) {
+    if (!profiling_on()) return launch();
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cudaErrorUnknown;
+    cudaEventRecord(a, s);
+    const cudaError_t e = launch();
+    cudaEventRecord(b, s);
+    profile_record(name, a, b);
+    return e;
+}
+
+}  // namespace ffgpu

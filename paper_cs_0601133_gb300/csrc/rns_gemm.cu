@@ -1,0 +1,398 @@
+// Tensor-core product over a residue number system, with the reduction mod p
+// fused into the epilogue.
+//
+// What it computes (section 3, C <- alpha*A*B + beta*C over Z/pZ): A and B
+// arrive as "channel planes": for each small modulus m_c (<= 256) the
+// balanced residues of the centred inputs, stored as bf16 (exact, |r| <= 128).
+// For every 128 x 256 output tile and every channel c the kernel forms
+// S_c = sum_t A_c[i][t] * B_c[j][t] on the tcgen05 tensor cores with an f32
+// accumulator in tensor memory.  This is the delayed reduction of section
+// 2.1.2 restated for the accumulator: products of balanced residues are below
+// 2^14 in magnitude, so 512 of them plus a reduced value (|v| <= 129) stay
+// below 2^24, where every f32 sum of integers is exact (eq. 1 with gamma = 24).
+// After each 512-long chunk the epilogue warps reduce the accumulator mod m_c
+// in place (tcgen05.ld -> fma -> tcgen05.st) and the MMAs continue on top of it.
+// After the last chunk each channel yields S mod m_c; the last channel of a
+// tile triggers the reconstruction of S mod p from all residues (Chinese
+// remainder theorem, the multi-modular route to p > 2^26 the paper lists as
+// future work in section 7), then C = (alpha*S + beta*C) mod p.
+//
+// Roles (one CTA per SM, persistent over tiles):
+//   warp 0      TMA producer: channel tiles of A (128x64) and B (256x64), 4 stages
+//   warp 1      TMEM allocator and single-thread MMA issuer (M=128, N=256, K=16)
+//   warps 2..9  epilogue: lane quarter (warp % 4) x column half ((warp-2) / 4)
+// Two 256-column accumulators: the jobs (tile, channel) of a CTA are paired and
+// their chunks interleaved, so one accumulator is reduced while the tensor
+// cores fill the other.
+#include "devutil.cuh"
+#include "internal.h"
+
+namespace ffgpu {
+
+namespace {
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kABytes = kTileM * kTileK * 2;
+constexpr uint32_t kBBytes = kTileN * kTileK * 2;
+constexpr uint32_t kStageBytes = kABytes + kBBytes;
+constexpr uint32_t kTmemCols = 512;
+constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
+constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + 256;
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+    const int per_group = kGroupM * tiles_n;
+    const int g = t / per_group;
+    const int first = g * kGroupM;
+    const int gm = min(tiles_m - first, kGroupM);
+    const int r = t - g * per_group;
+    tm = first + r % gm;
+    tn = r / gm;
+}
+
+// Wait that ignores the abort flag (used to drain in-flight asynchronous work
+// before the CTA releases shared and tensor memory); still bounded in time.
+__device__ __forceinline__ void mbar_drain_wait(uint64_t* bar, uint32_t parity, int* err) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitLimitCycles) {
+            atomicCAS(err, 0, (int)kDevTimeoutDrain);
+            return;
+        }
+    }
+}
+
+// Exact residue in [0, m) of an f32 holding an integer of magnitude < 2^24.
+__device__ __forceinline__ uint32_t f32_residue(float x, float m, float inv_m, int mi) {
+    const float q = rintf(x * inv_m);
+    int r = (int)fmaf(-q, m, x);
+    if (r < 0) r += mi;
+    if (r >= mi) r -= mi;
+    return (uint32_t)r;
+}
+
+// Reconstruction of X mod p for four adjacent outputs from their residues.
+// With M = prod m_c and b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c)
+// - q M where q = round(sum_c b_c / m_c), valid because the plan guarantees
+// |X| <= M/4 (the fraction is within 1/4 of an integer, far above f32 error).
+__device__ __forceinline__ void crt4(const RnsGemmParams& P, const unsigned char* slot, int g,
+                                     uint32_t (&X)[4]) {
+    unsigned long long S[4] = {0ull, 0ull, 0ull, 0ull};
+    float G[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < P.nch; ++c) {
+        const uint32_t w =
+            *reinterpret_cast<const uint32_t*>(slot + size_t(c) * kTileM * kTileN + 4 * g);
+        const uint32_t uc = P.u[c], mc = P.modu[c], Wc = P.W[c];
+        const float im = P.inv_m[c];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int t = (int)(((w >> (8 * e)) & 255u) * uc);
+            const int qf = (int)floorf((float)t * im);
+            int b = t - qf * (int)mc;
+            if (b < 0) b += (int)mc;
+            if (b >= (int)mc) b -= (int)mc;
+            G[e] = fmaf((float)b, im, G[e]);
+            S[e] += (unsigned long long)b * Wc;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const unsigned long long q = (unsigned long long)rintf(G[e]);
+        X[e] = mod_u64(S[e] + q * P.negMp, P.p, P.mu);
+    }
+}
+
+__device__ __forceinline__ void combine_tile_row(const RnsGemmParams& P, int tm, int tn,
+                                                 int row_local, int half,
+                                                 const unsigned char* slot_row) {
+    const int row = tm * kTileM + row_local;
+    if (row >= P.m) return;
+    uint32_t* crow = P.C + (long long)row * P.ldc;
+    const int col0 = tn * kTileN + half * 128;
+    for (int g = 0; g < 32; ++g) {
+        const int col = col0 + 4 * g;
+        if (col >= P.n) break;
+        uint32_t X[4];
+        if (P.direct) {
+            const uint32_t w = *reinterpret_cast<const uint32_t*>(slot_row + 4 * g);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) X[e] = (w >> (8 * e)) & 255u;
+        } else {
+            crt4(P, slot_row, g, X);
+        }
+        const bool full4 = col + 3 < P.n;
+        uint32_t old[4] = {0u, 0u, 0u, 0u};
+        if (P.beta != 0) {
+            if (full4 && P.vec_ok) {
+                const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
+                old[0] = v.x; old[1] = v.y; old[2] = v.z; old[3] = v.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (col + e < P.n) old[e] = crow[col + e];
+            }
+        }
+        uint32_t out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            out[e] = mod_u64((unsigned long long)P.alpha * X[e] + (unsigned long long)P.beta * old[e],
+                             P.p, P.mu);
+        if (full4 && P.vec_ok) {
+            *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (col + e < P.n) crow[col + e] = out[e];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB,
+                    const __grid_constant__ RnsGemmParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sA = base;
+    unsigned char* sB = base + kStages * kABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kStages;
+    uint64_t* acc_full = bars + 2 * kStages;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    const int my_tiles =
+        (int)blockIdx.x < P.num_tiles ? (P.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nch = P.nch;
+    const int J = my_tiles * nch;                       // jobs (tile, channel) of this CTA
+    const int H = (P.ksteps + kChunkSteps - 1) / kChunkSteps;  // chunks per job
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tc_alloc(tmem_slot, kTmemCols);
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0, last_parity = 0;
+            bool ok = true;
+            for (int pi = 0; 2 * pi < J && ok; ++pi) {
+                const int nj = min(2, J - 2 * pi);
+                for (int h = 0; h < H && ok; ++h) {
+                    const int k0 = h * kChunkSteps;
+                    const int steps = min(kChunkSteps, P.ksteps - k0);
+                    for (int s = 0; s < nj && ok; ++s) {
+                        const int j = 2 * pi + s;
+                        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
+                        const int c = j % nch;
+                        int tm, tn;
+                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
+                        for (int st = 0; st < steps; ++st) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, P.err,
+                                           kDevTimeoutProducer)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(&full[stage], kStageBytes);
+                            const int kx = (k0 + st) * kTileK;
+                            tma_load_3d(sA + stage * kABytes, &mapA, kx, tm * kTileM, c, &full[stage]);
+                            tma_load_3d(sB + stage * kBBytes, &mapB, kx, tn * kTileN, c, &full[stage]);
+                            issued |= 1u << stage;
+                            last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            // every issued copy must have landed before shared memory is released
+            for (int s2 = 0; s2 < kStages; ++s2)
+                if (issued & (1u << s2)) mbar_drain_wait(&full[s2], (last_parity >> s2) & 1u, P.err);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t accp[2] = {0u, 0u};
+            const uint32_t idesc = idesc_bf16_f32(kTileM, kTileN);
+            bool ok = true;
+            bool any = false;
+            for (int pi = 0; 2 * pi < J && ok; ++pi) {
+                const int nj = min(2, J - 2 * pi);
+                for (int h = 0; h < H && ok; ++h) {
+                    const int steps = min(kChunkSteps, P.ksteps - h * kChunkSteps);
+                    for (int s = 0; s < nj && ok; ++s) {
+                        if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, P.err, kDevTimeoutMma)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d = tmem + (uint32_t)(s * kTileN);
+                        for (int st = 0; st < steps; ++st) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, P.err, kDevTimeoutMma)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_addr(sA + stage * kABytes);
+                            const uint32_t b0 = smem_addr(sB + stage * kBBytes);
+#pragma unroll
+                            for (int kk = 0; kk < kTileK / 16; ++kk) {
+                                const uint32_t acc = (h > 0 || st > 0 || kk > 0) ? 1u : 0u;
+                                tc_mma_bf16(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
+                                            idesc, acc);
+                            }
+                            tc_commit(&empty[stage]);
+                            any = true;
+                            if (++stage == kStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        tc_commit(&acc_full[s]);
+                        accp[s] ^= 1u;
+                    }
+                }
+            }
+            // all issued MMAs must complete before tensor memory is released
+            if (any) {
+                tc_commit(drain);
+                mbar_drain_wait(drain, 0u, P.err);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_local = q * 32 + lane;
+        unsigned char* slot_base = P.slots + size_t(blockIdx.x) * kSlotBytesPerCta;
+        unsigned char* slot_row = slot_base + row_local * kTileN + half * 128;
+        uint32_t accp[2] = {0u, 0u};
+        bool ok = true;
+        for (int pi = 0; 2 * pi < J && ok; ++pi) {
+            const int nj = min(2, J - 2 * pi);
+            for (int h = 0; h < H && ok; ++h) {
+                const bool last_chunk = (h == H - 1);
+                for (int s = 0; s < nj; ++s) {
+                    const int j = 2 * pi + s;
+                    const int c = j % nch;
+                    if (!mbar_wait(&acc_full[s], accp[s], abort_flag, P.err, kDevTimeoutEpilogue)) {
+                        ok = false;
+                        break;
+                    }
+                    accp[s] ^= 1u;
+                    tc_fence_after();
+                    const uint32_t tbase =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
+                    const float mf = P.modf[c], im = P.inv_m[c];
+                    const int mi = (int)P.modu[c];
+                    if (!last_chunk) {
+#pragma unroll 1
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t v[32];
+                            tc_ld32(tbase + cc * 32, v);
+                            tc_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const float x = __uint_as_float(v[i]);
+                                const float qq = rintf(x * im);
+                                v[i] = __float_as_uint(fmaf(-qq, mf, x));
+                            }
+                            tc_st32(tbase + cc * 32, v);
+                        }
+                        tc_wait_st();
+                    } else {
+                        unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
+#pragma unroll 1
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t v[32];
+                            tc_ld32(tbase + cc * 32, v);
+                            tc_wait_ld();
+                            uint32_t w[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                uint32_t packed = 0;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    packed |= f32_residue(__uint_as_float(v[4 * i + e]), mf, im, mi)
+                                              << (8 * e);
+                                w[i] = packed;
+                            }
+                            uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
+                            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&acc_empty[s]);
+                    if (last_chunk && c == nch - 1) {
+                        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
+                        int tm, tn;
+                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
+                        combine_tile_row(P, tm, tn, row_local, half, slot_row);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tc_dealloc(tmem, kTmemCols);
+    }
+}
+
+}  // namespace
+
+size_t rns_gemm_smem_bytes() { return kSmemBytes; }
+
+cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
+                            const RnsGemmParams& prm, int grid, cudaStream_t s) {
+    static bool attr_set = false;  // per process; the attribute is per function
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rns_gemm_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    rns_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(mapA, mapB, prm);
+    return cudaGetLastError();
+}
+
+}  // namespace ffgpu

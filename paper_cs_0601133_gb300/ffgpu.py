@@ -1,0 +1,192 @@
+"""Python binding of libffgpu (ctypes).  Argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module
+turns torch tensors into pointers, leading dimensions and the current CUDA
+stream, and turns status codes into exceptions.  PyTorch is used for device
+memory and streams only.  There is no CPU fallback: if the library is missing
+or a call fails, an exception is raised.
+
+Tensors are row-major 2-D CUDA tensors of dtype torch.uint32 or torch.int32
+(the bits are read as uint32 words) with unit stride along rows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libffgpu.so")
+
+STATUS = {
+    0: "FFGPU_OK",
+    -1: "FFGPU_ERR_INVALID",
+    -2: "FFGPU_ERR_UNSUPPORTED_P",
+    -3: "FFGPU_ERR_NOMEM",
+    -4: "FFGPU_ERR_CUDA",
+    -5: "FFGPU_ERR_TIMEOUT",
+    -6: "FFGPU_ERR_BUDGET",
+}
+
+
+class FFGPUError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, "status %d" % status), (": " + what) if what else ""))
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("moduli", ctypes.c_uint32 * 16), ("k_chunk", ctypes.c_int32),
+                ("k_slices", ctypes.c_int32), ("tile_m", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("tile_k", ctypes.c_int32),
+                ("mma_flops", ctypes.c_double)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_I64, _U32, _VP, _I32 = ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int
+# name -> argument types (restype is int status unless listed in _RESTYPES)
+SIGNATURES = {
+    "ffgpu_status_string": [_I32],
+    "ffgpu_version": [],
+    "ffgpu_fgemm": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
+    "ffgpu_fgemm_workspace_size": [_I64, _I64, _I64, _U32, ctypes.POINTER(ctypes.c_size_t)],
+    "ffgpu_fgemm_ws": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64,
+                       _VP, ctypes.c_size_t, _VP],
+    "ffgpu_fgemm_plan": [_I64, _I64, _I64, _U32, ctypes.POINTER(PlanInfo)],
+    "ffgpu_last_device_error": [_VP],
+    "ffgpu_release_workspaces": [],
+    "ffgpu_profile_enable": [_I32],
+    "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
+}
+_RESTYPES = {"ffgpu_status_string": ctypes.c_char_p}
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libffgpu.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = _RESTYPES.get(name, ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str = "") -> None:
+    if status != 0:
+        raise FFGPUError(status, what)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _mat(t, name: str):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype not in (torch.uint32, torch.int32):
+        raise TypeError("%s must be uint32 or int32, got %s" % (name, t.dtype))
+    if t.dim() != 2:
+        raise ValueError("%s must be 2-D" % name)
+    if t.shape[1] > 1 and t.stride(1) != 1:
+        raise ValueError("%s must have unit stride along rows" % name)
+    ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)
+    return t.data_ptr(), max(ld, t.shape[1], 1)
+
+
+def fgemm(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, stream=None):
+    """C <- (alpha*A@B + beta*C) mod p on the GPU; allocates C (zeros) if None. Returns C."""
+    import torch
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ: %d vs %d" % (k, k2))
+    if C is None:
+        C = torch.zeros((m, n), dtype=torch.uint32, device=A.device)
+        beta = 0
+    if tuple(C.shape) != (m, n):
+        raise ValueError("C has shape %s, expected %s" % (tuple(C.shape), (m, n)))
+    a, lda = _mat(A, "A")
+    b, ldb = _mat(B, "B")
+    c, ldc = _mat(C, "C")
+    check(lib().ffgpu_fgemm(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
+                            _stream_ptr(stream)), "ffgpu_fgemm")
+    return C
+
+
+def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
+    """The raw C-ABI call on device pointers; returns the status code."""
+    return lib().ffgpu_fgemm(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr)
+
+
+def fgemm_workspace_size(m, n, k, p) -> int:
+    out = ctypes.c_size_t(0)
+    check(lib().ffgpu_fgemm_workspace_size(m, n, k, p, ctypes.byref(out)), "workspace_size")
+    return out.value
+
+
+def fgemm_ws(A, B, p, alpha, beta, C, workspace, stream=None):
+    """ffgpu_fgemm_ws with a caller-owned workspace tensor (any dtype, contiguous, CUDA)."""
+    m, k = A.shape
+    n = B.shape[1]
+    a, lda = _mat(A, "A")
+    b, ldb = _mat(B, "B")
+    c, ldc = _mat(C, "C")
+    nbytes = workspace.numel() * workspace.element_size()
+    check(lib().ffgpu_fgemm_ws(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
+                               workspace.data_ptr(), nbytes, _stream_ptr(stream)), "ffgpu_fgemm_ws")
+    return C
+
+
+def fgemm_plan(m: int, n: int, k: int, p: int) -> dict:
+    info = PlanInfo()
+    check(lib().ffgpu_fgemm_plan(m, n, k, p, ctypes.byref(info)), "plan")
+    return dict(mode=info.mode, channels=info.channels, moduli=list(info.moduli[: info.channels]),
+                k_chunk=info.k_chunk, k_slices=info.k_slices,
+                tile=(info.tile_m, info.tile_n, info.tile_k), mma_flops=info.mma_flops)
+
+
+def last_device_error(stream=None) -> int:
+    return lib().ffgpu_last_device_error(_stream_ptr(stream))
+
+
+def release_workspaces() -> None:
+    check(lib().ffgpu_release_workspaces(), "release_workspaces")
+
+
+def status_string(code: int) -> str:
+    return lib().ffgpu_status_string(code).decode()
+
+
+def version() -> int:
+    return lib().ffgpu_version()
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record CUDA events around every library kernel launch (on its stream)."""
+    check(lib().ffgpu_profile_enable(1 if on else 0), "profile_enable")
+
+
+def profile_read() -> dict:
+    """{kernel name: (launches, total ms)} since the last read; synchronizes the events."""
+    cap = 64
+    arr = (KernelTime * cap)()
+    cnt = ctypes.c_int(0)
+    check(lib().ffgpu_profile_read(arr, cap, ctypes.byref(cnt)), "profile_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(cnt.value, cap))}

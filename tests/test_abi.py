@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point the header declares, rejects bad arguments before touching
+the device, and plans moduli that satisfy the exactness bound."""
+import math
+import os
+import re
+
+import pytest
+
+import paper_cs_0601133_gb300 as ff
+from paper_cs_0601133_gb300 import ffgpu as binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"FFGPU_API\s+[\w\s\*]+?\b(ffgpu_\w+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert "ffgpu_fgemm" in names and len(names) >= 8
+    L = ff.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    # and the binding knows every one of them
+    assert names <= set(binding.SIGNATURES)
+
+
+def test_status_strings_and_version():
+    assert ff.version() >= 100
+    for code, name in binding.STATUS.items():
+        assert ff.status_string(code) == name
+
+
+def test_invalid_arguments_rejected_without_device():
+    f = ff.fgemm_ptr
+    assert f(4, 4, 4, 1, 1, 8, 4, 8, 4, 0, 8, 4) == -2          # p < 2
+    assert f(4, 4, 4, 2**31, 1, 8, 4, 8, 4, 0, 8, 4) == -2      # p > 2^31 - 1
+    assert f(-1, 4, 4, 7, 1, 8, 4, 8, 4, 0, 8, 4) == -1         # negative m
+    assert f(4, 4, 4, 7, 1, 8, 3, 8, 4, 0, 8, 4) == -1          # lda < k
+    assert f(4, 4, 4, 7, 1, 8, 4, 8, 3, 0, 8, 4) == -1          # ldb < n
+    assert f(4, 4, 4, 7, 1, 8, 4, 8, 4, 0, 8, 3) == -1          # ldc < n
+    assert f(4, 4, 4, 7, 1, 0, 4, 8, 4, 0, 8, 4) == -1          # null A
+    assert f(0, 4, 4, 7, 1, 0, 4, 0, 4, 0, 0, 4) == 0           # m = 0: nothing to do
+
+
+MODULI_LIMIT = 256
+
+
+def test_plan_moduli_are_coprime_and_sufficient():
+    for p in (2, 3, 5, 251, 256, 257, 65521, 8388593, 2147483647):
+        for k in (1, 64, 512, 8192, 65536, 1 << 20):
+            pl = ff.fgemm_plan(128, 128, k, p)
+            mods = pl["moduli"]
+            assert len(mods) == pl["channels"] >= 1
+            if p <= MODULI_LIMIT:
+                assert pl["mode"] == 1 and mods == [p]
+                continue
+            assert pl["mode"] == 2
+            assert all(2 <= m <= MODULI_LIMIT for m in mods)
+            for i in range(len(mods)):
+                for j in range(i + 1, len(mods)):
+                    assert math.gcd(mods[i], mods[j]) == 1
+            h = p // 2
+            ks = -(-k // pl["k_slices"])
+            M = math.prod(mods)
+            # the sum of ks products of centred residues stays within M/4
+            assert 4 * ks * h * h <= M
+            # and one channel fewer would not do (the plan is minimal)
+            assert 4 * ks * h * h > math.prod(mods[:-1]) or len(mods) == 1
+
+
+def test_plan_channel_counts_of_the_sweep():
+    # p < 2^31 at n = 8192: 10 channels; p < 2^16: 6; p < 2^8: the prime itself
+    assert ff.fgemm_plan(8192, 8192, 8192, 2147483647)["channels"] == 10
+    assert ff.fgemm_plan(8192, 8192, 8192, 8388593)["channels"] == 8
+    assert ff.fgemm_plan(8192, 8192, 8192, 65521)["channels"] == 6
+    assert ff.fgemm_plan(8192, 8192, 8192, 251)["channels"] == 1
+    assert ff.fgemm_plan(8192, 8192, 65536, 2147483647)["channels"] == 10
+
+
+def test_workspace_size_monotone():
+    a = ff.fgemm_workspace_size(1024, 1024, 1024, 65521)
+    b = ff.fgemm_workspace_size(2048, 2048, 2048, 65521)
+    assert 0 < a < b
+    assert ff.fgemm_workspace_size(1024, 1024, 0, 65521) == 0

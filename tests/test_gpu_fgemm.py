@@ -1,0 +1,156 @@
+"""GPU parity of ffgpu_fgemm against the CPU oracle, bit for bit.
+
+Sizes are chosen so that the oracle finishes in seconds while the kernel still
+crosses several tiles (128 x 256), several 512-long chunks of the inner
+dimension (in-place reductions), ragged tails in every dimension, more tiles
+than SMs (several tiles per persistent CTA) and both parities of the channel
+count (jobs paired across tiles).  The full-size configuration is checked on
+sampled entries and by Freivalds' test.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_cs_0601133_gb300 as ff
+from paper_cs_0601133_gb300 import workloads as W
+from tests.gpu_util import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SWEEP = [251, 65521, 8388593, 2147483647]
+
+
+def run(A, B, C, p, alpha, beta, pad=0):
+    dA, dB, dC = to_dev(A, pad), to_dev(B, pad), to_dev(C, pad)
+    ff.fgemm(dA, dB, p, alpha, beta, dC)
+    torch.cuda.synchronize()
+    assert ff.last_device_error() == 0
+    return from_dev(dC)
+
+
+def check(A, B, C, p, alpha, beta, pad=0):
+    got = run(A, B, C, p, alpha, beta, pad)
+    expect = oracle.fgemm(A, B, p, alpha, beta, C)
+    if not np.array_equal(got, expect):
+        bad = np.argwhere(got != expect)
+        i, j = bad[0]
+        raise AssertionError("p=%d shape=%s: %d mismatches, first at (%d,%d): got %d expect %d"
+                             % (p, (A.shape, B.shape), len(bad), i, j, got[i, j], expect[i, j]))
+
+
+def test_config1_512_cube_p65521():
+    A, B, C, _, _ = W.square_problem(512, 65521, with_alpha_beta=False)
+    check(A, B, C, 65521, 1, 0)
+
+
+@pytest.mark.parametrize("p", SWEEP + [2, 3, 256, 257, 1000003])
+def test_random_words_alpha_beta(p):
+    rng = W.rng_for("square", 11, p)
+    m, k, n = 300, 1100, 520          # ragged in every dimension, 3 chunks of k
+    A = W.uniform_words(rng, (m, k))
+    B = W.uniform_words(rng, (k, n))
+    C = W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, 2**32)), int(rng.integers(0, 2**32))
+    check(A, B, C, p, alpha, beta)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 7, 3), (129, 65, 257), (127, 64, 255),
+                                   (128, 512, 256), (256, 513, 512), (5, 2000, 9)])
+@pytest.mark.parametrize("p", [65521, 2147483647])
+def test_ragged_shapes(shape, p):
+    m, k, n = shape
+    rng = W.rng_for("square", 12, m * 7 + k * 3 + n)
+    A = W.uniform_residues(rng, (m, k), p)
+    B = W.uniform_residues(rng, (k, n), p)
+    C = W.uniform_residues(rng, (m, n), p)
+    check(A, B, C, p, 3, 5)
+
+
+@pytest.mark.parametrize("p", SWEEP)
+def test_padded_leading_dimensions(p):
+    rng = W.rng_for("square", 13, p)
+    A = W.uniform_residues(rng, (200, 300), p)
+    B = W.uniform_residues(rng, (300, 270), p)
+    C = W.uniform_residues(rng, (200, 270), p)
+    check(A, B, C, p, 7, 11, pad=5)
+
+
+@pytest.mark.parametrize("p", SWEEP)
+@pytest.mark.parametrize("k", [512, 2048, 4096])
+def test_adversarial_all_p_minus_1(p, k):
+    m, n = 256, 512
+    A, B, C = W.adversarial_problem(m, n, k, p)
+    alpha, beta = p - 1, p - 1
+    got = run(A, B, C, p, alpha, beta)
+    # closed form: (p-1)^2 = 1 mod p, so A*B = k*J and the result is alpha*k + beta*(p-1)
+    expect = (alpha * k + beta * (p - 1)) % p
+    assert np.all(got == expect)
+
+
+@pytest.mark.parametrize("p", [2147483647, 65521])
+def test_many_tiles_per_cta(p):
+    # 16 x 16 tiles > SM count: every persistent CTA walks several tiles
+    m, n, k = 2048, 4096, 256
+    rng = W.rng_for("square", 14, p)
+    A = W.uniform_residues(rng, (m, k), p)
+    B = W.uniform_residues(rng, (k, n), p)
+    C = W.uniform_residues(rng, (m, n), p)
+    check(A, B, C, p, 2, 3)
+
+
+def test_odd_and_even_channel_counts():
+    # p < 2^31 with k = 512 needs 9 channels (odd: jobs pair across tiles), k = 1024 needs 10
+    p = 2147483647
+    assert ff.fgemm_plan(1, 1, 512, p)["channels"] % 2 == 1
+    for k in (512, 1024):
+        rng = W.rng_for("square", 15, k)
+        A = W.uniform_residues(rng, (600, k), p)
+        B = W.uniform_residues(rng, (k, 1100), p)
+        C = W.uniform_residues(rng, (600, 1100), p)
+        check(A, B, C, p, 1, 1)
+
+
+def test_k_zero_and_empty():
+    p = 65521
+    rng = W.rng_for("square", 16)
+    C = W.uniform_words(rng, (33, 47))
+    got = run(np.zeros((33, 0), np.uint32), np.zeros((0, 47), np.uint32), C, p, 9, 10)
+    assert np.array_equal(got, (10 * C.astype(np.uint64) % p).astype(np.uint32))
+    dC = to_dev(C)
+    assert ff.fgemm_ptr(0, 47, 5, p, 1, 0, 5, 0, 47, 0, dC.data_ptr(), 47) == 0
+
+
+def test_caller_workspace_matches_pool():
+    p = 8388593
+    rng = W.rng_for("square", 17)
+    A = W.uniform_residues(rng, (300, 700), p)
+    B = W.uniform_residues(rng, (700, 400), p)
+    C = W.uniform_residues(rng, (300, 400), p)
+    ws_bytes = ff.fgemm_workspace_size(300, 400, 700, p)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    dA, dB, dC = to_dev(A), to_dev(B), to_dev(C)
+    ff.fgemm_ws(dA, dB, p, 5, 6, dC, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(from_dev(dC), oracle.fgemm(A, B, p, 5, 6, C))
+    small = torch.empty(ws_bytes // 2, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ff.FFGPUError):
+        ff.fgemm_ws(dA, dB, p, 5, 6, dC, small)
+
+
+@pytest.mark.parametrize("p", [65521, 2147483647])
+def test_full_size_8192_sampled(p):
+    """The bench configuration (n = 8192, alpha, beta uniform): 4096 sampled
+    entries recomputed by the oracle, plus Freivalds' test on the whole C."""
+    n = 8192
+    A, B, C, alpha, beta = W.square_problem(n, p)
+    got = run(A, B, C, p, alpha, beta)
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, n, 4096)
+    cols = rng.integers(0, n, 4096)
+    # include the corners and the last tile's ragged edges
+    rows[:4] = [0, 0, n - 1, n - 1]
+    cols[:4] = [0, n - 1, 0, n - 1]
+    expect = oracle.fgemm_entries(A, B, p, alpha, beta, C, rows, cols)
+    assert np.array_equal(got[rows, cols], expect)
+    assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
