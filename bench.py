@@ -40,8 +40,8 @@ KERNEL_SOURCE = os.path.join(ROOT, "paper_cs_0601133_gb300", "csrc", "rns_gemm.c
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["own", "reference"], default="own")
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--p", type=int, default=2147483647)
@@ -165,9 +165,11 @@ def run_reference(args):
     from paper_cs_0601133_gb300 import workloads as W
     import oracle
     A, B, C, alpha, beta = W.square_problem(args.n, args.p)
-    # rows per step: about 5 s of CPU work per step
+    # rows per step sized so the whole run (warm-up + timed steps) takes about
+    # two minutes of CPU work
+    per_step_s = min(5.0, 120.0 / max(1, args.steps + args.warmup))
     t = oracle_sample(A, B, C, args.p, alpha, beta, 4)
-    rows = int(max(2, min(args.n, 4 * 5.0 / max(t, 1e-3))))
+    rows = int(max(1, min(args.n, 4 * per_step_s / max(t, 1e-3))))
     for _ in range(args.warmup):
         oracle_sample(A, B, C, args.p, alpha, beta, rows)
     times = [oracle_sample(A, B, C, args.p, alpha, beta, rows) for _ in range(args.steps)]

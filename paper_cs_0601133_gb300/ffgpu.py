@@ -104,7 +104,7 @@ def _mat(t, name: str):
         raise TypeError("%s must be uint32 or int32, got %s" % (name, t.dtype))
     if t.dim() != 2:
         raise ValueError("%s must be 2-D" % name)
-    if t.shape[1] > 1 and t.stride(1) != 1:
+    if t.numel() > 0 and t.shape[1] > 1 and t.stride(1) != 1:
         raise ValueError("%s must have unit stride along rows" % name)
     ld = t.stride(0) if t.shape[0] > 1 else max(t.shape[1], 1)
     return t.data_ptr(), max(ld, t.shape[1], 1)
