@@ -90,6 +90,40 @@ FFGPU_API ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t 
                             uint32_t beta, uint32_t* C, int64_t ldc,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * ffgpu_fgemm for callers that cannot let the library allocate device memory.
+ * The paper has no counterpart: this is a deployment variant of fgemm.
+ *
+ * Who needs it: code whose host framework owns all device memory and forbids
+ * allocation in its execution path, latency-critical paths that cannot afford
+ * an allocation's implicit synchronisation or its failure, and processes that
+ * have already reserved the whole device.  The call computes the same result
+ * as ffgpu_fgemm (same arguments, same output, bit for bit) but takes its
+ * scratch from a static device array of FFGPU_NOALLOC_SCRATCH_BYTES that the
+ * library holds on every GPU that loads it, until the process exits.  It calls
+ * no cudaMalloc, cudaFree or allocating library routine and records no
+ * profiling events.
+ *
+ * Limit: a problem whose scratch (bf16 channel planes of A and B, plus the
+ * residue slots of at most 32 persistent CTAs) exceeds the array returns
+ * FFGPU_ERR_NOMEM and enqueues nothing; ffgpu_fgemm_workspace_size gives the
+ * order of magnitude (for p < 2^31 about 20*(m+n)*k bytes, so m = n = k = 1024
+ * fits).
+ *
+ * Set-up: the first call on a device looks up the array's device address on
+ * that device (which may load the library's GPU code there); make that first
+ * call before any stream capture.  Every call shares the one array and it
+ * keeps the previous call's contents: calls whose work may overlap on the GPU
+ * (different streams, or different host threads) race and must be ordered by
+ * the caller.  A bounded wait that runs out inside the kernel ends it early and
+ * leaves C undefined; this entry point does not report such a failure.
+ */
+#define FFGPU_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+FFGPU_API ffgpu_status ffgpu_fgemm_noalloc(int64_t m, int64_t n, int64_t k, uint32_t p,
+                                           uint32_t alpha, const uint32_t* A, int64_t lda,
+                                           const uint32_t* B, int64_t ldb, uint32_t beta,
+                                           uint32_t* C, int64_t ldc, void* stream);
+
 /* Description of how ffgpu_fgemm computes a problem (for benchmarks and tests). */
 typedef struct {
     int32_t mode;         /* 1 = single modulus p (p <= 256); 2 = residue number system */

@@ -106,7 +106,7 @@ static std::mutex g_mu;
 static std::map<std::pair<int, cudaStream_t>, Pool> g_pools;
 static std::map<int, int> g_sms;
 
-static int sm_count(int dev) {
+int sm_count(int dev) {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_sms.find(dev);
     if (it != g_sms.end()) return it->second;
@@ -199,7 +199,7 @@ static int grid_for_tiles(int64_t m, int64_t n, int dev_sms) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, dev_sms));
 }
 
-static ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
+ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
                                const void* B, int64_t ldb, const void* C, int64_t ldc) {
     if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
     if (m < 0 || n < 0 || k < 0) return FFGPU_ERR_INVALID;
@@ -211,7 +211,7 @@ static ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, cons
 }
 
 // Workspace bytes for the largest launch of a problem.
-static size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
+size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
     if (m == 0 || n == 0 || k == 0) return 0;
     RnsPlan pl;
     make_plan(p, k, pl);
@@ -222,21 +222,23 @@ static size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sm
 // The launch sequence: per slice of the inner dimension, convert A and B to
 // channel planes and run the tensor-core kernel (beta applies to the first
 // slice only; later slices accumulate with beta = 1).
-static ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
-                              const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
-                              uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
-                              int* err, cudaStream_t s) {
+ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                       const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                       uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                       int* err, cudaStream_t s, int max_grid, bool untimed) {
     const unsigned long long mu = barrett_mu(p);
+    auto launch = [&](const char* name, auto&& f) { return untimed ? f() : timed_launch(name, s, f); };
     const uint32_t al = alpha % p;
     uint32_t be = beta % p;
     if (k == 0)
-        return timed_launch("scale_mod_p", s, [&] { return launch_scale(C, ldc, (int)m, (int)n, p, be, mu, s); }) ==
+        return launch("scale_mod_p", [&] { return launch_scale(C, ldc, (int)m, (int)n, p, be, mu, s); }) ==
                        cudaSuccess
                    ? FFGPU_OK
                    : FFGPU_ERR_CUDA;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int grid = grid_for_tiles(m, n, sm_count(dev));
+    int grid = grid_for_tiles(m, n, sm_count(dev));
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
     RnsPlan pl0;
     make_plan(p, k, pl0);
     const int64_t kslice = std::min<int64_t>(k, pl0.k_slice);
@@ -261,11 +263,11 @@ static ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint3
             cp.pmod[c] = p % pl.mod[c];
             cp.magic[c] = ((1ull << 40) + pl.mod[c] - 1) / pl.mod[c];
         }
-        if (timed_launch("convert_rows", s, [&] {
+        if (launch("convert_rows", [&] {
                 return launch_convert_rows(A + k0, lda, (int)m, (int)ks, (int)kp, cp, wsb + L.planesA, s);
             }) != cudaSuccess)
             return FFGPU_ERR_CUDA;
-        if (timed_launch("convert_transpose", s, [&] {
+        if (launch("convert_transpose", [&] {
                 return launch_convert_transpose(B + k0 * ldb, ldb, (int)ks, (int)n, (int)kp, cp, wsb + L.planesB,
                                                 s);
             }) != cudaSuccess)
@@ -303,7 +305,7 @@ static ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint3
             P.W[c] = pl.W[c];
         }
         P.negMp = pl.negMp;
-        if (timed_launch("rns_gemm", s, [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess)
+        if (launch("rns_gemm", [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess)
             return FFGPU_ERR_CUDA;
         be = 1;  // later slices accumulate onto the partial result
     }
@@ -381,7 +383,7 @@ ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
     if (workspace_bytes < fgemm_ws_bytes(m, n, k, p, sm_count(dev))) return FFGPU_ERR_NOMEM;
     if (workspace_bytes && (reinterpret_cast<uintptr_t>(workspace) & 255)) return FFGPU_ERR_INVALID;
     return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, workspace, workspace_bytes,
-                     pool->err, s);
+                     pool->err, s, 0, false);
 }
 
 ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
@@ -397,7 +399,7 @@ ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t a
     st = pool_get(s, need, &pool);
     if (st != FFGPU_OK) return st;
     return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, pool->ptr, pool->bytes, pool->err,
-                     s);
+                     s, 0, false);
 }
 
 ffgpu_status ffgpu_last_device_error(void* stream) {

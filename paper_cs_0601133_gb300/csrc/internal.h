@@ -93,6 +93,19 @@ cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s);
 size_t rns_gemm_smem_bytes();
 
+// fgemm launch sequence shared by the entry points (ffgpu_host.cu).  ws is a
+// 256-byte aligned workspace of ws_bytes; max_grid > 0 caps the number of
+// persistent CTAs (and so the residue slots the workspace must hold); untimed
+// launches skip the optional profiling events.
+ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                       const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                       uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                       int* err, cudaStream_t s, int max_grid, bool untimed);
+size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);
+ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
+                        const void* B, int64_t ldb, const void* C, int64_t ldc);
+int sm_count(int dev);
+
 // Kernel timing (ffgpu_profile_*): brackets a launch with events on `s`.
 bool profiling_on();
 void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop);

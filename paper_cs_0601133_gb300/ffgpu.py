@@ -62,6 +62,7 @@ SIGNATURES = {
     "ffgpu_fgemm_plan": [_I64, _I64, _I64, _U32, ctypes.POINTER(PlanInfo)],
     "ffgpu_last_device_error": [_VP],
     "ffgpu_release_workspaces": [],
+    "ffgpu_fgemm_noalloc": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
 }
@@ -133,6 +134,13 @@ def fgemm(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, stream=None):
 def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
     """The raw C-ABI call on device pointers; returns the status code."""
     return lib().ffgpu_fgemm(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr)
+
+
+def fgemm_noalloc_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
+    """ffgpu_fgemm_noalloc on device pointers (scratch from the library's static
+    device array, no allocation); returns the status code."""
+    return lib().ffgpu_fgemm_noalloc(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc,
+                                     stream_ptr)
 
 
 def fgemm_workspace_size(m, n, k, p) -> int:
