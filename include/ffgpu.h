@@ -124,6 +124,24 @@ FFGPU_API ffgpu_status ffgpu_fgemm_noalloc(int64_t m, int64_t n, int64_t k, uint
                                            const uint32_t* B, int64_t ldb, uint32_t beta,
                                            uint32_t* C, int64_t ldc, void* stream);
 
+/*
+ * ftrsm (section 4, Algorithm 1: block recursive triangular solve with a
+ * matrix right-hand side), in place on B:
+ *     side 0 (left):  B <- alpha * T^{-1} * B,  T is m x m;
+ *     side 1 (right): B <- alpha * B * T^{-1},  T is n x n.
+ * uplo 0 = lower, 1 = upper triangle of T is used (the other is not read);
+ * diag 0 = non-unit, 1 = unit diagonal (diagonal entries are not read).
+ * T (ldt) and B (ldb) are row-major device arrays; B is m x n.
+ * Triangles of up to 64 rows are solved by substitution mod p; every other
+ * step is an fgemm update on the same stream.  A non-invertible diagonal entry
+ * (non-unit) cannot be detected before the kernels run: it is recorded on the
+ * device and ffgpu_last_device_error then returns FFGPU_ERR_INVALID (B is
+ * undefined).
+ */
+FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p,
+                                   uint32_t alpha, const uint32_t* T, int64_t ldt, uint32_t* B,
+                                   int64_t ldb, void* stream);
+
 /* Description of how ffgpu_fgemm computes a problem (for benchmarks and tests). */
 typedef struct {
     int32_t mode;         /* 1 = single modulus p (p <= 256); 2 = residue number system */
@@ -139,7 +157,8 @@ FFGPU_API ffgpu_status ffgpu_fgemm_plan(int64_t m, int64_t n, int64_t k, uint32_
 
 /*
  * Synchronizes `stream`, returns FFGPU_ERR_TIMEOUT if a kernel launched on it
- * since the last call recorded a failure (and clears the record), FFGPU_OK
+ * since the last call recorded a timed-out wait, FFGPU_ERR_INVALID if an
+ * ftrsm met a non-invertible diagonal entry (and clears the record), FFGPU_OK
  * otherwise, or FFGPU_ERR_CUDA if the stream reports a CUDA error.
  */
 FFGPU_API ffgpu_status ffgpu_last_device_error(void* stream);

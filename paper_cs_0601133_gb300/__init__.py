@@ -4,9 +4,9 @@ The computation lives in the CUDA library ``libffgpu.so`` (C ABI declared in
 ``include/ffgpu.h``); ``ffgpu`` is its thin Python binding.  ``workloads``
 draws the seeded synthetic inputs.
 """
-from .ffgpu import (FFGPUError, fgemm, fgemm_noalloc_ptr, fgemm_plan, fgemm_ptr, fgemm_workspace_size, fgemm_ws,
+from .ffgpu import (FFGPUError, fgemm, fgemm_noalloc_ptr, fgemm_plan, fgemm_ptr, fgemm_workspace_size, fgemm_ws, ftrsm,
                     profile_enable, profile_read,
                     last_device_error, lib, release_workspaces, status_string, version)
 
-__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws",
+__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm",
            "last_device_error", "lib", "release_workspaces", "status_string", "version"]

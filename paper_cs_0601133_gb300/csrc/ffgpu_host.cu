@@ -402,6 +402,23 @@ ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t a
                      s, 0, false);
 }
 
+ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                         const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* stream) {
+    if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
+    if (side < 0 || side > 1 || uplo < 0 || uplo > 1 || diag < 0 || diag > 1) return FFGPU_ERR_INVALID;
+    if (m < 0 || n < 0 || m > INT32_MAX / 2 || n > INT32_MAX / 2) return FFGPU_ERR_INVALID;
+    if (m == 0 || n == 0) return FFGPU_OK;
+    const int64_t nt = side == 0 ? m : n;
+    if (!T || !B || ldt < nt || ldb < n) return FFGPU_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    Pool* pool = nullptr;
+    ffgpu_status st = pool_get(s, ftrsm_ws_bytes(side, m, n, p, sm_count(dev)), &pool);
+    if (st != FFGPU_OK) return st;
+    return ftrsm_run(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, pool->ptr, pool->bytes, pool->err, s);
+}
+
 ffgpu_status ffgpu_last_device_error(void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -421,7 +438,7 @@ ffgpu_status ffgpu_last_device_error(void* stream) {
     if (cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFGPU_ERR_CUDA;
     if (v != 0) {
         cudaMemset(err, 0, sizeof(int));
-        return FFGPU_ERR_TIMEOUT;
+        return v == kDevSingular ? FFGPU_ERR_INVALID : FFGPU_ERR_TIMEOUT;
     }
     return FFGPU_OK;
 }

@@ -32,6 +32,7 @@ enum DevErr : int {
     kDevTimeoutMma = 2,
     kDevTimeoutEpilogue = 3,
     kDevTimeoutDrain = 4,
+    kDevSingular = 5,  // a non-unit triangular solve met a non-invertible diagonal entry
 };
 
 struct RnsPlan {
@@ -105,6 +106,12 @@ size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);
 ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
                         const void* B, int64_t ldb, const void* C, int64_t ldc);
 int sm_count(int dev);
+
+// ftrsm (ftrsm.cu)
+size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);
+ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                       const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* ws, size_t ws_bytes,
+                       int* err, cudaStream_t s);
 
 // Kernel timing (ffgpu_profile_*): brackets a launch with events on `s`.
 bool profiling_on();

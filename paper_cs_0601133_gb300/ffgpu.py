@@ -63,6 +63,7 @@ SIGNATURES = {
     "ffgpu_last_device_error": [_VP],
     "ffgpu_release_workspaces": [],
     "ffgpu_fgemm_noalloc": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
+    "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
 }
@@ -134,6 +135,19 @@ def fgemm(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, stream=None):
 def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
     """The raw C-ABI call on device pointers; returns the status code."""
     return lib().ffgpu_fgemm(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr)
+
+
+def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: str = "U", stream=None):
+    """In place: B <- alpha*T^{-1}*B (side "L") or alpha*B*T^{-1} (side "R") mod p. Returns B."""
+    m, n = B.shape
+    nt = m if side == "L" else n
+    if tuple(T.shape) != (nt, nt):
+        raise ValueError("T must be %d x %d" % (nt, nt))
+    t, ldt = _mat(T, "T")
+    b, ldb = _mat(B, "B")
+    check(lib().ffgpu_ftrsm(0 if side == "L" else 1, 0 if uplo == "L" else 1, 1 if diag == "U" else 0,
+                            m, n, p, alpha % 2**32, t, ldt, b, ldb, _stream_ptr(stream)), "ffgpu_ftrsm")
+    return B
 
 
 def fgemm_noalloc_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:

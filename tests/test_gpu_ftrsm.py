@@ -1,0 +1,83 @@
+"""GPU parity of ffgpu_ftrsm (section 4, Algorithm 1) against the CPU oracle.
+
+Sizes cross the 64-row leaf several times (recursion depth 2-4), with ragged
+splits, both sides, both triangles, unit and non-unit diagonals, and alpha.
+A larger solve is checked by its residual op(T) X = alpha B with Freivalds'
+test (random vectors, exact matrix-vector products on the CPU)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_cs_0601133_gb300 as ff
+from paper_cs_0601133_gb300 import workloads as W
+from tests.gpu_util import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def solve(T, B, p, alpha, side, uplo, diag):
+    dT, dB = to_dev(T), to_dev(B)
+    ff.ftrsm(dT, dB, p, alpha, side, uplo, diag)
+    torch.cuda.synchronize()
+    rc = ff.last_device_error()
+    return from_dev(dB), rc
+
+
+@pytest.mark.parametrize("p", [3, 251, 65521, 2147483647])
+@pytest.mark.parametrize("side", ["L", "R"])
+@pytest.mark.parametrize("uplo", ["L", "U"])
+@pytest.mark.parametrize("diag", ["U", "N"])
+def test_against_oracle(p, side, uplo, diag):
+    rng = W.rng_for("ftrsm", p, ord(side), ord(uplo), ord(diag))
+    m, n = (300, 170) if side == "L" else (170, 300)
+    nt = m if side == "L" else n
+    T = W.triangular(rng, nt, p, uplo, diag == "U")
+    # words above p and garbage in the unused triangle must not matter
+    T = T + (W.uniform_words(rng, T.shape) % 7).astype(np.uint32) * (np.triu(np.ones_like(T), 1) if uplo == "L" else np.tril(np.ones_like(T), -1))
+    B = W.uniform_words(rng, (m, n))
+    alpha = int(rng.integers(1, p))
+    got, rc = solve(T, B, p, alpha, side, uplo, diag)
+    assert rc == 0
+    expect = oracle.ftrsm(T, B, p, alpha, side, uplo, diag)
+    assert np.array_equal(got, expect)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (64, 3), (65, 1), (129, 200), (1000, 5)])
+def test_shapes_left_lower_unit(shape):
+    p = 65521
+    m, n = shape
+    rng = W.rng_for("ftrsm", 7, m, n)
+    T = W.unit_lower_triangular(rng, m, p)
+    B = W.uniform_residues(rng, (m, n), p)
+    got, rc = solve(T, B, p, 1, "L", "L", "U")
+    assert rc == 0
+    assert np.array_equal(got, oracle.ftrsm(T, B, p, 1, "L", "L", "U"))
+
+
+def test_large_residual_freivalds():
+    p = 2147483647
+    m, n = 2048, 1536
+    rng = W.rng_for("ftrsm", 8)
+    T = W.unit_lower_triangular(rng, m, p)
+    B = W.uniform_residues(rng, (m, n), p)
+    alpha = 12345
+    X, rc = solve(T, B, p, alpha, "L", "L", "U")
+    assert rc == 0
+    for t in range(2):
+        x = W.uniform_residues(np.random.default_rng(t), (n,), p)
+        lhs = oracle.matvec(T, oracle.matvec(X, x, p), p)
+        rhs = (alpha * oracle.matvec(B, x, p).astype(object) % p).astype(np.uint32)
+        assert np.array_equal(lhs, rhs)
+
+
+def test_singular_diagonal_is_reported():
+    p = 65521
+    rng = W.rng_for("ftrsm", 9)
+    T = W.triangular(rng, 100, p, "L", False)
+    T[37, 37] = 0
+    B = W.uniform_residues(rng, (100, 10), p)
+    _, rc = solve(T, B, p, 1, "L", "L", "N")
+    assert rc == -1  # FFGPU_ERR_INVALID
+    # the record is cleared once read
+    assert ff.last_device_error() == 0
