@@ -142,6 +142,31 @@ FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int6
                                    uint32_t alpha, const uint32_t* T, int64_t ldt, uint32_t* B,
                                    int64_t ldb, void* stream);
 
+/* One independent fgemm of a batch: C <- (alpha*A*B + beta*C) mod p. */
+typedef struct {
+    int64_t m, n, k;
+    uint32_t p, alpha, beta;
+    const uint32_t* A;
+    int64_t lda;
+    const uint32_t* B;
+    int64_t ldb;
+    uint32_t* C;
+    int64_t ldc;
+} ffgpu_fgemm_desc;
+
+/*
+ * Batched fgemm: `count` independent problems of any shapes and moduli
+ * (descs is a HOST array; every matrix is device memory).  Problems are
+ * grouped by padded inner length; for each group of at most a few GiB of
+ * channel planes the library enqueues one grouped conversion of all A's, one
+ * of all B's, and ONE persistent tensor-core launch whose CTAs walk a job
+ * list (instance, tile, modulus) balanced by cost (longest first).  Results
+ * equal ffgpu_fgemm on each descriptor.  No C may overlap an A, a B or
+ * another C of the batch.  Invalid descriptors fail the whole call before
+ * anything is enqueued.
+ */
+FFGPU_API ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream);
+
 /* Description of how ffgpu_fgemm computes a problem (for benchmarks and tests). */
 typedef struct {
     int32_t mode;         /* 1 = single modulus p (p <= 256); 2 = residue number system */

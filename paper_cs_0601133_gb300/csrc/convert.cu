@@ -68,42 +68,56 @@ __device__ __forceinline__ void residues8(const ConvertParams& cp, const uint32_
     }
 }
 
-// X: rows x cols (ldx) -> planes[c][rows][colsp], colsp a multiple of 64.
-__global__ void __launch_bounds__(256) convert_rows_kernel(const uint32_t* __restrict__ X, long long ldx,
-                                                           int rows, int cols, int colsp,
-                                                           const __grid_constant__ ConvertParams cp,
-                                                           uint4* __restrict__ planes, int vec_ok) {
+// Rows [r_begin, r_end) of X (rows x cols, ldx) -> planes[c][r][colsp]; rows
+// at or past `rows` (padding up to a tile multiple) are written as zeros.
+__device__ __forceinline__ void convert_rows_range(const uint32_t* __restrict__ X, long long ldx, int rows,
+                                                   int cols, int colsp, int r_begin, int r_end,
+                                                   const ConvertParams& cp, uint4* __restrict__ planes,
+                                                   size_t plane16, int vec_ok, long long tid,
+                                                   long long nthreads) {
     const long long gpr = colsp / 8;
-    const long long total = (long long)rows * gpr;
-    const size_t plane16 = (size_t)rows * colsp / 8;  // plane size in 16-byte units
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-         g += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(g / gpr);
-        const int c0 = (int)(g - (long long)r * gpr) * 8;
-        const uint32_t* src = X + (long long)r * ldx + c0;
+    const long long total = (long long)(r_end - r_begin) * gpr;
+    for (long long g = tid; g < total; g += nthreads) {
+        const int r = r_begin + (int)(g / gpr);
+        const int c0 = (int)(g % gpr) * 8;
         uint32_t x[8];
-        if (vec_ok && c0 + 8 <= cols) {
-            const uint4 a = __ldg(reinterpret_cast<const uint4*>(src));
-            const uint4 b = __ldg(reinterpret_cast<const uint4*>(src) + 1);
-            x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
-            x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
-        } else {
+        if (r >= rows) {
 #pragma unroll
-            for (int e = 0; e < 8; ++e) x[e] = (c0 + e < cols) ? __ldg(src + e) : 0u;
+            for (int e = 0; e < 8; ++e) x[e] = 0u;
+        } else {
+            const uint32_t* src = X + (long long)r * ldx + c0;
+            if (vec_ok && c0 + 8 <= cols) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(src));
+                const uint4 b = __ldg(reinterpret_cast<const uint4*>(src) + 1);
+                x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+                x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = (c0 + e < cols) ? __ldg(src + e) : 0u;
+            }
         }
         residues8(cp, x, planes + ((size_t)r * colsp + c0) / 8, plane16);
     }
 }
 
-// X: rows x cols (ldx), rows = inner dimension -> planes[c][cols][rowsp]
-// (transposed, so the inner dimension is contiguous), through a 64 x 64 tile.
-__global__ void __launch_bounds__(256) convert_transpose_kernel(const uint32_t* __restrict__ X,
-                                                                long long ldx, int rows, int cols,
-                                                                int rowsp,
-                                                                const __grid_constant__ ConvertParams cp,
-                                                                uint4* __restrict__ planes) {
-    __shared__ uint32_t tile[64][65];
-    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+// X: rows x cols (ldx) -> planes[c][rows][colsp], colsp a multiple of 64.
+__global__ void __launch_bounds__(256) convert_rows_kernel(const uint32_t* __restrict__ X, long long ldx,
+                                                           int rows, int cols, int colsp,
+                                                           const __grid_constant__ ConvertParams cp,
+                                                           uint4* __restrict__ planes, int vec_ok) {
+    const size_t plane16 = (size_t)rows * colsp / 8;  // plane size in 16-byte units
+    convert_rows_range(X, ldx, rows, cols, colsp, 0, rows, cp, planes, plane16, vec_ok,
+                       blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+// One 64 x 64 tile (rows [r0, r0+64) = inner dimension, columns [c0, c0+64))
+// of X (rows x cols, ldx) -> planes[c][col][rowsp] (transposed so that the
+// inner dimension is contiguous).  Columns at or past `cols` up to cols_pad are
+// written as zeros.
+__device__ __forceinline__ void convert_transpose_tile(const uint32_t* __restrict__ X, long long ldx, int rows,
+                                                       int cols, int cols_pad, int rowsp, int r0, int c0,
+                                                       const ConvertParams& cp, uint4* __restrict__ planes,
+                                                       size_t plane16, uint32_t (*tile)[65]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int idx = threadIdx.x + 256 * i;
@@ -112,18 +126,67 @@ __global__ void __launch_bounds__(256) convert_transpose_kernel(const uint32_t* 
         tile[rr][cc] = (gr < rows && gc < cols) ? __ldg(X + (long long)gr * ldx + gc) : 0u;
     }
     __syncthreads();
-    const size_t plane16 = (size_t)cols * rowsp / 8;
 #pragma unroll 1
     for (int it = 0; it < 2; ++it) {
         const int w = threadIdx.x + 256 * it;
         const int cl = w >> 3, g = w & 7;
         const int gc = c0 + cl;
-        if (gc >= cols) continue;
+        if (gc >= cols_pad) continue;
         uint32_t x[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) x[e] = tile[g * 8 + e][cl];
         residues8(cp, x, planes + ((size_t)gc * rowsp + r0 + g * 8) / 8, plane16);
     }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) convert_transpose_kernel(const uint32_t* __restrict__ X,
+                                                                long long ldx, int rows, int cols,
+                                                                int rowsp,
+                                                                const __grid_constant__ ConvertParams cp,
+                                                                uint4* __restrict__ planes) {
+    __shared__ uint32_t tile[64][65];
+    convert_transpose_tile(X, ldx, rows, cols, cols, rowsp, blockIdx.y * 64, blockIdx.x * 64, cp, planes,
+                           (size_t)cols * rowsp / 8, tile);
+}
+
+// Grouped conversions: block b serves the instance i with
+// block_begin[i] <= b < block_begin[i+1] (binary search).
+__device__ __forceinline__ int find_job(const long long* __restrict__ block_begin, int njobs, long long b) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (block_begin[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+constexpr int kRowsPerGroupedBlock = 16;
+
+__global__ void __launch_bounds__(256) convert_rows_grouped_kernel(const ConvJob* __restrict__ jobs,
+                                                                   const long long* __restrict__ block_begin,
+                                                                   int njobs) {
+    const int i = find_job(block_begin, njobs, blockIdx.x);
+    const ConvJob& J = jobs[i];
+    const int lb = (int)(blockIdx.x - block_begin[i]);
+    const int r_begin = lb * kRowsPerGroupedBlock;
+    const int r_end = min(J.rows_pad, r_begin + kRowsPerGroupedBlock);
+    convert_rows_range(J.X, J.ldx, J.rows, J.cols, J.kp, r_begin, r_end, J.cp, J.dst, J.plane16, J.vec_ok,
+                       threadIdx.x, blockDim.x);
+}
+
+__global__ void __launch_bounds__(256) convert_transpose_grouped_kernel(const ConvJob* __restrict__ jobs,
+                                                                        const long long* __restrict__ block_begin,
+                                                                        int njobs) {
+    __shared__ uint32_t tile[64][65];
+    const int i = find_job(block_begin, njobs, blockIdx.x);
+    const ConvJob& J = jobs[i];
+    const int lb = (int)(blockIdx.x - block_begin[i]);
+    const int tiles_c = (J.rows_pad + 63) / 64;   // output rows (columns of B), padded
+    const int tc = lb % tiles_c, tk = lb / tiles_c;
+    // B: rows = k (inner dimension), cols = n, rows_pad = n padded, kp = k padded
+    convert_transpose_tile(J.X, J.ldx, J.rows, J.cols, J.rows_pad, J.kp, tk * 64, tc * 64, J.cp, J.dst,
+                           J.plane16, tile);
 }
 
 __global__ void __launch_bounds__(256) scale_kernel(uint32_t* C, long long ldc, int m, int n, uint32_t p,
@@ -162,6 +225,25 @@ cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows,
     dim3 grid((cols + 63) / 64, rowsp / 64);
     convert_transpose_kernel<<<grid, 256, 0, s>>>(X, ldx, rows, cols, rowsp, cp,
                                                    static_cast<uint4*>(planes));
+    return cudaGetLastError();
+}
+
+long long convert_rows_grouped_blocks(int rows_pad) {
+    return (rows_pad + kRowsPerGroupedBlock - 1) / kRowsPerGroupedBlock;
+}
+long long convert_transpose_grouped_blocks(int cols_pad, int kp) { return (long long)((cols_pad + 63) / 64) * (kp / 64); }
+
+cudaError_t launch_convert_rows_grouped(const ConvJob* jobs, const long long* block_begin, int njobs,
+                                        long long nblocks, cudaStream_t s) {
+    if (njobs == 0 || nblocks == 0) return cudaSuccess;
+    convert_rows_grouped_kernel<<<(unsigned)nblocks, 256, 0, s>>>(jobs, block_begin, njobs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_transpose_grouped(const ConvJob* jobs, const long long* block_begin, int njobs,
+                                             long long nblocks, cudaStream_t s) {
+    if (njobs == 0 || nblocks == 0) return cudaSuccess;
+    convert_transpose_grouped_kernel<<<(unsigned)nblocks, 256, 0, s>>>(jobs, block_begin, njobs);
     return cudaGetLastError();
 }
 

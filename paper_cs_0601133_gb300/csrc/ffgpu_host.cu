@@ -45,7 +45,7 @@ static int64_t k_capacity(uint32_t p, int c) {
 }
 
 // Plan for one launch summing `k` products.
-static void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
+void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
     std::memset(&pl, 0, sizeof(pl));
     pl.p = p;
     if (p <= 256) {
@@ -72,7 +72,7 @@ static void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
     pl.negMp = (uint32_t)((p - (uint32_t)(M % p)) % p);
 }
 
-static unsigned long long barrett_mu(uint32_t p) { return ~0ull / p; }
+unsigned long long barrett_mu(uint32_t p) { return ~0ull / p; }
 
 // ---------------------------------------------------------------------------
 // Kernel timing
@@ -96,12 +96,6 @@ void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop) {
 // Devices, pools, descriptors
 // ---------------------------------------------------------------------------
 
-struct Pool {
-    void* ptr = nullptr;
-    size_t bytes = 0;
-    int* err = nullptr;
-};
-
 static std::mutex g_mu;
 static std::map<std::pair<int, cudaStream_t>, Pool> g_pools;
 static std::map<int, int> g_sms;
@@ -118,7 +112,7 @@ int sm_count(int dev) {
 
 // Pool of (current device, stream); allocates the error word on first use and
 // grows the buffer to `need` bytes with stream-ordered allocation.
-static ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
+ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
@@ -148,7 +142,7 @@ static ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
     return FFGPU_OK;
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -164,7 +158,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // 3-D map over channel planes [nch][rows][kp] of bf16, box 64 x box_rows x 1,
 // 128-byte swizzle (the layout the tensor-core descriptors expect).
-static bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uint64_t nch,
+bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uint64_t nch,
                           uint32_t box_rows) {
     auto enc = tensor_map_encoder();
     if (!enc) return false;
@@ -208,6 +202,32 @@ ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void*
     if (!C || ldc < n) return FFGPU_ERR_INVALID;
     if (k > 0 && (!A || !B || lda < k || ldb < n)) return FFGPU_ERR_INVALID;
     return FFGPU_OK;
+}
+
+// Kernel view of one instance (everything but the grouped-launch placement).
+void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, uint32_t al, uint32_t be,
+               uint32_t* C, int64_t ldc) {
+    std::memset(&I, 0, sizeof(I));
+    I.m = (int)m;
+    I.n = (int)n;
+    I.ksteps = (int)(kp / kTileK);
+    I.nch = pl.nch;
+    I.direct = pl.mode == 1;
+    I.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
+    I.p = pl.p;
+    I.alpha = al;
+    I.beta = be;
+    I.negMp = pl.negMp;
+    I.mu = barrett_mu(pl.p);
+    I.C = C;
+    I.ldc = ldc;
+    for (int c = 0; c < pl.nch; ++c) {
+        I.modf[c] = (float)pl.mod[c];
+        I.inv_m[c] = 1.0f / (float)pl.mod[c];
+        I.modu[c] = pl.mod[c];
+        I.u[c] = pl.u[c];
+        I.W[c] = pl.W[c];
+    }
 }
 
 // Workspace bytes for the largest launch of a problem.
@@ -280,31 +300,12 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
 
         RnsGemmParams P;
         std::memset(&P, 0, sizeof(P));
-        P.m = (int)m;
-        P.n = (int)n;
-        P.ksteps = (int)(kp / kTileK);
+        fill_inst(P.inst, m, n, kp, pl, al, be, C, ldc);
         P.tiles_m = (int)((m + kTileM - 1) / kTileM);
         P.tiles_n = (int)((n + kTileN - 1) / kTileN);
         P.num_tiles = P.tiles_m * P.tiles_n;
-        P.nch = pl.nch;
-        P.direct = pl.mode == 1;
-        P.p = p;
-        P.alpha = al;
-        P.beta = be;
-        P.mu = mu;
-        P.C = C;
-        P.ldc = ldc;
-        P.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
         P.slots = wsb + L.slots;
         P.err = err;
-        for (int c = 0; c < pl.nch; ++c) {
-            P.modf[c] = (float)pl.mod[c];
-            P.inv_m[c] = 1.0f / (float)pl.mod[c];
-            P.modu[c] = pl.mod[c];
-            P.u[c] = pl.u[c];
-            P.W[c] = pl.W[c];
-        }
-        P.negMp = pl.negMp;
         if (launch("rns_gemm", [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess)
             return FFGPU_ERR_CUDA;
         be = 1;  // later slices accumulate onto the partial result
@@ -400,6 +401,17 @@ ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t a
     if (st != FFGPU_OK) return st;
     return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, pool->ptr, pool->bytes, pool->err,
                      s, 0, false);
+}
+
+ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream) {
+    if (count < 0 || (count > 0 && !descs)) return FFGPU_ERR_INVALID;
+    for (int64_t i = 0; i < count; ++i) {
+        const ffgpu_fgemm_desc& d = descs[i];
+        const ffgpu_status st = check_args(d.m, d.n, d.k, d.p, d.A, d.lda, d.B, d.ldb, d.C, d.ldc);
+        if (st != FFGPU_OK) return st;
+    }
+    if (count == 0) return FFGPU_OK;
+    return batched_run(count, descs, static_cast<cudaStream_t>(stream));
 }
 
 ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,

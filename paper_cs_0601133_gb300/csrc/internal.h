@@ -46,27 +46,49 @@ struct RnsPlan {
     int64_t k_slice;               // largest inner length one launch may sum
 };
 
-// Parameters of the tensor-core kernel (passed by value).
-struct RnsGemmParams {
+// One fgemm instance as the tensor-core kernel sees it.
+struct InstInfo {
     int m, n;
-    int ksteps;          // kp / 64
-    int tiles_m, tiles_n, num_tiles;
+    int ksteps;                    // kp / 64
     int nch;
     int direct;
+    int vec_ok;                    // 16-byte vector access to C is legal
     uint32_t p;
     uint32_t alpha, beta;          // reduced mod p
+    uint32_t negMp;
     unsigned long long mu;         // floor((2^64-1)/p)
     uint32_t* C;
     long long ldc;
-    int vec_ok;                    // 16-byte vector access to C is legal
-    unsigned char* slots;          // per-CTA residue slots
-    int* err;                      // device error word
+    int bucket;                    // grouped launch: tensor-map pair of this instance
+    int rowA, rowB;                // grouped launch: first plane row of this instance
     float modf[kMaxChannels];
     float inv_m[kMaxChannels];
     uint32_t modu[kMaxChannels];
     uint32_t u[kMaxChannels];
     uint32_t W[kMaxChannels];
-    uint32_t negMp;
+};
+
+// Parameters of the single-instance tensor-core kernel (passed by value).
+struct RnsGemmParams {
+    InstInfo inst;
+    int tiles_m, tiles_n, num_tiles;
+    unsigned char* slots;          // per-CTA residue slots
+    int* err;                      // device error word
+};
+
+// Grouped launch: jobs (instance, tile, channel), listed per CTA.  c holds
+// the channel in bits 0-7 and the tile's residue slot (0/1) in bit 8.
+struct GroupJob {
+    int inst, tm, tn, c;
+};
+constexpr int kGroupedSlots = 2;
+struct GroupGemmParams {
+    const InstInfo* insts;
+    const GroupJob* jobs;
+    const int* cta_begin;          // jobs of CTA b: [cta_begin[b], cta_begin[b+1])
+    const CUtensorMap* maps;       // 2 per k-bucket: A planes, B planes (64-byte aligned)
+    unsigned char* slots;
+    int* err;
 };
 
 constexpr size_t kSlotBytesPerCta = size_t(kMaxChannels) * kTileM * kTileN;
@@ -83,7 +105,29 @@ struct ConvertParams {
     unsigned long long magic[kMaxChannels];  // ceil(2^40 / m_c)
 };
 
+// One matrix of a grouped conversion.  A (rows mode): X is rows (= m) x cols
+// (= k), written to dst[c][r][kp] for r < rows_pad (m padded).  B (transposed
+// mode): X is rows (= k) x cols (= n), written to dst[c][j][kp] for
+// j < rows_pad (n padded).  Padding is written as zeros.
+struct ConvJob {
+    const uint32_t* X;
+    long long ldx;
+    int rows, cols;
+    int rows_pad;
+    int kp;
+    int vec_ok;
+    uint4* dst;            // this matrix's first plane row (channel 0) in its bucket pool
+    size_t plane16;        // channel stride of the bucket pool, in 16-byte units
+    ConvertParams cp;
+};
+
 // host launchers (implemented in the .cu files)
+long long convert_rows_grouped_blocks(int rows_pad);
+long long convert_transpose_grouped_blocks(int cols_pad, int kp);
+cudaError_t launch_convert_rows_grouped(const ConvJob* jobs, const long long* block_begin, int njobs,
+                                        long long nblocks, cudaStream_t s);
+cudaError_t launch_convert_transpose_grouped(const ConvJob* jobs, const long long* block_begin, int njobs,
+                                             long long nblocks, cudaStream_t s);
 cudaError_t launch_convert_rows(const uint32_t* X, long long ldx, int rows, int cols, int colsp,
                                 const ConvertParams& cp, void* planes, cudaStream_t s);
 cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows, int cols, int rowsp,
@@ -92,7 +136,16 @@ cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, u
                          unsigned long long mu, cudaStream_t s);
 cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s);
+cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s);
 size_t rns_gemm_smem_bytes();
+
+// Workspace pool of one (device, stream).
+struct Pool {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    int* err = nullptr;
+};
+ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out);
 
 // fgemm launch sequence shared by the entry points (ffgpu_host.cu).  ws is a
 // 256-byte aligned workspace of ws_bytes; max_grid > 0 caps the number of
@@ -106,6 +159,15 @@ size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);
 ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
                         const void* B, int64_t ldb, const void* C, int64_t ldc);
 int sm_count(int dev);
+
+void make_plan(uint32_t p, int64_t k, RnsPlan& pl);
+unsigned long long barrett_mu(uint32_t p);
+void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, uint32_t al, uint32_t be,
+               uint32_t* C, int64_t ldc);
+bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uint64_t nch, uint32_t box_rows);
+
+// batched fgemm (batched.cu)
+ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* d, cudaStream_t s);
 
 // ftrsm (ftrsm.cu)
 size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);

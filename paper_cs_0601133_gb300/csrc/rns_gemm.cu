@@ -24,6 +24,11 @@
 // Two 256-column accumulators: the jobs (tile, channel) of a CTA are paired and
 // their chunks interleaved, so one accumulator is reduced while the tensor
 // cores fill the other.
+//
+// Two schedulers share the kernel body: one instance with tiles dealt
+// round-robin to the persistent CTAs, and a grouped launch where the host lists
+// each CTA's jobs (instance, tile, channel) over many instances of different
+// shapes and moduli (section 8 of the build's scope: one launch for a batch).
 #include "devutil.cuh"
 #include "internal.h"
 
@@ -75,15 +80,15 @@ __device__ __forceinline__ uint32_t f32_residue(float x, float m, float inv_m, i
 // With M = prod m_c and b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c)
 // - q M where q = round(sum_c b_c / m_c), valid because the plan guarantees
 // |X| <= M/4 (the fraction is within 1/4 of an integer, far above f32 error).
-__device__ __forceinline__ void crt4(const RnsGemmParams& P, const unsigned char* slot, int g,
+__device__ __forceinline__ void crt4(const InstInfo& I, const unsigned char* slot, int g,
                                      uint32_t (&X)[4]) {
     unsigned long long S[4] = {0ull, 0ull, 0ull, 0ull};
     float G[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = 0; c < P.nch; ++c) {
+    for (int c = 0; c < I.nch; ++c) {
         const uint32_t w =
             *reinterpret_cast<const uint32_t*>(slot + size_t(c) * kTileM * kTileN + 4 * g);
-        const uint32_t uc = P.u[c], mc = P.modu[c], Wc = P.W[c];
-        const float im = P.inv_m[c];
+        const uint32_t uc = I.u[c], mc = I.modu[c], Wc = I.W[c];
+        const float im = I.inv_m[c];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int t = (int)(((w >> (8 * e)) & 255u) * uc);
@@ -98,59 +103,124 @@ __device__ __forceinline__ void crt4(const RnsGemmParams& P, const unsigned char
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const unsigned long long q = (unsigned long long)rintf(G[e]);
-        X[e] = mod_u64(S[e] + q * P.negMp, P.p, P.mu);
+        X[e] = mod_u64(S[e] + q * I.negMp, I.p, I.mu);
     }
 }
 
-__device__ __forceinline__ void combine_tile_row(const RnsGemmParams& P, int tm, int tn,
-                                                 int row_local, int half,
-                                                 const unsigned char* slot_row) {
+__device__ __forceinline__ void combine_tile_row(const InstInfo& I, int tm, int tn, int row_local,
+                                                 int half, const unsigned char* slot_row) {
     const int row = tm * kTileM + row_local;
-    if (row >= P.m) return;
-    uint32_t* crow = P.C + (long long)row * P.ldc;
+    if (row >= I.m) return;
+    uint32_t* crow = I.C + (long long)row * I.ldc;
     const int col0 = tn * kTileN + half * 128;
     for (int g = 0; g < 32; ++g) {
         const int col = col0 + 4 * g;
-        if (col >= P.n) break;
+        if (col >= I.n) break;
         uint32_t X[4];
-        if (P.direct) {
+        if (I.direct) {
             const uint32_t w = *reinterpret_cast<const uint32_t*>(slot_row + 4 * g);
 #pragma unroll
             for (int e = 0; e < 4; ++e) X[e] = (w >> (8 * e)) & 255u;
         } else {
-            crt4(P, slot_row, g, X);
+            crt4(I, slot_row, g, X);
         }
-        const bool full4 = col + 3 < P.n;
+        const bool full4 = col + 3 < I.n;
         uint32_t old[4] = {0u, 0u, 0u, 0u};
-        if (P.beta != 0) {
-            if (full4 && P.vec_ok) {
+        if (I.beta != 0) {
+            if (full4 && I.vec_ok) {
                 const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
                 old[0] = v.x; old[1] = v.y; old[2] = v.z; old[3] = v.w;
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (col + e < P.n) old[e] = crow[col + e];
+                    if (col + e < I.n) old[e] = crow[col + e];
             }
         }
         uint32_t out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            out[e] = mod_u64((unsigned long long)P.alpha * X[e] + (unsigned long long)P.beta * old[e],
-                             P.p, P.mu);
-        if (full4 && P.vec_ok) {
+            out[e] = mod_u64((unsigned long long)I.alpha * X[e] + (unsigned long long)I.beta * old[e],
+                             I.p, I.mu);
+        if (full4 && I.vec_ok) {
             *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
         } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                if (col + e < P.n) crow[col + e] = out[e];
+                if (col + e < I.n) crow[col + e] = out[e];
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
-    rns_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
-                    const __grid_constant__ CUtensorMap mapB,
-                    const __grid_constant__ RnsGemmParams P) {
+// A job of the kernel: one channel of one output tile of one instance.
+struct Job {
+    const InstInfo* inst;
+    const CUtensorMap* mapA;
+    const CUtensorMap* mapB;
+    int tm, tn, c;
+    int H;        // chunks of kChunkSteps k-steps
+    int slot;     // residue slot of the job's tile
+};
+
+// Single instance, tiles dealt round-robin to the CTAs, channels in order.
+struct SingleSched {
+    const RnsGemmParams& P;
+    const CUtensorMap* mA;
+    const CUtensorMap* mB;
+    int my_tiles;
+    __device__ SingleSched(const RnsGemmParams& p, const CUtensorMap* a, const CUtensorMap* b)
+        : P(p), mA(a), mB(b) {
+        my_tiles = (int)blockIdx.x < P.num_tiles
+                       ? (P.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                       : 0;
+    }
+    __device__ int num_jobs() const { return my_tiles * P.inst.nch; }
+    __device__ void job(int j, Job& d) const {
+        const int nch = P.inst.nch;
+        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
+        d.inst = &P.inst;
+        d.mapA = mA;
+        d.mapB = mB;
+        d.c = j % nch;
+        tile_coords(t, P.tiles_m, P.tiles_n, d.tm, d.tn);
+        d.H = (P.inst.ksteps + kChunkSteps - 1) / kChunkSteps;
+        d.slot = 0;  // every job has the same length: a tile's reconstruction precedes the next tile's residues
+    }
+    static constexpr int kSlots = 1;
+    __device__ unsigned char* slots() const { return P.slots; }
+    __device__ int* err() const { return P.err; }
+};
+
+// Grouped launch: the host lists every CTA's jobs.
+struct GroupSched {
+    const GroupGemmParams& P;
+    int begin, count;
+    __device__ GroupSched(const GroupGemmParams& p, const CUtensorMap*, const CUtensorMap*) : P(p) {
+        begin = P.cta_begin[blockIdx.x];
+        count = P.cta_begin[blockIdx.x + 1] - begin;
+    }
+    __device__ int num_jobs() const { return count; }
+    __device__ void job(int j, Job& d) const {
+        const GroupJob g = P.jobs[begin + j];
+        const InstInfo* I = P.insts + g.inst;
+        d.inst = I;
+        d.mapA = P.maps + 2 * I->bucket;
+        d.mapB = P.maps + 2 * I->bucket + 1;
+        d.tm = g.tm;
+        d.tn = g.tn;
+        d.c = g.c & 0xFF;
+        d.H = (I->ksteps + kChunkSteps - 1) / kChunkSteps;
+        // jobs of different lengths: a pair may finish the next tile's first
+        // channel before this tile's reconstruction, so tiles alternate slots
+        d.slot = (g.c >> 8) & 1;
+    }
+    static constexpr int kSlots = 2;
+    __device__ unsigned char* slots() const { return P.slots; }
+    __device__ int* err() const { return P.err; }
+};
+
+template <class Sched, class Params>
+__device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUtensorMap* mapB,
+                                              const Params& P) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -168,11 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
-    const int my_tiles =
-        (int)blockIdx.x < P.num_tiles ? (P.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int nch = P.nch;
-    const int J = my_tiles * nch;                       // jobs (tile, channel) of this CTA
-    const int H = (P.ksteps + kChunkSteps - 1) / kChunkSteps;  // chunks per job
+    const Sched S(P, mapA, mapB);
+    const int J = S.num_jobs();   // jobs (tile, channel) of this CTA
+    int* err = S.err();
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -188,9 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_fence_init();
     }
     if (warp == 1) tc_alloc(tmem_slot, kTmemCols);
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&mapA);
-        tma_prefetch_desc(&mapB);
+    if (warp == 0 && lane == 0 && mapA != nullptr) {
+        tma_prefetch_desc(mapA);
+        tma_prefetch_desc(mapB);
     }
     tc_fence_before();
     __syncthreads();
@@ -206,25 +274,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                for (int h = 0; h < H && ok; ++h) {
-                    const int k0 = h * kChunkSteps;
-                    const int steps = min(kChunkSteps, P.ksteps - k0);
+                Job jb[2];
+                S.job(2 * pi, jb[0]);
+                if (nj > 1) S.job(2 * pi + 1, jb[1]);
+                const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
+                for (int h = 0; h < Hmax && ok; ++h) {
                     for (int s = 0; s < nj && ok; ++s) {
-                        const int j = 2 * pi + s;
-                        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
-                        const int c = j % nch;
-                        int tm, tn;
-                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
+                        const Job& d = jb[s];
+                        if (h >= d.H) continue;
+                        const int k0 = h * kChunkSteps;
+                        const int steps = min(kChunkSteps, d.inst->ksteps - k0);
+                        const int rowA = d.inst->rowA + d.tm * kTileM;
+                        const int rowB = d.inst->rowB + d.tn * kTileN;
                         for (int st = 0; st < steps; ++st) {
-                            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, P.err,
-                                           kDevTimeoutProducer)) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err, kDevTimeoutProducer)) {
                                 ok = false;
                                 break;
                             }
                             mbar_arrive_expect_tx(&full[stage], kStageBytes);
                             const int kx = (k0 + st) * kTileK;
-                            tma_load_3d(sA + stage * kABytes, &mapA, kx, tm * kTileM, c, &full[stage]);
-                            tma_load_3d(sB + stage * kBBytes, &mapB, kx, tn * kTileN, c, &full[stage]);
+                            tma_load_3d(sA + stage * kABytes, d.mapA, kx, rowA, d.c, &full[stage]);
+                            tma_load_3d(sB + stage * kBBytes, d.mapB, kx, rowB, d.c, &full[stage]);
                             issued |= 1u << stage;
                             last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
                             if (++stage == kStages) {
@@ -237,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // every issued copy must have landed before shared memory is released
             for (int s2 = 0; s2 < kStages; ++s2)
-                if (issued & (1u << s2)) mbar_drain_wait(&full[s2], (last_parity >> s2) & 1u, P.err);
+                if (issued & (1u << s2)) mbar_drain_wait(&full[s2], (last_parity >> s2) & 1u, err);
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
@@ -250,17 +320,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool any = false;
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                for (int h = 0; h < H && ok; ++h) {
-                    const int steps = min(kChunkSteps, P.ksteps - h * kChunkSteps);
+                Job jb[2];
+                S.job(2 * pi, jb[0]);
+                if (nj > 1) S.job(2 * pi + 1, jb[1]);
+                const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
+                for (int h = 0; h < Hmax && ok; ++h) {
                     for (int s = 0; s < nj && ok; ++s) {
-                        if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, P.err, kDevTimeoutMma)) {
+                        const Job& d = jb[s];
+                        if (h >= d.H) continue;
+                        const int steps = min(kChunkSteps, d.inst->ksteps - h * kChunkSteps);
+                        if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t d = tmem + (uint32_t)(s * kTileN);
+                        const uint32_t dt = tmem + (uint32_t)(s * kTileN);
                         for (int st = 0; st < steps; ++st) {
-                            if (!mbar_wait(&full[stage], phase, abort_flag, P.err, kDevTimeoutMma)) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, err, kDevTimeoutMma)) {
                                 ok = false;
                                 break;
                             }
@@ -270,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                             for (int kk = 0; kk < kTileK / 16; ++kk) {
                                 const uint32_t acc = (h > 0 || st > 0 || kk > 0) ? 1u : 0u;
-                                tc_mma_bf16(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
+                                tc_mma_bf16(dt, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
                                             idesc, acc);
                             }
                             tc_commit(&empty[stage]);
@@ -289,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // all issued MMAs must complete before tensor memory is released
             if (any) {
                 tc_commit(drain);
-                mbar_drain_wait(drain, 0u, P.err);
+                mbar_drain_wait(drain, 0u, err);
             }
         }
     } else {
@@ -297,18 +373,25 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_local = q * 32 + lane;
-        unsigned char* slot_base = P.slots + size_t(blockIdx.x) * kSlotBytesPerCta;
-        unsigned char* slot_row = slot_base + row_local * kTileN + half * 128;
+        unsigned char* slot_base = S.slots() + size_t(blockIdx.x) * Sched::kSlots * kSlotBytesPerCta;
+        const size_t row_off = size_t(row_local) * kTileN + half * 128;
         uint32_t accp[2] = {0u, 0u};
         bool ok = true;
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
-            for (int h = 0; h < H && ok; ++h) {
-                const bool last_chunk = (h == H - 1);
+            Job jb[2];
+            S.job(2 * pi, jb[0]);
+            if (nj > 1) S.job(2 * pi + 1, jb[1]);
+            const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
+            for (int h = 0; h < Hmax && ok; ++h) {
                 for (int s = 0; s < nj; ++s) {
-                    const int j = 2 * pi + s;
-                    const int c = j % nch;
-                    if (!mbar_wait(&acc_full[s], accp[s], abort_flag, P.err, kDevTimeoutEpilogue)) {
+                    const Job& d = jb[s];
+                    if (h >= d.H) continue;
+                    const bool last_chunk = (h == d.H - 1);
+                    const InstInfo& I = *d.inst;
+                    const int c = d.c;
+                    unsigned char* slot_row = slot_base + size_t(d.slot) * kSlotBytesPerCta + row_off;
+                    if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
                         ok = false;
                         break;
                     }
@@ -316,8 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t tbase =
                         tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
-                    const float mf = P.modf[c], im = P.inv_m[c];
-                    const int mi = (int)P.modu[c];
+                    const float mf = I.modf[c], im = I.inv_m[c];
+                    const int mi = (int)I.modu[c];
                     if (!last_chunk) {
 #pragma unroll 1
                         for (int cc = 0; cc < 4; ++cc) {
@@ -358,12 +441,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&acc_empty[s]);
-                    if (last_chunk && c == nch - 1) {
-                        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
-                        int tm, tn;
-                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
-                        combine_tile_row(P, tm, tn, row_local, half, slot_row);
-                    }
+                    if (last_chunk && c == I.nch - 1) combine_tile_row(I, d.tm, d.tn, row_local, half, slot_row);
                 }
             }
         }
@@ -375,6 +453,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         tc_dealloc(tmem, kTmemCols);
     }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                    const __grid_constant__ CUtensorMap mapB,
+                    const __grid_constant__ RnsGemmParams P) {
+    rns_gemm_body<SingleSched>(&mapA, &mapB, P);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_grouped_kernel(const __grid_constant__ GroupGemmParams P) {
+    rns_gemm_body<GroupSched>(nullptr, nullptr, P);
 }
 
 }  // namespace
@@ -392,6 +482,19 @@ cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
         attr_set = true;
     }
     rns_gemm_kernel<<<grid, kThreads, kSmemBytes, s>>>(mapA, mapB, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rns_gemm_grouped_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    rns_gemm_grouped_kernel<<<grid, kThreads, kSmemBytes, s>>>(prm);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,13 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class FgemmDesc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("p", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -63,6 +70,7 @@ SIGNATURES = {
     "ffgpu_last_device_error": [_VP],
     "ffgpu_release_workspaces": [],
     "ffgpu_fgemm_noalloc": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
+    "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
@@ -135,6 +143,24 @@ def fgemm(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, stream=None):
 def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
     """The raw C-ABI call on device pointers; returns the status code."""
     return lib().ffgpu_fgemm(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr)
+
+
+def fgemm_batched(problems, stream=None):
+    """problems: iterable of (A, B, C, p, alpha, beta) with CUDA tensors; every
+    C <- (alpha*A@B + beta*C) mod p, all in one batched call. Returns the Cs."""
+    probs = list(problems)
+    arr = (FgemmDesc * max(1, len(probs)))()
+    for i, (A, B, C, p, alpha, beta) in enumerate(probs):
+        m, k = A.shape
+        n = B.shape[1]
+        if B.shape[0] != k or tuple(C.shape) != (m, n):
+            raise ValueError("problem %d: shapes %s %s %s do not match" % (i, tuple(A.shape), tuple(B.shape), tuple(C.shape)))
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        c, ldc = _mat(C, "C")
+        arr[i] = FgemmDesc(m, n, k, p, alpha % 2**32, beta % 2**32, a, lda, b, ldb, c, ldc)
+    check(lib().ffgpu_fgemm_batched(len(probs), arr, _stream_ptr(stream)), "ffgpu_fgemm_batched")
+    return [pr[2] for pr in probs]
 
 
 def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: str = "U", stream=None):

@@ -1,0 +1,114 @@
+"""GPU parity of ffgpu_fgemm_batched (one grouped conversion per operand and one
+persistent grouped tensor-core launch per wave) against the CPU oracle, and
+against ffgpu_fgemm on the same descriptors.
+
+Workloads follow the multi-modular configuration: uneven shapes drawn
+log-uniform in [16, 1024], integer matrices with entries in [-2^20, 2^20]
+reduced modulo several of the 32 primes just below 2^31, plus mixed moduli of
+every size class in one batch."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_cs_0601133_gb300 as ff
+from paper_cs_0601133_gb300 import workloads as W
+from tests.gpu_util import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run_batch(problems):
+    dev = [(to_dev(A), to_dev(B), to_dev(C), p, al, be) for (A, B, C, p, al, be) in problems]
+    ff.fgemm_batched(dev)
+    torch.cuda.synchronize()
+    assert ff.last_device_error() == 0
+    return [from_dev(d[2]) for d in dev]
+
+
+def test_mixed_shapes_and_moduli():
+    rng = W.rng_for("multimodular", 100)
+    primes = [2, 3, 251, 256, 257, 65521, 1000003, 8388593, 2147483647]
+    problems = []
+    for i in range(40):
+        m, n, k = (int(v) for v in W.log_uniform_int(rng, 16, 600, 3))
+        p = primes[i % len(primes)]
+        A = W.uniform_words(rng, (m, k))
+        B = W.uniform_words(rng, (k, n))
+        C = W.uniform_words(rng, (m, n))
+        problems.append((A, B, C, p, int(rng.integers(0, 2**32)), int(rng.integers(0, 2**32))))
+    outs = run_batch(problems)
+    for (A, B, C, p, al, be), got in zip(problems, outs):
+        assert np.array_equal(got, oracle.fgemm(A, B, p, al, be, C)), (A.shape, B.shape, p)
+
+
+def test_multimodular_instances_subset():
+    shapes, primes = W.multimodular_instances(count=24, nprimes=32)
+    use = primes[::8]  # 4 of the 32 primes
+    problems = []
+    for i, (m, n, k) in enumerate(shapes):
+        Ai, Bi = W.multimodular_integers(i, int(m), int(n), int(k))
+        for p in use:
+            A = W.reduce_signed(Ai, p)
+            B = W.reduce_signed(Bi, p)
+            C = np.zeros((int(m), int(n)), np.uint32)
+            problems.append((A, B, C, p, 1, 0))
+    outs = run_batch(problems)
+    for (A, B, C, p, al, be), got in zip(problems, outs):
+        assert np.array_equal(got, oracle.fgemm(A, B, p, al, be, C))
+
+
+def test_batched_equals_single_calls():
+    rng = W.rng_for("multimodular", 101)
+    problems = []
+    for i in range(12):
+        m, n, k = (int(v) for v in W.log_uniform_int(rng, 16, 1024, 3))
+        p = W.primes_below(2**31, 32)[i]
+        problems.append((W.uniform_residues(rng, (m, k), p), W.uniform_residues(rng, (k, n), p),
+                         W.uniform_residues(rng, (m, n), p), p, 3, 4))
+    outs = run_batch(problems)
+    for (A, B, C, p, al, be), got in zip(problems, outs):
+        dC = to_dev(C)
+        ff.fgemm(to_dev(A), to_dev(B), p, al, be, dC)
+        torch.cuda.synchronize()
+        assert np.array_equal(got, from_dev(dC))
+
+
+def test_degenerate_members():
+    p = 65521
+    rng = W.rng_for("multimodular", 102)
+    C0 = W.uniform_words(rng, (20, 30))
+    A1 = W.uniform_residues(rng, (40, 50), p)
+    B1 = W.uniform_residues(rng, (50, 60), p)
+    C1 = W.uniform_residues(rng, (40, 60), p)
+    problems = [
+        (np.zeros((20, 0), np.uint32), np.zeros((0, 30), np.uint32), C0, p, 5, 7),   # k = 0: beta*C
+        (A1, B1, C1, p, 2, 3),
+    ]
+    outs = run_batch(problems)
+    assert np.array_equal(outs[0], (7 * C0.astype(np.uint64) % p).astype(np.uint32))
+    assert np.array_equal(outs[1], oracle.fgemm(A1, B1, p, 2, 3, C1))
+    assert ff.fgemm_batched([]) == []
+
+
+def test_many_instances_several_waves_sampled():
+    """2048 fgemms (256 integer instances x 8 primes): more channel planes than
+    one wave holds.  32 products checked entirely, every other one on 16
+    sampled entries."""
+    shapes, primes = W.multimodular_instances(count=256, nprimes=32)
+    use = primes[::4]
+    problems = []
+    for i, (m, n, k) in enumerate(shapes):
+        Ai, Bi = W.multimodular_integers(i, int(m), int(n), int(k))
+        for p in use:
+            problems.append((W.reduce_signed(Ai, p), W.reduce_signed(Bi, p),
+                             np.zeros((int(m), int(n)), np.uint32), p, 1, 0))
+    outs = run_batch(problems)
+    rng = np.random.default_rng(0)
+    for idx, ((A, B, C, p, al, be), got) in enumerate(zip(problems, outs)):
+        if idx % 64 == 0:
+            assert np.array_equal(got, oracle.fgemm(A, B, p, al, be, C))
+        else:
+            r = rng.integers(0, A.shape[0], 16)
+            c = rng.integers(0, B.shape[1], 16)
+            assert np.array_equal(got[r, c], oracle.fgemm_entries(A, B, p, al, be, C, r, c))
