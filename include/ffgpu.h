@@ -75,6 +75,34 @@ FFGPU_API ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, 
                          const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                          uint32_t beta, uint32_t* C, int64_t ldc, void* stream);
 
+/*
+ * fgemm with a choice of arithmetic path and Winograd levels (section 3.2):
+ *   path FFGPU_PATH_RNS  (0): the residue-number-system tensor-core path (default);
+ *   path FFGPU_PATH_FP64 (1): residues carried in doubles on the FP64 DMMA unit,
+ *                             reduced after every 16 products (eq. 2, gamma = 53),
+ *                             p < 2^25;
+ *   path FFGPU_PATH_FP32 (2): residues carried in floats (SIMT FFMA), reduced
+ *                             before the sum can reach 2^24 (eq. 1-2, gamma = 24),
+ *                             p <= 256.
+ * winograd_levels (0..8): recursive levels of Winograd's variant with the
+ * schedule of Table 2 (additions mod p, products by the chosen path) and
+ * dynamic peeling of odd dimensions.  Every combination gives the same exact
+ * result as ffgpu_fgemm.  p outside a path's range: FFGPU_ERR_UNSUPPORTED_P.
+ */
+typedef struct {
+    int32_t path;
+    int32_t winograd_levels;
+    int32_t reserved[6];   /* must be zero */
+} ffgpu_options;
+#define FFGPU_PATH_RNS 0
+#define FFGPU_PATH_FP64 1
+#define FFGPU_PATH_FP32 2
+
+FFGPU_API ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                                      const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                                      uint32_t beta, uint32_t* C, int64_t ldc, const ffgpu_options* opt,
+                                      void* stream);
+
 /* Bytes of device workspace ffgpu_fgemm_ws needs for this problem. */
 FFGPU_API ffgpu_status ffgpu_fgemm_workspace_size(int64_t m, int64_t n, int64_t k, uint32_t p,
                                         size_t* bytes);

@@ -403,6 +403,21 @@ ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t a
                      s, 0, false);
 }
 
+ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
+                            int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
+                            const ffgpu_options* opt, void* stream) {
+    ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
+    if (st != FFGPU_OK || m == 0 || n == 0) return st;
+    const int path = opt ? opt->path : 0, levels = opt ? opt->winograd_levels : 0;
+    if (opt)
+        for (int i = 0; i < 6; ++i)
+            if (opt->reserved[i] != 0) return FFGPU_ERR_INVALID;
+    if (path == 0 && levels == 0)
+        return ffgpu_fgemm(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, stream);
+    return fgemm_ex_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, path, levels,
+                        static_cast<cudaStream_t>(stream));
+}
+
 ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream) {
     if (count < 0 || (count > 0 && !descs)) return FFGPU_ERR_INVALID;
     for (int64_t i = 0; i < count; ++i) {

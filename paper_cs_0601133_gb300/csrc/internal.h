@@ -166,6 +166,11 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
                uint32_t* C, int64_t ldc);
 bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uint64_t nch, uint32_t box_rows);
 
+// paths and Winograd levels (winograd.cu)
+ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
+                          int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
+                          int path, int levels, cudaStream_t s);
+
 // batched fgemm (batched.cu)
 ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* d, cudaStream_t s);
 

@@ -1,0 +1,196 @@
+// Strassen-Winograd levels over residues mod p (section 3.2) on top of any
+// base path, and the ffgpu_fgemm_ex entry point.
+//
+// One level follows the schedule of Table 2 for C <- alpha*A*B + beta*C with
+// three temporaries X1 (m/2 x k/2), X2 (k/2 x n/2), X3 (m/2 x n/2): the eight
+// pre-additions S1..S4, T1..T4 and the post-additions are elementwise kernels
+// mod p (so, unlike the paper's delayed version, intermediate values do not
+// grow: Theorem 3.1's bound is not needed), the seven products recurse.
+// Row 16 is taken with A22 (P4 = alpha*A22*T4 - beta*C21), the reading under
+// which the schedule computes A*B.  Odd dimensions are handled by dynamic
+// peeling (appendix, "case of an arbitrary k"): the even top-left block by
+// Winograd, then a rank-1 update for an odd k, and the last column / last row
+// by the base path.
+#include <algorithm>
+
+#include "devutil.cuh"
+#include "internal.h"
+
+namespace ffgpu {
+
+uint32_t dmma_max_p();
+uint32_t sgemm_max_p();
+cudaError_t launch_dmma_fgemm(int m, int n, int k, const uint32_t* A, long long lda, const uint32_t* B,
+                              long long ldb, uint32_t* C, long long ldc, uint32_t p, uint32_t al, uint32_t be,
+                              cudaStream_t s);
+cudaError_t launch_sgemm_fgemm(int m, int n, int k, const uint32_t* A, long long lda, const uint32_t* B,
+                               long long ldb, uint32_t* C, long long ldc, uint32_t p, uint32_t al, uint32_t be,
+                               cudaStream_t s);
+
+namespace {
+
+// Z = (X + c*Y) mod p elementwise (any uint32 words; Z may alias X or Y).
+__global__ void __launch_bounds__(256) axpy_mod_kernel(int rows, int cols, const uint32_t* X, long long ldx,
+                                                       const uint32_t* Y, long long ldy, uint32_t* Z,
+                                                       long long ldz, uint32_t c, uint32_t p,
+                                                       unsigned long long mu) {
+    const long long total = (long long)rows * cols;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i / cols), q = (int)(i - (long long)r * cols);
+        const unsigned long long x = X[(long long)r * ldx + q], y = Y[(long long)r * ldy + q];
+        Z[(long long)r * ldz + q] = mod_u64(x + (unsigned long long)c * y, p, mu);
+    }
+}
+
+struct WinoCtx {
+    int path;
+    uint32_t p;
+    unsigned long long mu;
+    void* fg_ws;
+    size_t fg_ws_bytes;
+    unsigned char* tmp;
+    int* err;
+    cudaStream_t s;
+    int sms;
+    bool dry;            // size the workspace only
+    size_t need_fg;      // dry run: largest base-path workspace
+    size_t need_tmp;     // dry run: temporaries
+};
+
+ffgpu_status axpy(WinoCtx& c, int64_t rows, int64_t cols, const uint32_t* X, int64_t ldx, const uint32_t* Y,
+                  int64_t ldy, uint32_t* Z, int64_t ldz, uint32_t coef) {
+    if (c.dry || rows == 0 || cols == 0) return FFGPU_OK;
+    long long g = (rows * cols + 255) / 256;
+    g = std::min<long long>(std::max<long long>(g, 1), 152 * 16);
+    return timed_launch("winograd_axpy", c.s, [&] {
+               axpy_mod_kernel<<<(int)g, 256, 0, c.s>>>((int)rows, (int)cols, X, ldx, Y, ldy, Z, ldz, coef, c.p,
+                                                        c.mu);
+               return cudaGetLastError();
+           }) == cudaSuccess
+               ? FFGPU_OK
+               : FFGPU_ERR_CUDA;
+}
+
+ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, const uint32_t* A, int64_t lda,
+                  const uint32_t* B, int64_t ldb, uint32_t be, uint32_t* C, int64_t ldc) {
+    if (m == 0 || n == 0) return FFGPU_OK;
+    if (c.path == 0) {
+        if (c.dry) {
+            c.need_fg = std::max(c.need_fg, fgemm_ws_bytes(m, n, k, c.p, c.sms));
+            return FFGPU_OK;
+        }
+        return fgemm_run(m, n, k, c.p, al, A, lda, B, ldb, be, C, ldc, c.fg_ws, c.fg_ws_bytes, c.err, c.s, 0,
+                         false);
+    }
+    if (c.dry) return FFGPU_OK;
+    if (k == 0)
+        return timed_launch("scale_mod_p", c.s, [&] { return launch_scale(C, ldc, (int)m, (int)n, c.p, be, c.mu, c.s); }) ==
+                       cudaSuccess
+                   ? FFGPU_OK
+                   : FFGPU_ERR_CUDA;
+    cudaError_t e;
+    if (c.path == 1)
+        e = timed_launch("dmma_fgemm", c.s, [&] {
+            return launch_dmma_fgemm((int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, c.p, al, be, c.s);
+        });
+    else
+        e = timed_launch("sgemm_fgemm", c.s, [&] {
+            return launch_sgemm_fgemm((int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, c.p, al, be, c.s);
+        });
+    return e == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA;
+}
+
+#define FF_TRY(x)                             \
+    do {                                      \
+        const ffgpu_status st_ = (x);         \
+        if (st_ != FFGPU_OK) return st_;      \
+    } while (0)
+
+ffgpu_status wino(WinoCtx& c, int level, int64_t m, int64_t n, int64_t k, uint32_t al, const uint32_t* A,
+                  int64_t lda, const uint32_t* B, int64_t ldb, uint32_t be, uint32_t* C, int64_t ldc,
+                  size_t tmp_off) {
+    if (level == 0 || m < 2 || n < 2 || k < 2) return base(c, m, n, k, al, A, lda, B, ldb, be, C, ldc);
+    const int64_t m2 = m & ~int64_t(1), n2 = n & ~int64_t(1), k2 = k & ~int64_t(1);
+    if (m2 != m || n2 != n || k2 != k) {  // dynamic peeling
+        FF_TRY(wino(c, level, m2, n2, k2, al, A, lda, B, ldb, be, C, ldc, tmp_off));
+        if (k2 != k) FF_TRY(base(c, m2, n2, 1, al, A + k2, lda, B + k2 * ldb, ldb, 1, C, ldc));
+        if (n2 != n) FF_TRY(base(c, m2, 1, k, al, A, lda, B + n2, ldb, be, C + n2, ldc));
+        if (m2 != m) FF_TRY(base(c, 1, n, k, al, A + m2 * lda, lda, B, ldb, be, C + m2 * ldc, ldc));
+        return FFGPU_OK;
+    }
+    const int64_t h = m / 2, kh = k / 2, w = n / 2;
+    const uint32_t p = c.p, neg1 = p - 1;
+    const uint32_t *A11 = A, *A12 = A + kh, *A21 = A + h * lda, *A22 = A + h * lda + kh;
+    const uint32_t *B11 = B, *B12 = B + w, *B21 = B + kh * ldb, *B22 = B + kh * ldb + w;
+    uint32_t *C11 = C, *C12 = C + w, *C21 = C + h * ldc, *C22 = C + h * ldc + w;
+    // temporaries of this level, then the next level's
+    const size_t b1 = size_t(h) * kh * 4, b2 = size_t(kh) * w * 4, b3 = size_t(h) * w * 4;
+    const size_t o1 = tmp_off, o2 = o1 + ((b1 + 255) & ~size_t(255)), o3 = o2 + ((b2 + 255) & ~size_t(255));
+    const size_t next = o3 + ((b3 + 255) & ~size_t(255));
+    if (c.dry) c.need_tmp = std::max(c.need_tmp, next);
+    uint32_t* X1 = c.dry ? nullptr : reinterpret_cast<uint32_t*>(c.tmp + o1);
+    uint32_t* X2 = c.dry ? nullptr : reinterpret_cast<uint32_t*>(c.tmp + o2);
+    uint32_t* X3 = c.dry ? nullptr : reinterpret_cast<uint32_t*>(c.tmp + o3);
+    const int L = level - 1;
+    FF_TRY(axpy(c, h, kh, A21, lda, A22, lda, X1, kh, 1));                    // 1  S1 = A21 + A22
+    FF_TRY(axpy(c, kh, w, B12, ldb, B11, ldb, X2, w, neg1));                  // 2  T1 = B12 - B11
+    FF_TRY(wino(c, L, h, w, kh, al, X1, kh, X2, w, 0, X3, w, next));          // 3  P5 = a S1 T1
+    FF_TRY(axpy(c, h, w, X3, w, C22, ldc, C22, ldc, be));                     // 4  C22 = P5 + b C22
+    FF_TRY(axpy(c, h, w, X3, w, C12, ldc, C12, ldc, be));                     // 5  C12 = P5 + b C12
+    FF_TRY(axpy(c, h, kh, X1, kh, A11, lda, X1, kh, neg1));                   // 6  S2 = S1 - A11
+    FF_TRY(axpy(c, kh, w, B22, ldb, X2, w, X2, w, neg1));                     // 7  T2 = B22 - T1
+    FF_TRY(wino(c, L, h, w, kh, al, A11, lda, B11, ldb, 0, X3, w, next));     // 8  P1 = a A11 B11
+    FF_TRY(axpy(c, h, w, X3, w, C11, ldc, C11, ldc, be));                     // 9  C11 = P1 + b C11
+    FF_TRY(wino(c, L, h, w, kh, al, X1, kh, X2, w, 1, X3, w, next));          // 10 U2 = a S2 T2 + P1
+    FF_TRY(wino(c, L, h, w, kh, al, A12, lda, B21, ldb, 1, C11, ldc, next));  // 11 U1 = a A12 B21 + C11
+    FF_TRY(axpy(c, h, kh, A12, lda, X1, kh, X1, kh, neg1));                   // 12 S4 = A12 - S2
+    FF_TRY(axpy(c, kh, w, X2, w, B21, ldb, X2, w, neg1));                     // 13 T4 = T2 - B21
+    FF_TRY(wino(c, L, h, w, kh, al, X1, kh, B22, ldb, 1, C12, ldc, next));    // 14 C12 = a S4 B22 + C12
+    FF_TRY(axpy(c, h, w, X3, w, C12, ldc, C12, ldc, 1));                      // 15 U5 = U2 + C12
+    FF_TRY(wino(c, L, h, w, kh, al, A22, lda, X2, w, (p - be) % p, C21, ldc, next));  // 16 P4 = a A22 T4 - b C21
+    FF_TRY(axpy(c, h, kh, A11, lda, A21, lda, X1, kh, neg1));                 // 17 S3 = A11 - A21
+    FF_TRY(axpy(c, kh, w, B22, ldb, B12, ldb, X2, w, neg1));                  // 18 T3 = B22 - B12
+    FF_TRY(wino(c, L, h, w, kh, al, X1, kh, X2, w, 1, X3, w, next));          // 19 U3 = a S3 T3 + U2
+    FF_TRY(axpy(c, h, w, X3, w, C22, ldc, C22, ldc, 1));                      // 20 U7 = U3 + C22
+    FF_TRY(axpy(c, h, w, X3, w, C21, ldc, C21, ldc, neg1));                   // 21 U6 = U3 - C21
+    return FFGPU_OK;
+}
+
+}  // namespace
+
+ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
+                          int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
+                          int path, int levels, cudaStream_t s) {
+    if (path < 0 || path > 2 || levels < 0 || levels > 8) return FFGPU_ERR_INVALID;
+    if (path == 1 && p > dmma_max_p()) return FFGPU_ERR_UNSUPPORTED_P;
+    if (path == 2 && p > sgemm_max_p()) return FFGPU_ERR_UNSUPPORTED_P;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    WinoCtx c;
+    c.path = path;
+    c.p = p;
+    c.mu = ~0ull / p;
+    c.fg_ws = nullptr;
+    c.fg_ws_bytes = 0;
+    c.tmp = nullptr;
+    c.err = nullptr;
+    c.s = s;
+    c.sms = sm_count(dev);
+    c.dry = true;
+    c.need_fg = 0;
+    c.need_tmp = 0;
+    const uint32_t al = alpha % p, be = beta % p;
+    FF_TRY(wino(c, levels, m, n, k, al, A, lda, B, ldb, be, C, ldc, 0));
+    const size_t fg = (c.need_fg + 255) & ~size_t(255);
+    Pool* pool = nullptr;
+    FF_TRY(pool_get(s, fg + c.need_tmp, &pool));
+    c.dry = false;
+    c.fg_ws = pool->ptr;
+    c.fg_ws_bytes = fg;
+    c.tmp = static_cast<unsigned char*>(pool->ptr) + fg;
+    c.err = pool->err;
+    return wino(c, levels, m, n, k, al, A, lda, B, ldb, be, C, ldc, 0);
+}
+
+}  // namespace ffgpu

@@ -47,6 +47,14 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
+class Options(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("winograd_levels", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+PATHS = {"rns": 0, "fp64": 1, "fp32": 2}
+
+
 class FgemmDesc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("p", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
@@ -70,6 +78,8 @@ SIGNATURES = {
     "ffgpu_last_device_error": [_VP],
     "ffgpu_release_workspaces": [],
     "ffgpu_fgemm_noalloc": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
+    "ffgpu_fgemm_ex": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64,
+                       ctypes.POINTER(Options), _VP],
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_profile_enable": [_I32],
@@ -143,6 +153,25 @@ def fgemm(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, stream=None):
 def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:
     """The raw C-ABI call on device pointers; returns the status code."""
     return lib().ffgpu_fgemm(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr)
+
+
+def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "rns",
+             winograd_levels: int = 0, stream=None):
+    """fgemm through a chosen arithmetic path ("rns", "fp64", "fp32") with
+    `winograd_levels` levels of Winograd's variant. Returns C."""
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    if C is None:
+        C = torch.zeros((m, n), dtype=torch.uint32, device=A.device)
+        beta = 0
+    a, lda = _mat(A, "A")
+    b, ldb = _mat(B, "B")
+    c, ldc = _mat(C, "C")
+    opt = Options(PATHS[path], winograd_levels)
+    check(lib().ffgpu_fgemm_ex(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
+                               ctypes.byref(opt), _stream_ptr(stream)), "ffgpu_fgemm_ex")
+    return C
 
 
 def fgemm_batched(problems, stream=None):

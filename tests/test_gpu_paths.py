@@ -1,0 +1,67 @@
+"""GPU parity of the comparison paths (FP64 DMMA, FP32 SIMT) and of Winograd's
+levels (Table 2 schedule, dynamic peeling) on every path, against the oracle.
+
+This is the precision comparison: the same exact result must come out of the
+residue-number-system tensor-core path, the double-precision path and the
+single-precision path, each with 0, 1 or 2 levels of Winograd's algorithm."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_cs_0601133_gb300 as ff
+from paper_cs_0601133_gb300 import workloads as W
+from tests.gpu_util import from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("rns", 65521), ("rns", 2147483647), ("rns", 251), ("fp64", 251), ("fp64", 65521),
+         ("fp64", 1048573), ("fp64", 8388593), ("fp32", 251), ("fp32", 2)]
+
+
+def run(A, B, C, p, alpha, beta, path, levels):
+    dC = to_dev(C)
+    ff.fgemm_ex(to_dev(A), to_dev(B), p, alpha, beta, dC, path=path, winograd_levels=levels)
+    torch.cuda.synchronize()
+    assert ff.last_device_error() == 0
+    return from_dev(dC)
+
+
+@pytest.mark.parametrize("path,p", CASES)
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_paths_and_levels(path, p, levels):
+    rng = W.rng_for("precision", ord(path[2]), p, levels)
+    m, k, n = 301, 515, 263      # odd in every dimension: peeling at each level
+    A = W.uniform_words(rng, (m, k))
+    B = W.uniform_words(rng, (k, n))
+    C = W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta, path, levels)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
+
+
+@pytest.mark.parametrize("path,p", [("fp64", 8388593), ("fp32", 251), ("rns", 2147483647)])
+def test_adversarial_long_k(path, p):
+    # all entries p - 1: the delayed-reduction bound is reached on every path
+    m, n, k = 128, 192, 4096
+    A, B, C = W.adversarial_problem(m, n, k, p)
+    got = run(A, B, C, p, 1, 1, path, 1)
+    assert np.all(got == (k + (p - 1)) % p)
+
+
+def test_three_levels_even_sizes():
+    p = 65521
+    rng = W.rng_for("precision", 3)
+    A = W.uniform_residues(rng, (1024, 1024), p)
+    B = W.uniform_residues(rng, (1024, 1024), p)
+    C = W.uniform_residues(rng, (1024, 1024), p)
+    got = run(A, B, C, p, 7, 9, "rns", 3)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, 7, 9, C))
+
+
+def test_unsupported_modulus_for_a_path():
+    A = to_dev(np.zeros((4, 4), np.uint32))
+    with pytest.raises(ff.FFGPUError):
+        ff.fgemm_ex(A, A, 257, path="fp32")
+    with pytest.raises(ff.FFGPUError):
+        ff.fgemm_ex(A, A, 2**25 + 1, path="fp64")
