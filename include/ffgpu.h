@@ -195,6 +195,57 @@ typedef struct {
  */
 FFGPU_API ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream);
 
+/*
+ * Request server (continuous batching).  Not in the paper: the deployment of
+ * fgemm / ftrsm as a service.  Requests carry HOST operands (pinned memory
+ * for overlap) and a host output buffer.  An engine thread admits pending
+ * requests in arrival order whenever one of `streams` worker streams is free
+ * and a device arena of `budget_bytes` (allocated at creation, the HBM budget)
+ * holds the request's operands and workspace; the admitted request is copied
+ * in, computed and copied out on its stream, overlapping with the others.
+ * Each result equals what ffgpu_fgemm / ffgpu_ftrsm give alone.
+ */
+typedef struct ffgpu_server ffgpu_server;
+
+typedef struct {
+    int32_t kind;            /* 0 = fgemm, 1 = ftrsm */
+    int32_t side, uplo, diag;  /* ftrsm: as in ffgpu_ftrsm */
+    int64_t m, n, k;         /* fgemm: A m x k, B k x n;  ftrsm: B m x n (k unused) */
+    uint32_t p, alpha, beta;
+    const uint32_t* A;       /* host; fgemm A, ftrsm T */
+    int64_t lda;
+    const uint32_t* B;       /* host; fgemm B, ftrsm right-hand sides */
+    int64_t ldb;
+    const uint32_t* C_in;    /* host; fgemm C when beta != 0 (else may be NULL) */
+    int64_t ldc_in;
+    uint32_t* out;           /* host; result m x n (fgemm C, ftrsm X) */
+    int64_t ldo;
+    uint64_t tag;            /* caller's identifier, echoed in the completion */
+} ffgpu_request;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;          /* ffgpu_status of the request */
+    double t_submit_us, t_admit_us, t_done_us;  /* CLOCK_MONOTONIC, microseconds */
+} ffgpu_completion;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t pending, inflight, peak_inflight;
+    int64_t peak_bytes, budget_bytes, used_bytes;
+} ffgpu_server_stats;
+
+/* Creates a server on the current device (1..64 streams, budget >= 1 MiB). */
+FFGPU_API ffgpu_status ffgpu_server_create(int streams, size_t budget_bytes, ffgpu_server** out);
+/* Queues a request (returns at once).  FFGPU_ERR_BUDGET if it can never fit the budget. */
+FFGPU_API ffgpu_status ffgpu_server_submit(ffgpu_server* server, const ffgpu_request* req);
+/* Up to `cap` completions; waits up to wait_ms for the first one. */
+FFGPU_API ffgpu_status ffgpu_server_poll(ffgpu_server* server, ffgpu_completion* out, int cap, int* count,
+                                         int wait_ms);
+FFGPU_API ffgpu_status ffgpu_server_get_stats(ffgpu_server* server, ffgpu_server_stats* out);
+/* Drops pending requests, waits for admitted ones, frees everything. */
+FFGPU_API ffgpu_status ffgpu_server_destroy(ffgpu_server* server);
+
 /* Description of how ffgpu_fgemm computes a problem (for benchmarks and tests). */
 typedef struct {
     int32_t mode;         /* 1 = single modulus p (p <= 256); 2 = residue number system */

@@ -5,9 +5,9 @@ The computation lives in the CUDA library ``libffgpu.so`` (C ABI declared in
 draws the seeded synthetic inputs.
 """
 from .ffgpu import (FFGPUError, fgemm, fgemm_noalloc_ptr, fgemm_plan, fgemm_ptr, fgemm_workspace_size, fgemm_ws, ftrsm,
-                    fgemm_batched, fgemm_ex,
+                    fgemm_batched, fgemm_ex, Server,
                     profile_enable, profile_read,
                     last_device_error, lib, release_workspaces, status_string, version)
 
-__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex",
+__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex", "Server",
            "last_device_error", "lib", "release_workspaces", "status_string", "version"]

@@ -55,6 +55,27 @@ class Options(ctypes.Structure):
 PATHS = {"rns": 0, "fp64": 1, "fp32": 2}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("side", ctypes.c_int32), ("uplo", ctypes.c_int32),
+                ("diag", ctypes.c_int32), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("k", ctypes.c_int64), ("p", ctypes.c_uint32), ("alpha", ctypes.c_uint32),
+                ("beta", ctypes.c_uint32), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("C_in", ctypes.c_void_p),
+                ("ldc_in", ctypes.c_int64), ("out", ctypes.c_void_p), ("ldo", ctypes.c_int64),
+                ("tag", ctypes.c_uint64)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("t_submit_us", ctypes.c_double),
+                ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "admitted", "completed", "failed", "pending",
+                                               "inflight", "peak_inflight", "peak_bytes", "budget_bytes",
+                                               "used_bytes")]
+
+
 class FgemmDesc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("p", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
@@ -80,6 +101,11 @@ SIGNATURES = {
     "ffgpu_fgemm_noalloc": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _VP],
     "ffgpu_fgemm_ex": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64,
                        ctypes.POINTER(Options), _VP],
+    "ffgpu_server_create": [_I32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)],
+    "ffgpu_server_submit": [_VP, ctypes.POINTER(Request)],
+    "ffgpu_server_poll": [_VP, ctypes.POINTER(Completion), _I32, ctypes.POINTER(ctypes.c_int), _I32],
+    "ffgpu_server_get_stats": [_VP, ctypes.POINTER(ServerStats)],
+    "ffgpu_server_destroy": [_VP],
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_profile_enable": [_I32],
@@ -267,3 +293,53 @@ def profile_read() -> dict:
     cnt = ctypes.c_int(0)
     check(lib().ffgpu_profile_read(arr, cap, ctypes.byref(cnt)), "profile_read")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(cnt.value, cap))}
+
+
+class Server:
+    """Continuous-batching request server (ffgpu_server_*).  Operands are host
+    numpy arrays (uint32, C-contiguous rows; pinned memory overlaps better);
+    the caller keeps them alive until the request's completion is polled."""
+
+    def __init__(self, streams: int = 4, budget_bytes: int = 40 << 30):
+        h = ctypes.c_void_p()
+        check(lib().ffgpu_server_create(streams, budget_bytes, ctypes.byref(h)), "server_create")
+        self.h = h
+
+    def submit_fgemm(self, A, B, out, p, alpha=1, beta=0, C=None, tag=0):
+        r = Request(kind=0, m=A.shape[0], n=B.shape[1], k=A.shape[1], p=p, alpha=alpha % 2**32,
+                    beta=beta % 2**32, A=A.ctypes.data, lda=A.strides[0] // 4, B=B.ctypes.data,
+                    ldb=B.strides[0] // 4, C_in=C.ctypes.data if C is not None else None,
+                    ldc_in=(C.strides[0] // 4) if C is not None else 0, out=out.ctypes.data,
+                    ldo=out.strides[0] // 4, tag=tag)
+        check(lib().ffgpu_server_submit(self.h, ctypes.byref(r)), "server_submit")
+
+    def submit_ftrsm(self, T, B, out, p, alpha=1, side="L", uplo="L", diag="U", tag=0):
+        r = Request(kind=1, side=0 if side == "L" else 1, uplo=0 if uplo == "L" else 1,
+                    diag=1 if diag == "U" else 0, m=B.shape[0], n=B.shape[1], k=0, p=p,
+                    alpha=alpha % 2**32, beta=0, A=T.ctypes.data, lda=T.strides[0] // 4,
+                    B=B.ctypes.data, ldb=B.strides[0] // 4, out=out.ctypes.data,
+                    ldo=out.strides[0] // 4, tag=tag)
+        check(lib().ffgpu_server_submit(self.h, ctypes.byref(r)), "server_submit")
+
+    def poll(self, wait_ms: int = 0, cap: int = 256):
+        arr = (Completion * cap)()
+        cnt = ctypes.c_int(0)
+        check(lib().ffgpu_server_poll(self.h, arr, cap, ctypes.byref(cnt), wait_ms), "server_poll")
+        return [(int(arr[i].tag), int(arr[i].status), arr[i].t_submit_us, arr[i].t_admit_us, arr[i].t_done_us)
+                for i in range(cnt.value)]
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        check(lib().ffgpu_server_get_stats(self.h, ctypes.byref(st)), "server_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            check(lib().ffgpu_server_destroy(self.h), "server_destroy")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
