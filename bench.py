@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--p", type=int, default=2147483647)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve"], default="headline",
+                    help="headline: the driver's line; the others print one line per configuration point")
     return ap.parse_args()
 
 
@@ -270,6 +273,9 @@ def run_own(args):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world)
+    serve = None
+    if not args.no_serve and rank == 0:
+        serve = run_serve_small()
 
     if rank == 0:
         base = None
@@ -287,6 +293,7 @@ def run_own(args):
             "cpu_baseline": base,
             "e2e": e2e,
             "clocks": clocks,
+            "serve": serve,
             "gpu_launches": launches,
             "kernels_ms": {k: {"launches": v[0], "total_ms": v[1]} for k, v in kernels.items()},
         }
@@ -335,10 +342,102 @@ def run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world):
             "ms_per_step": ms / args.steps}
 
 
+def run_serve_small():
+    """Serving mix (Poisson arrivals of fgemm / unit-lower ftrsm, n log-uniform in
+    [64, 4096], p from the four sweep primes, 40 GB budget): 400 requests at 0.8 of
+    the unbatched capacity, continuous batching (4 streams) vs the unbatched FIFO."""
+    from paper_cs_0601133_gb300 import serving
+    r = serving.serve_benchmark(n_requests=400, fracs=(0.8,), streams=4)
+    run = r["runs"][0]
+    keep = ("throughput_rps", "p50_ms", "p99_ms", "mean_ms", "failed", "peak_inflight")
+    return {"requests": 400, "load": run["load"], "rate_rps": run["rate_rps"],
+            "capacity_rps_unbatched": r["capacity_rps_unbatched"],
+            "batched": {k: run["batched"][k] for k in keep},
+            "unbatched": {k: run["unbatched"][k] for k in keep}}
+
+
+def time_call(fn, torch, steps, warmup):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_sweep(args):
+    """Square fgemm sweep: n in {2048, 4096, 8192, 16384}, p the largest prime
+    below 2^8, 2^16, 2^23, 2^31; alpha, beta uniform; one line per point."""
+    import torch
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+    peak, _ = measured_peak()
+    for n in (2048, 4096, 8192, 16384):
+        for p in W.sweep_primes():
+            A, B, C, alpha, beta = W.square_problem(n, p)
+            dA = torch.from_numpy(A.view(np.int32)).cuda()
+            dB = torch.from_numpy(B.view(np.int32)).cuda()
+            dC = torch.from_numpy(C.view(np.int32)).cuda()
+            steps = max(3, min(50, int(4e12 / (2.0 * n ** 3))))
+            ms = time_call(lambda: ff.fgemm(dA, dB, p, alpha, beta, dC), torch, steps, 2)
+            plan = ff.fgemm_plan(n, n, n, p)
+            print(json.dumps({"workload": "sweep", "n": n, "p": p, "channels": plan["channels"],
+                              "ms": ms, "GOPS": 2.0 * n ** 3 / (ms / 1e3) / 1e9,
+                              "tensor_TFLOPs_incl_conversion": plan["mma_flops"] / (ms / 1e3) / 1e12,
+                              "frac_of_peak_incl_conversion": plan["mma_flops"] / (ms / 1e3) / 1e12 / peak}),
+                  flush=True)
+            del dA, dB, dC
+    return 0
+
+
+def run_precision(args):
+    """Precision comparison: m = n = 8192; the RNS tensor-core path, the FP64 DMMA
+    path and the FP32 path, each with 0/1/2 Winograd levels; inner dimension
+    8192 for all, up to 65536 for the RNS path."""
+    import torch
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+    n = 8192
+    cases = [("rns", 2147483647, (8192, 16384, 32768, 65536)), ("rns", 65521, (8192, 65536)),
+             ("fp64", 8388593, (8192,)), ("fp64", 65521, (8192,)), ("fp32", 251, (8192, 65536))]
+    for path, p, ks in cases:
+        for k in ks:
+            rng = W.rng_for("precision", 50, p, k)
+            dA = torch.from_numpy(W.uniform_residues(rng, (n, k), p).view(np.int32)).cuda()
+            dB = torch.from_numpy(W.uniform_residues(rng, (k, n), p).view(np.int32)).cuda()
+            dC = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+            for lv in (0, 1, 2):
+                steps = 1 if path == "fp64" else 3
+                ms = time_call(lambda: ff.fgemm_ex(dA, dB, p, 1, 0, dC, path=path, winograd_levels=lv),
+                               torch, steps, 1)
+                print(json.dumps({"workload": "precision", "path": path, "p": p, "m": n, "n": n, "k": k,
+                                  "winograd_levels": lv, "ms": ms,
+                                  "GOPS": 2.0 * n * n * k / (ms / 1e3) / 1e9}), flush=True)
+            del dA, dB, dC
+    return 0
+
+
+def run_serve_full(args):
+    from paper_cs_0601133_gb300 import serving
+    r = serving.serve_benchmark(n_requests=2000, fracs=(0.5, 0.8, 0.95), streams=4)
+    print(json.dumps({"workload": "serve", **r}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "precision":
+        return run_precision(args)
+    if args.workload == "serve":
+        return run_serve_full(args)
     return run_own(args)
 
 
