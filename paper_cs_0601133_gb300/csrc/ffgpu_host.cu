@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -48,7 +49,7 @@ static int64_t k_capacity(uint32_t p, int c) {
 void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
     std::memset(&pl, 0, sizeof(pl));
     pl.p = p;
-    if (p <= 256) {
+    if (p <= kDirectMaxP) {
         pl.mode = 1;
         pl.nch = 1;
         pl.mod[0] = p;
@@ -73,6 +74,23 @@ void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
 }
 
 unsigned long long barrett_mu(uint32_t p) { return ~0ull / p; }
+
+// Longest chunk of k-steps (64 products each) the f32 accumulator can sum
+// exactly: with R the largest residue magnitude, a reduced value |v| <= R + 1
+// plus 64*steps products of magnitude <= R^2 must stay below 2^24 (eq. 1 with
+// gamma = 24).  FFGPU_CHUNK_STEPS may ask for fewer (tuning).
+int chunk_steps_for(const RnsPlan& pl) {
+    uint32_t R = 0;
+    for (int c = 0; c < pl.nch; ++c) R = std::max(R, pl.mod[c] / 2);
+    const unsigned long long r2 = std::max<unsigned long long>(1ull, (unsigned long long)R * R);
+    unsigned long long steps = ((1ull << 24) - R - 2) / r2 / 64;
+    steps = std::min<unsigned long long>(std::max<unsigned long long>(steps, 1ull), 64ull);
+    if (const char* e = std::getenv("FFGPU_CHUNK_STEPS")) {
+        const long long want = std::atoll(e);
+        if (want >= 1 && (unsigned long long)want < steps) steps = (unsigned long long)want;
+    }
+    return (int)steps;
+}
 
 // ---------------------------------------------------------------------------
 // Kernel timing
@@ -211,6 +229,7 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
     I.m = (int)m;
     I.n = (int)n;
     I.ksteps = (int)(kp / kTileK);
+    I.chunk_steps = chunk_steps_for(pl);
     I.nch = pl.nch;
     I.direct = pl.mode == 1;
     I.vec_ok = ((reinterpret_cast<uintptr_t>(C) & 15) == 0) && (ldc % 4 == 0);
@@ -228,6 +247,16 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
         I.u[c] = pl.u[c];
         I.W[c] = pl.W[c];
     }
+}
+
+// Kernel choice: the CTA-pair kernel for problems with more than one 128-row
+// block (and a grid of at least one pair); FFGPU_KERNEL=single|pair forces one.
+bool use_pair_kernel(int64_t m, int grid) {
+    const char* f = std::getenv("FFGPU_KERNEL");
+    if (f && std::strcmp(f, "single") == 0) return false;
+    if (grid < 2 || rns_gemm_pair_max_clusters() < 1) return false;
+    if (f && std::strcmp(f, "pair") == 0) return true;
+    return m > kTileM;
 }
 
 // Workspace bytes for the largest launch of a problem.
@@ -293,21 +322,30 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
             }) != cudaSuccess)
             return FFGPU_ERR_CUDA;
 
+        // CTA-pair kernel (256 x 256 tiles) unless the problem has a single row
+        // block or the caller forces the one-CTA kernel
+        const bool pair = use_pair_kernel(m, grid);
         CUtensorMap mapA, mapB;
         if (!encode_planes(&mapA, wsb + L.planesA, kp, m, pl.nch, kTileM) ||
-            !encode_planes(&mapB, wsb + L.planesB, kp, n, pl.nch, kTileN))
+            !encode_planes(&mapB, wsb + L.planesB, kp, n, pl.nch, pair ? 128 : kTileN))
             return FFGPU_ERR_CUDA;
 
         RnsGemmParams P;
         std::memset(&P, 0, sizeof(P));
         fill_inst(P.inst, m, n, kp, pl, al, be, C, ldc);
-        P.tiles_m = (int)((m + kTileM - 1) / kTileM);
+        const int tile_rows = pair ? 2 * kTileM : kTileM;
+        P.tiles_m = (int)((m + tile_rows - 1) / tile_rows);
         P.tiles_n = (int)((n + kTileN - 1) / kTileN);
         P.num_tiles = P.tiles_m * P.tiles_n;
         P.slots = wsb + L.slots;
         P.err = err;
-        if (launch("rns_gemm", [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess)
+        if (pair) {
+            const int pgrid = 2 * std::max(1, std::min(std::min(P.num_tiles, grid / 2), rns_gemm_pair_max_clusters()));
+            if (launch("rns_gemm_pair", [&] { return launch_rns_gemm_pair(mapA, mapB, P, pgrid, s); }) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+        } else if (launch("rns_gemm", [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess) {
             return FFGPU_ERR_CUDA;
+        }
         be = 1;  // later slices accumulate onto the partial result
     }
     return FFGPU_OK;
@@ -360,7 +398,7 @@ ffgpu_status ffgpu_fgemm_plan(int64_t m, int64_t n, int64_t k, uint32_t p, ffgpu
     out->mode = pl.mode;
     out->channels = pl.nch;
     for (int c = 0; c < pl.nch; ++c) out->moduli[c] = pl.mod[c];
-    out->k_chunk = kChunkSteps * kTileK;
+    out->k_chunk = chunk_steps_for(pl) * kTileK;
     out->k_slices = (int32_t)((std::max<int64_t>(k, 1) + ks - 1) / ks);
     out->tile_m = kTileM;
     out->tile_n = kTileN;

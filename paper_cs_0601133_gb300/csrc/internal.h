@@ -10,19 +10,21 @@
 namespace ffgpu {
 
 // ---------------------------------------------------------------------------
-// Residue number system.  Moduli <= 256 whose balanced residues (|r| <= 128)
-// are exact bfloat16 values; pairwise coprime; in decreasing order so that the
-// first c of them give the largest product for c channels.
+// Residue number system.  Odd moduli <= 255 whose balanced residues
+// (|r| <= 127) are exact bfloat16 values; pairwise coprime; in decreasing
+// order so that the first c of them give the largest product for c channels.
 // ---------------------------------------------------------------------------
 constexpr int kMaxChannels = 12;
-constexpr uint32_t kModuli[kMaxChannels] = {256, 255, 253, 251, 247, 241,
-                                            239, 233, 229, 227, 223, 211};
+constexpr uint32_t kModuli[kMaxChannels] = {255, 253, 251, 247, 241, 239,
+                                            233, 229, 227, 223, 211, 199};
+// Largest modulus handled as a single channel (residues |x| <= 127).
+constexpr uint32_t kDirectMaxP = 255;
 
 // Tile of the tensor-core kernel.
 constexpr int kTileM = 128;
 constexpr int kTileN = 256;
 constexpr int kTileK = 64;       // one 128-byte swizzle row of bf16
-constexpr int kChunkSteps = 8;   // 8 x 64 = 512 products summed between in-place reductions
+constexpr int kChunkSteps = 16;  // default: 16 x 64 = 1024 products summed between in-place reductions
 constexpr int kStages = 4;
 
 // Error codes written to the device error word.
@@ -50,6 +52,7 @@ struct RnsPlan {
 struct InstInfo {
     int m, n;
     int ksteps;                    // kp / 64
+    int chunk_steps;               // k-steps summed between in-place reductions
     int nch;
     int direct;
     int vec_ok;                    // 16-byte vector access to C is legal
@@ -137,6 +140,10 @@ cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, u
 cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s);
 cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s);
+cudaError_t launch_rns_gemm_pair(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
+                                 int grid, cudaStream_t s);
+bool use_pair_kernel(int64_t m, int grid);
+int rns_gemm_pair_max_clusters();
 size_t rns_gemm_smem_bytes();
 
 // Workspace pool of one (device, stream).
@@ -161,6 +168,7 @@ ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void*
 int sm_count(int dev);
 
 void make_plan(uint32_t p, int64_t k, RnsPlan& pl);
+int chunk_steps_for(const RnsPlan& pl);
 unsigned long long barrett_mu(uint32_t p);
 void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, uint32_t al, uint32_t be,
                uint32_t* C, int64_t ldc);

@@ -7,11 +7,12 @@
 // For every 128 x 256 output tile and every channel c the kernel forms
 // S_c = sum_t A_c[i][t] * B_c[j][t] on the tcgen05 tensor cores with an f32
 // accumulator in tensor memory.  This is the delayed reduction of section
-// 2.1.2 restated for the accumulator: products of balanced residues are below
-// 2^14 in magnitude, so 512 of them plus a reduced value (|v| <= 129) stay
-// below 2^24, where every f32 sum of integers is exact (eq. 1 with gamma = 24).
-// After each 512-long chunk the epilogue warps reduce the accumulator mod m_c
-// in place (tcgen05.ld -> fma -> tcgen05.st) and the MMAs continue on top of it.
+// 2.1.2 restated for the accumulator: products of balanced residues are at
+// most 127^2 in magnitude, so 1024 of them plus a reduced value (|v| <= 128)
+// stay below 2^24, where every f32 sum of integers is exact (eq. 1 with
+// gamma = 24).  After each chunk of that length the epilogue warps reduce the
+// accumulator mod m_c in place (tcgen05.ld -> fma -> tcgen05.st) and the MMAs
+// continue on top of it.
 // After the last chunk each channel yields S mod m_c; the last channel of a
 // tile triggers the reconstruction of S mod p from all residues (Chinese
 // remainder theorem, the multi-modular route to p > 2^26 the paper lists as
@@ -182,7 +183,7 @@ struct SingleSched {
         d.mapB = mB;
         d.c = j % nch;
         tile_coords(t, P.tiles_m, P.tiles_n, d.tm, d.tn);
-        d.H = (P.inst.ksteps + kChunkSteps - 1) / kChunkSteps;
+        d.H = (P.inst.ksteps + P.inst.chunk_steps - 1) / P.inst.chunk_steps;
         d.slot = 0;  // every job has the same length: a tile's reconstruction precedes the next tile's residues
     }
     static constexpr int kSlots = 1;
@@ -208,7 +209,7 @@ struct GroupSched {
         d.tm = g.tm;
         d.tn = g.tn;
         d.c = g.c & 0xFF;
-        d.H = (I->ksteps + kChunkSteps - 1) / kChunkSteps;
+        d.H = (I->ksteps + I->chunk_steps - 1) / I->chunk_steps;
         // jobs of different lengths: a pair may finish the next tile's first
         // channel before this tile's reconstruction, so tiles alternate slots
         d.slot = (g.c >> 8) & 1;
@@ -282,8 +283,9 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     for (int s = 0; s < nj && ok; ++s) {
                         const Job& d = jb[s];
                         if (h >= d.H) continue;
-                        const int k0 = h * kChunkSteps;
-                        const int steps = min(kChunkSteps, d.inst->ksteps - k0);
+                        const int cs = d.inst->chunk_steps;
+                        const int k0 = h * cs;
+                        const int steps = min(cs, d.inst->ksteps - k0);
                         const int rowA = d.inst->rowA + d.tm * kTileM;
                         const int rowB = d.inst->rowB + d.tn * kTileN;
                         for (int st = 0; st < steps; ++st) {
@@ -328,7 +330,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     for (int s = 0; s < nj && ok; ++s) {
                         const Job& d = jb[s];
                         if (h >= d.H) continue;
-                        const int steps = min(kChunkSteps, d.inst->ksteps - h * kChunkSteps);
+                        const int cs = d.inst->chunk_steps;
+                        const int steps = min(cs, d.inst->ksteps - h * cs);
                         if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
                             ok = false;
                             break;
@@ -467,9 +470,324 @@ __global__ void __launch_bounds__(kThreads, 1)
     rns_gemm_body<GroupSched>(nullptr, nullptr, P);
 }
 
+
+// ---------------------------------------------------------------------------
+// CTA-pair variant (cluster of 2, tcgen05 cta_group::2): one 256 x 256 output
+// tile per pair; CTA rank r owns rows [128 r, 128 r + 128) of the tile and
+// column half r of the B tile.  The leader (rank 0) issues M=256 N=256 MMAs
+// that read A from each CTA's own shared memory and B from both halves, and
+// writes each CTA's 128 x 256 accumulator into that CTA's tensor memory.  Per
+// SM and stage the TMA moves 32 KB instead of 48 KB for the same tensor work,
+// which leaves room for 6 stages.  Barriers: both CTAs' copies complete on the
+// leader's full[] barrier; the leader's commits arrive on empty[] and
+// acc_full[] in both CTAs; both CTAs' epilogues arrive on the leader's
+// acc_empty[] (16 warps).
+constexpr int kPStages = 6;
+constexpr uint32_t kPABytes = 128 * kTileK * 2;
+constexpr uint32_t kPBBytes = 128 * kTileK * 2;
+constexpr uint32_t kPStageBytes = kPABytes + kPBBytes;
+constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + 256;
+constexpr int kPairTile = 256;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                         const __grid_constant__ RnsGemmParams P) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sA = base;
+    unsigned char* sB = base + kPStages * kPABytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kPStages * kPBBytes);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + kPStages;
+    uint64_t* acc_full = bars + 2 * kPStages;
+    uint64_t* acc_empty = acc_full + 2;
+    uint64_t* drain = acc_empty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const InstInfo& I = P.inst;
+    int* err = P.err;
+
+    const int pair = (int)blockIdx.x >> 1, npairs = (int)gridDim.x >> 1;
+    const int my_tiles = pair < P.num_tiles ? (P.num_tiles - 1 - pair) / npairs + 1 : 0;
+    const int nch = I.nch;
+    const int J = my_tiles * nch;
+    const int CS = I.chunk_steps;
+    const int H = (I.ksteps + CS - 1) / CS;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kPStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 2 * kEpiWarps);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) tc_alloc_pair(tmem_slot, kTmemCols);
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&mapA);
+        tma_prefetch_desc(&mapB);
+    }
+    tc_fence_before();
+    cluster_sync();  // barriers of both CTAs initialised, tensor memory allocated
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ---------------------------------------------------- producer (both CTAs)
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued = 0, last_parity = 0;
+            bool ok = true;
+            for (int pi = 0; 2 * pi < J && ok; ++pi) {
+                const int nj = min(2, J - 2 * pi);
+                for (int h = 0; h < H && ok; ++h) {
+                    const int k0 = h * CS;
+                    const int steps = min(CS, I.ksteps - k0);
+                    for (int s = 0; s < nj && ok; ++s) {
+                        const int j = 2 * pi + s;
+                        const int t = pair + (j / nch) * npairs;
+                        const int c = j % nch;
+                        int tm, tn;
+                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
+                        const int rowA = tm * kPairTile + (int)rank * 128;
+                        const int rowB = tn * kPairTile + (int)rank * 128;
+                        for (int st = 0; st < steps; ++st) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err, kDevTimeoutProducer)) {
+                                ok = false;
+                                break;
+                            }
+                            if (leader) mbar_arrive_expect_tx(&full[stage], 2 * kPStageBytes);
+                            const uint32_t fb = cluster_addr(&full[stage], 0);
+                            const int kx = (k0 + st) * kTileK;
+                            tma_load_3d_pair(sA + stage * kPABytes, &mapA, kx, rowA, c, fb);
+                            tma_load_3d_pair(sB + stage * kPBBytes, &mapB, kx, rowB, c, fb);
+                            issued |= 1u << stage;
+                            last_parity = (last_parity & ~(1u << stage)) | (phase << stage);
+                            if (++stage == kPStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                    }
+                }
+            }
+            // the leader's full[] barriers count both CTAs' copies: draining them
+            // covers every copy into either CTA's shared memory
+            if (leader)
+                for (int s2 = 0; s2 < kPStages; ++s2)
+                    if (issued & (1u << s2)) mbar_drain_wait(&full[s2], (last_parity >> s2) & 1u, err);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer (leader)
+        if (lane == 0 && leader) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t accp[2] = {0u, 0u};
+            const uint32_t idesc = idesc_bf16_f32(2 * kTileM, kTileN);
+            bool ok = true;
+            bool any = false;
+            for (int pi = 0; 2 * pi < J && ok; ++pi) {
+                const int nj = min(2, J - 2 * pi);
+                for (int h = 0; h < H && ok; ++h) {
+                    const int steps = min(CS, I.ksteps - h * CS);
+                    for (int s = 0; s < nj && ok; ++s) {
+                        if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t dt = tmem + (uint32_t)(s * kTileN);
+                        for (int st = 0; st < steps; ++st) {
+                            if (!mbar_wait(&full[stage], phase, abort_flag, err, kDevTimeoutMma)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_addr(sA + stage * kPABytes);
+                            const uint32_t b0 = smem_addr(sB + stage * kPBBytes);
+#pragma unroll
+                            for (int kk = 0; kk < kTileK / 16; ++kk) {
+                                const uint32_t acc = (h > 0 || st > 0 || kk > 0) ? 1u : 0u;
+                                tc_mma_bf16_pair(dt, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                                 acc);
+                            }
+                            tc_commit_pair_both(&empty[stage]);
+                            any = true;
+                            if (++stage == kPStages) {
+                                stage = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!ok) break;
+                        tc_commit_pair_both(&acc_full[s]);
+                        accp[s] ^= 1u;
+                    }
+                }
+            }
+            if (any) {
+                tc_commit_pair_local(drain);
+                mbar_drain_wait(drain, 0u, err);
+            }
+        }
+    } else {
+        // ---------------------------------------------------- epilogue (both CTAs)
+        const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_local = q * 32 + lane;
+        unsigned char* slot_row = P.slots + size_t(blockIdx.x) * kSlotBytesPerCta + size_t(row_local) * kTileN +
+                                  half * 128;
+        const uint32_t acc_empty_leader[2] = {cluster_addr(&acc_empty[0], 0), cluster_addr(&acc_empty[1], 0)};
+        uint32_t accp[2] = {0u, 0u};
+        bool ok = true;
+        for (int pi = 0; 2 * pi < J && ok; ++pi) {
+            const int nj = min(2, J - 2 * pi);
+            for (int h = 0; h < H && ok; ++h) {
+                const bool last_chunk = (h == H - 1);
+                for (int s = 0; s < nj; ++s) {
+                    const int j = 2 * pi + s;
+                    const int c = j % nch;
+                    if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
+                        ok = false;
+                        break;
+                    }
+                    accp[s] ^= 1u;
+                    tc_fence_after();
+                    const uint32_t tbase =
+                        tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
+                    const float mf = I.modf[c], im = I.inv_m[c];
+                    const int mi = (int)I.modu[c];
+                    if (!last_chunk) {
+#pragma unroll 1
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t v[32];
+                            tc_ld32(tbase + cc * 32, v);
+                            tc_wait_ld();
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const float x = __uint_as_float(v[i]);
+                                const float qq = rintf(x * im);
+                                v[i] = __float_as_uint(fmaf(-qq, mf, x));
+                            }
+                            tc_st32(tbase + cc * 32, v);
+                        }
+                        tc_wait_st();
+                    } else {
+                        unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
+#pragma unroll 1
+                        for (int cc = 0; cc < 4; ++cc) {
+                            uint32_t v[32];
+                            tc_ld32(tbase + cc * 32, v);
+                            tc_wait_ld();
+                            uint32_t w[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) {
+                                uint32_t packed = 0;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    packed |= f32_residue(__uint_as_float(v[4 * i + e]), mf, im, mi) << (8 * e);
+                                w[i] = packed;
+                            }
+                            uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
+                            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (leader)
+                            mbar_arrive(&acc_empty[s]);
+                        else
+                            mbar_arrive_cluster(acc_empty_leader[s]);
+                    }
+                    if (last_chunk && c == nch - 1) {
+                        const int t = pair + (j / nch) * npairs;
+                        int tm, tn;
+                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
+                        // rows of this CTA: tile row block (2 tm + rank) of 128
+                        combine_tile_row(I, 2 * tm + (int)rank, tn, row_local, half, slot_row);
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    cluster_sync();  // no CTA leaves while its peer may still read its shared memory
+    if (warp == 1) {
+        tc_fence_after();
+        tc_dealloc_pair(tmem, kTmemCols);
+    }
+}
+
 }  // namespace
 
 size_t rns_gemm_smem_bytes() { return kSmemBytes; }
+
+static cudaLaunchConfig_t pair_config(int grid, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = kPairSmemBytes;
+    cfg.stream = s;
+    attr->id = cudaLaunchAttributeClusterDimension;
+    attr->val.clusterDim.x = 2;
+    attr->val.clusterDim.y = 1;
+    attr->val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+static cudaError_t pair_attr() {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(rns_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kPairSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    return cudaSuccess;
+}
+
+// Number of CTA pairs that can be resident at once (GPCs with an odd number of
+// SMs leave one SM out): the persistent grid must not exceed it.
+int rns_gemm_pair_max_clusters() {
+    static int cached = -1;
+    if (cached < 0) {
+        if (pair_attr() != cudaSuccess) return 0;
+        cudaLaunchAttribute attr;
+        cudaLaunchConfig_t cfg = pair_config(2, 0, &attr);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, rns_gemm_pair_kernel, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cached = n;
+    }
+    return cached;
+}
+
+cudaError_t launch_rns_gemm_pair(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
+                                 int grid, cudaStream_t s) {
+    cudaError_t e = pair_attr();
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr;
+    cudaLaunchConfig_t cfg = pair_config(grid, s, &attr);
+    return cudaLaunchKernelEx(&cfg, rns_gemm_pair_kernel, mapA, mapB, prm);
+}
 
 cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s) {

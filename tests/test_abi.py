@@ -51,7 +51,7 @@ def test_invalid_arguments_rejected_without_device():
     assert f(0, 4, 4, 7, 1, 0, 4, 0, 4, 0, 0, 4) == 0           # m = 0: nothing to do
 
 
-MODULI_LIMIT = 256
+MODULI_LIMIT = 255
 
 
 def test_plan_moduli_are_coprime_and_sufficient():
@@ -63,6 +63,9 @@ def test_plan_moduli_are_coprime_and_sufficient():
             if p <= MODULI_LIMIT:
                 assert pl["mode"] == 1 and mods == [p]
                 continue
+            # chunk of products summed exactly in f32: reduced value + chunk * max|r|^2 < 2^24
+            R = max(m // 2 for m in mods)
+            assert pl["k_chunk"] % 64 == 0 and (R + 1) + pl["k_chunk"] * R * R < 2**24
             assert pl["mode"] == 2
             assert all(2 <= m <= MODULI_LIMIT for m in mods)
             for i in range(len(mods)):
@@ -78,12 +81,14 @@ def test_plan_moduli_are_coprime_and_sufficient():
 
 
 def test_plan_channel_counts_of_the_sweep():
-    # p < 2^31 at n = 8192: 10 channels; p < 2^16: 6; p < 2^8: the prime itself
+    # p < 2^31 at n = 8192: 10 channels; p < 2^16: 6; p < 2^8: the prime itself;
+    # 1024 products between in-place reductions (residues |r| <= 127)
     assert ff.fgemm_plan(8192, 8192, 8192, 2147483647)["channels"] == 10
     assert ff.fgemm_plan(8192, 8192, 8192, 8388593)["channels"] == 8
     assert ff.fgemm_plan(8192, 8192, 8192, 65521)["channels"] == 6
     assert ff.fgemm_plan(8192, 8192, 8192, 251)["channels"] == 1
     assert ff.fgemm_plan(8192, 8192, 65536, 2147483647)["channels"] == 10
+    assert ff.fgemm_plan(8192, 8192, 8192, 2147483647)["k_chunk"] == 1024
 
 
 def test_workspace_size_monotone():

@@ -154,3 +154,30 @@ def test_full_size_8192_sampled(p):
     expect = oracle.fgemm_entries(A, B, p, alpha, beta, C, rows, cols)
     assert np.array_equal(got[rows, cols], expect)
     assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
+
+
+@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("shape,p", [((300, 1100, 520), 2147483647), ((129, 65, 257), 65521),
+                                     ((2048, 256, 4096), 2147483647), ((600, 512, 1100), 2147483647),
+                                     ((256, 2048, 512), 251)])
+def test_both_tensor_core_kernels(kernel, shape, p, monkeypatch):
+    """The one-CTA kernel (128 x 256 tiles) and the CTA-pair kernel (256 x 256
+    tiles, cta_group::2) must both be exact on ragged shapes, several tiles
+    per CTA, odd channel counts and long inner dimensions."""
+    monkeypatch.setenv("FFGPU_KERNEL", kernel)
+    m, k, n = shape
+    rng = W.rng_for("square", 20, m + k + n, p)
+    A = W.uniform_words(rng, (m, k))
+    B = W.uniform_words(rng, (k, n))
+    C = W.uniform_words(rng, (m, n))
+    check(A, B, C, p, 5, 7)
+
+
+@pytest.mark.parametrize("kernel", ["single", "pair"])
+def test_both_kernels_adversarial(kernel, monkeypatch):
+    monkeypatch.setenv("FFGPU_KERNEL", kernel)
+    p = 2147483647
+    m, n, k = 512, 512, 4096
+    A, B, C = W.adversarial_problem(m, n, k, p)
+    got = run(A, B, C, p, p - 1, p - 1)
+    assert np.all(got == ((p - 1) * k + (p - 1) * (p - 1)) % p)
