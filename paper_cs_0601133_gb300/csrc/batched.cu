@@ -97,7 +97,7 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     cta_begin[grid] = (int)jobs.size();
 
     // workspace layout: slots | pools | tables
-    size_t off = align_up(size_t(grid) * kGroupedSlots * kSlotBytesPerCta, 256);
+    size_t off = align_up(size_t(grid) * kSlotsPerCta * kSlotBytesPerCta, 256);
     for (auto& B : buckets) {
         B.offA = off;
         off = align_up(off + size_t(B.nch) * B.rowsA * B.kp * 2, 256);
@@ -208,6 +208,7 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     P.cta_begin = reinterpret_cast<const int*>(ws + t_cta);
     P.maps = reinterpret_cast<const CUtensorMap*>(ws + t_maps);
     P.slots = ws;
+    P.slot_stride = kSlotBytesPerCta;
     P.err = pool->err;
     if (timed_launch("rns_gemm_grouped", s, [&] { return launch_rns_gemm_grouped(P, grid, s); }) != cudaSuccess)
         return FFGPU_ERR_CUDA;

@@ -195,10 +195,12 @@ struct Layout {
     size_t slots, planesA, planesB, total;
 };
 
+size_t slot_stride_for(int nch) { return size_t(nch) * kTileM * kTileN; }
+
 static Layout layout_for(int64_t m, int64_t n, int64_t kp, int nch, int grid) {
     Layout L;
     L.slots = 0;
-    L.planesA = align256(size_t(grid) * kSlotBytesPerCta);
+    L.planesA = align256(size_t(grid) * kSlotsPerCta * slot_stride_for(nch));
     L.planesB = L.planesA + align256(size_t(nch) * m * kp * 2);
     L.total = L.planesB + align256(size_t(nch) * n * kp * 2);
     return L;
@@ -338,6 +340,7 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
         P.tiles_n = (int)((n + kTileN - 1) / kTileN);
         P.num_tiles = P.tiles_m * P.tiles_n;
         P.slots = wsb + L.slots;
+        P.slot_stride = slot_stride_for(pl.nch);
         P.err = err;
         if (pair) {
             const int pgrid = 2 * std::max(1, std::min(std::min(P.num_tiles, grid / 2), rns_gemm_pair_max_clusters()));

@@ -75,7 +75,8 @@ struct InstInfo {
 struct RnsGemmParams {
     InstInfo inst;
     int tiles_m, tiles_n, num_tiles;
-    unsigned char* slots;          // per-CTA residue slots
+    unsigned char* slots;          // per-CTA residue slots: 2 x slot_stride bytes per CTA
+    size_t slot_stride;            // bytes of one slot: channels x 128 x 256
     int* err;                      // device error word
 };
 
@@ -84,17 +85,18 @@ struct RnsGemmParams {
 struct GroupJob {
     int inst, tm, tn, c;
 };
-constexpr int kGroupedSlots = 2;
 struct GroupGemmParams {
     const InstInfo* insts;
     const GroupJob* jobs;
     const int* cta_begin;          // jobs of CTA b: [cta_begin[b], cta_begin[b+1])
     const CUtensorMap* maps;       // 2 per k-bucket: A planes, B planes (64-byte aligned)
-    unsigned char* slots;
+    unsigned char* slots;          // 2 x slot_stride bytes per CTA
+    size_t slot_stride;
     int* err;
 };
 
-constexpr size_t kSlotBytesPerCta = size_t(kMaxChannels) * kTileM * kTileN;
+constexpr size_t kSlotBytesPerCta = size_t(kMaxChannels) * kTileM * kTileN;  // one slot, any channel count
+constexpr int kSlotsPerCta = 2;  // double buffered: residues of one tile, reconstruction of the previous
 
 // Conversion parameters: uint32 words -> bf16 channel planes.
 struct ConvertParams {

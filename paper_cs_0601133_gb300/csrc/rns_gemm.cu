@@ -37,8 +37,9 @@ namespace ffgpu {
 
 namespace {
 
-constexpr int kThreads = 320;
+constexpr int kThreads = 448;   // 2 control warps, 8 epilogue warps, 4 combine warps
 constexpr int kEpiWarps = 8;
+constexpr int kFirstCombineWarp = 10;
 constexpr uint32_t kABytes = kTileM * kTileK * 2;
 constexpr uint32_t kBBytes = kTileN * kTileK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
@@ -77,28 +78,29 @@ __device__ __forceinline__ uint32_t f32_residue(float x, float m, float inv_m, i
     return (uint32_t)r;
 }
 
-// Reconstruction of X mod p for four adjacent outputs from their residues.
-// With M = prod m_c and b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c)
-// - q M where q = round(sum_c b_c / m_c), valid because the plan guarantees
+// Reconstruction of X mod p for four adjacent outputs from their residues
+// (w[c] holds the four residues of channel c, one per byte).  With
+// M = prod m_c and b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c) - q M
+// where q = round(sum_c b_c / m_c), valid because the plan guarantees
 // |X| <= M/4 (the fraction is within 1/4 of an integer, far above f32 error).
-__device__ __forceinline__ void crt4(const InstInfo& I, const unsigned char* slot, int g,
-                                     uint32_t (&X)[4]) {
+__device__ __forceinline__ void crt4(const InstInfo& I, const uint32_t (&w)[kMaxChannels], uint32_t (&X)[4]) {
     unsigned long long S[4] = {0ull, 0ull, 0ull, 0ull};
     float G[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = 0; c < I.nch; ++c) {
-        const uint32_t w =
-            *reinterpret_cast<const uint32_t*>(slot + size_t(c) * kTileM * kTileN + 4 * g);
-        const uint32_t uc = I.u[c], mc = I.modu[c], Wc = I.W[c];
-        const float im = I.inv_m[c];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int t = (int)(((w >> (8 * e)) & 255u) * uc);
-            const int qf = (int)floorf((float)t * im);
-            int b = t - qf * (int)mc;
-            if (b < 0) b += (int)mc;
-            if (b >= (int)mc) b -= (int)mc;
-            G[e] = fmaf((float)b, im, G[e]);
-            S[e] += (unsigned long long)b * Wc;
+    for (int c = 0; c < kMaxChannels; ++c) {
+        if (c < I.nch) {
+            const uint32_t uc = I.u[c], mc = I.modu[c], Wc = I.W[c];
+            const float im = I.inv_m[c];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int t = (int)(((w[c] >> (8 * e)) & 255u) * uc);
+                const int qf = (int)floorf((float)t * im);
+                int b = t - qf * (int)mc;
+                if (b < 0) b += (int)mc;
+                if (b >= (int)mc) b -= (int)mc;
+                G[e] = fmaf((float)b, im, G[e]);
+                S[e] += (unsigned long long)b * Wc;
+            }
         }
     }
 #pragma unroll
@@ -108,46 +110,60 @@ __device__ __forceinline__ void crt4(const InstInfo& I, const unsigned char* slo
     }
 }
 
-__device__ __forceinline__ void combine_tile_row(const InstInfo& I, int tm, int tn, int row_local,
-                                                 int half, const unsigned char* slot_row) {
-    const int row = tm * kTileM + row_local;
-    if (row >= I.m) return;
-    uint32_t* crow = I.C + (long long)row * I.ldc;
-    const int col0 = tn * kTileN + half * 128;
-    for (int g = 0; g < 32; ++g) {
-        const int col = col0 + 4 * g;
-        if (col >= I.n) break;
-        uint32_t X[4];
-        if (I.direct) {
-            const uint32_t w = *reinterpret_cast<const uint32_t*>(slot_row + 4 * g);
+// Reconstruction and C update for the 128 x 256 block of one CTA, by one of
+// the kCombineWarps combine warps: warp cw takes rows [32 cw, 32 cw + 32); the
+// lanes of a warp cover 128 consecutive columns (4 each), so the residue loads
+// (128 B per channel) and the C accesses (512 B) are coalesced, and the loads of
+// all channels are issued before any arithmetic.
+constexpr int kCombineWarps = 4;
+
+__device__ __forceinline__ void combine_block(const InstInfo& I, int row0, int col0, const unsigned char* slot,
+                                              size_t chan_stride, int cw, int lane) {
+    for (int r = cw * 32; r < cw * 32 + 32; ++r) {
+        const int row = row0 + r;
+        if (row >= I.m) break;
+        uint32_t* crow = I.C + (long long)row * I.ldc;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            const int lc = pass * 128 + 4 * lane;
+            const int col = col0 + lc;
+            if (col >= I.n) continue;
+            const unsigned char* src = slot + size_t(r) * kTileN + lc;
+            uint32_t w[kMaxChannels];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) X[e] = (w >> (8 * e)) & 255u;
-        } else {
-            crt4(I, slot_row, g, X);
-        }
-        const bool full4 = col + 3 < I.n;
-        uint32_t old[4] = {0u, 0u, 0u, 0u};
-        if (I.beta != 0) {
+            for (int c = 0; c < kMaxChannels; ++c)
+                w[c] = c < I.nch ? *reinterpret_cast<const uint32_t*>(src + size_t(c) * chan_stride) : 0u;
+            uint32_t X[4];
+            if (I.direct) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) X[e] = (w[0] >> (8 * e)) & 255u;
+            } else {
+                crt4(I, w, X);
+            }
+            const bool full4 = col + 3 < I.n;
+            uint32_t old[4] = {0u, 0u, 0u, 0u};
+            if (I.beta != 0) {
+                if (full4 && I.vec_ok) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
+                    old[0] = v.x; old[1] = v.y; old[2] = v.z; old[3] = v.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (col + e < I.n) old[e] = crow[col + e];
+                }
+            }
+            uint32_t out[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                out[e] = mod_u64((unsigned long long)I.alpha * X[e] + (unsigned long long)I.beta * old[e], I.p,
+                                 I.mu);
             if (full4 && I.vec_ok) {
-                const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
-                old[0] = v.x; old[1] = v.y; old[2] = v.z; old[3] = v.w;
+                *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
-                    if (col + e < I.n) old[e] = crow[col + e];
+                    if (col + e < I.n) crow[col + e] = out[e];
             }
-        }
-        uint32_t out[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-            out[e] = mod_u64((unsigned long long)I.alpha * X[e] + (unsigned long long)I.beta * old[e],
-                             I.p, I.mu);
-        if (full4 && I.vec_ok) {
-            *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (col + e < I.n) crow[col + e] = out[e];
         }
     }
 }
@@ -184,10 +200,10 @@ struct SingleSched {
         d.c = j % nch;
         tile_coords(t, P.tiles_m, P.tiles_n, d.tm, d.tn);
         d.H = (P.inst.ksteps + P.inst.chunk_steps - 1) / P.inst.chunk_steps;
-        d.slot = 0;  // every job has the same length: a tile's reconstruction precedes the next tile's residues
+        d.slot = (j / nch) & 1;  // tiles alternate the two residue slots
     }
-    static constexpr int kSlots = 1;
     __device__ unsigned char* slots() const { return P.slots; }
+    __device__ size_t slot_stride() const { return P.slot_stride; }
     __device__ int* err() const { return P.err; }
 };
 
@@ -210,12 +226,10 @@ struct GroupSched {
         d.tn = g.tn;
         d.c = g.c & 0xFF;
         d.H = (I->ksteps + I->chunk_steps - 1) / I->chunk_steps;
-        // jobs of different lengths: a pair may finish the next tile's first
-        // channel before this tile's reconstruction, so tiles alternate slots
-        d.slot = (g.c >> 8) & 1;
+        d.slot = (g.c >> 8) & 1;  // tiles alternate the two residue slots
     }
-    static constexpr int kSlots = 2;
     __device__ unsigned char* slots() const { return P.slots; }
+    __device__ size_t slot_stride() const { return P.slot_stride; }
     __device__ int* err() const { return P.err; }
 };
 
@@ -233,7 +247,9 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
     uint64_t* acc_full = bars + 2 * kStages;
     uint64_t* acc_empty = acc_full + 2;
     uint64_t* drain = acc_empty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* slot_full = drain + 1;    // [2] epilogue -> combine warps: a tile's residues are complete
+    uint64_t* slot_empty = slot_full + 2;  // [2] combine -> epilogue warps: the slot may be rewritten
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(slot_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -251,6 +267,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
             mbar_init(&acc_empty[a], kEpiWarps);
+            mbar_init(&slot_full[a], kEpiWarps);
+            mbar_init(&slot_empty[a], kCombineWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -371,14 +389,16 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                 mbar_drain_wait(drain, 0u, err);
             }
         }
-    } else {
+    } else if (warp < kFirstCombineWarp) {
         // ------------------------------------------------------------ epilogue
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_local = q * 32 + lane;
-        unsigned char* slot_base = S.slots() + size_t(blockIdx.x) * Sched::kSlots * kSlotBytesPerCta;
+        const size_t sstride = S.slot_stride();
+        unsigned char* slot_base = S.slots() + size_t(blockIdx.x) * 2 * sstride;
         const size_t row_off = size_t(row_local) * kTileN + half * 128;
         uint32_t accp[2] = {0u, 0u};
+        uint32_t sep[2] = {0u, 0u};  // slot_empty phases
         bool ok = true;
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
@@ -393,7 +413,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     const bool last_chunk = (h == d.H - 1);
                     const InstInfo& I = *d.inst;
                     const int c = d.c;
-                    unsigned char* slot_row = slot_base + size_t(d.slot) * kSlotBytesPerCta + row_off;
+                    unsigned char* slot_row = slot_base + size_t(d.slot) * sstride + row_off;
                     if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
                         ok = false;
                         break;
@@ -420,6 +440,15 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                         }
                         tc_wait_st();
                     } else {
+                        // the tile's first residues: wait until the combine warps released this slot
+                        if (c == 0) {
+                            if (!mbar_wait(&slot_empty[d.slot], sep[d.slot] ^ 1u, abort_flag, err,
+                                           kDevTimeoutEpilogue)) {
+                                ok = false;
+                                break;
+                            }
+                            sep[d.slot] ^= 1u;
+                        }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
 #pragma unroll 1
                         for (int cc = 0; cc < 4; ++cc) {
@@ -442,11 +471,31 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                         }
                     }
                     tc_fence_before();
+                    if (last_chunk && c == I.nch - 1) __threadfence_block();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&acc_empty[s]);
-                    if (last_chunk && c == I.nch - 1) combine_tile_row(I, d.tm, d.tn, row_local, half, slot_row);
+                    if (lane == 0) {
+                        mbar_arrive(&acc_empty[s]);
+                        if (last_chunk && c == I.nch - 1) mbar_arrive(&slot_full[d.slot]);
+                    }
                 }
             }
+        }
+    } else {
+        // ------------------------------------------------------------ combine warps
+        const int cw = warp - kFirstCombineWarp;
+        const size_t sstride = S.slot_stride();
+        unsigned char* slot_base = S.slots() + size_t(blockIdx.x) * 2 * sstride;
+        uint32_t sfp[2] = {0u, 0u};
+        for (int j = 0; j < J; ++j) {
+            Job d;
+            S.job(j, d);
+            if (d.c != d.inst->nch - 1) continue;  // one reconstruction per tile
+            if (!mbar_wait(&slot_full[d.slot], sfp[d.slot], abort_flag, err, kDevTimeoutEpilogue)) break;
+            sfp[d.slot] ^= 1u;
+            combine_block(*d.inst, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+                          size_t(kTileM) * kTileN, cw, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&slot_empty[d.slot]);
         }
     }
 
@@ -503,7 +552,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* acc_full = bars + 2 * kPStages;
     uint64_t* acc_empty = acc_full + 2;
     uint64_t* drain = acc_empty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* slot_full = drain + 1;       // [2] epilogue -> combine warps (this CTA)
+    uint64_t* slot_empty = slot_full + 2;  // [2] combine -> epilogue warps (this CTA)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(slot_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -528,6 +579,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
             mbar_init(&acc_empty[a], 2 * kEpiWarps);
+            mbar_init(&slot_full[a], kEpiWarps);
+            mbar_init(&slot_empty[a], kCombineWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -641,15 +694,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_drain_wait(drain, 0u, err);
             }
         }
-    } else {
+    } else if (warp < kFirstCombineWarp) {
         // ---------------------------------------------------- epilogue (both CTAs)
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_local = q * 32 + lane;
-        unsigned char* slot_row = P.slots + size_t(blockIdx.x) * kSlotBytesPerCta + size_t(row_local) * kTileN +
-                                  half * 128;
+        unsigned char* slot_base = P.slots + size_t(blockIdx.x) * 2 * P.slot_stride;
+        const size_t row_off = size_t(row_local) * kTileN + half * 128;
         const uint32_t acc_empty_leader[2] = {cluster_addr(&acc_empty[0], 0), cluster_addr(&acc_empty[1], 0)};
         uint32_t accp[2] = {0u, 0u};
+        uint32_t sep[2] = {0u, 0u};
         bool ok = true;
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
@@ -658,6 +712,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int s = 0; s < nj; ++s) {
                     const int j = 2 * pi + s;
                     const int c = j % nch;
+                    const int slot = (j / nch) & 1;
+                    unsigned char* slot_row = slot_base + size_t(slot) * P.slot_stride + row_off;
                     if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
                         ok = false;
                         break;
@@ -684,6 +740,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                         tc_wait_st();
                     } else {
+                        if (c == 0) {
+                            if (!mbar_wait(&slot_empty[slot], sep[slot] ^ 1u, abort_flag, err, kDevTimeoutEpilogue)) {
+                                ok = false;
+                                break;
+                            }
+                            sep[slot] ^= 1u;
+                        }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
 #pragma unroll 1
                         for (int cc = 0; cc < 4; ++cc) {
@@ -705,22 +768,34 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     tc_fence_before();
+                    if (last_chunk && c == nch - 1) __threadfence_block();
                     __syncwarp();
                     if (lane == 0) {
                         if (leader)
                             mbar_arrive(&acc_empty[s]);
                         else
                             mbar_arrive_cluster(acc_empty_leader[s]);
-                    }
-                    if (last_chunk && c == nch - 1) {
-                        const int t = pair + (j / nch) * npairs;
-                        int tm, tn;
-                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
-                        // rows of this CTA: tile row block (2 tm + rank) of 128
-                        combine_tile_row(I, 2 * tm + (int)rank, tn, row_local, half, slot_row);
+                        if (last_chunk && c == nch - 1) mbar_arrive(&slot_full[slot]);
                     }
                 }
             }
+        }
+    } else {
+        // ---------------------------------------------------- combine warps (both CTAs)
+        const int cw = warp - kFirstCombineWarp;
+        unsigned char* slot_base = P.slots + size_t(blockIdx.x) * 2 * P.slot_stride;
+        uint32_t sfp[2] = {0u, 0u};
+        for (int ti = 0; ti < my_tiles; ++ti) {
+            const int slot = ti & 1;
+            if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;
+            sfp[slot] ^= 1u;
+            int tm, tn;
+            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
+            // rows of this CTA: the 128-row block 2 tm + rank
+            combine_block(I, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
+                          size_t(kTileM) * kTileN, cw, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&slot_empty[slot]);
         }
     }
 
