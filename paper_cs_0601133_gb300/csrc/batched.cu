@@ -149,13 +149,12 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
         std::memset(&cp, 0, sizeof(cp));
         cp.p = d.p;
         cp.half_p = d.p / 2;
-        cp.mu = barrett_mu(d.p);
+        cp.mu32 = 0xFFFFFFFFu / cp.p;
         cp.nch = b.pl.nch;
         cp.direct = b.pl.mode == 1;
         for (int c = 0; c < b.pl.nch; ++c) {
             cp.mod[c] = b.pl.mod[c];
-            cp.pmod[c] = d.p % b.pl.mod[c];
-            cp.magic[c] = ((1ull << 40) + b.pl.mod[c] - 1) / b.pl.mod[c];
+            cp.magic32[c] = (uint32_t)(((1ull << 39) + b.pl.mod[c] - 1) / b.pl.mod[c]);
         }
         ConvJob& a = convA[i];
         a.X = d.A;

@@ -4,9 +4,9 @@
 // The conversion is the "few conversions" step the paper keeps out of the
 // product (section 1 and section 2.1.2: a residue is embedded in Z, here as a
 // centred representative, eq. 2): x -> x mod p -> centred x~ in
-// (-p/2, p/2] -> for each modulus m_c the balanced residue of x~ mod m_c in
-// [-m_c/2, m_c/2), written as an exact bf16.  With a single modulus (p <= 256)
-// the plane holds x~ itself.  Rows are padded with zeros to a multiple of 64
+// [-(p-1)/2, p/2] -> for each odd modulus m_c the balanced residue of
+// x~ mod m_c in [-(m_c-1)/2, (m_c-1)/2], written as an exact bf16.  With a
+// single modulus (p <= 255) the plane holds x~ itself.  Rows are padded with zeros to a multiple of 64
 // columns so every tensor-core tile sees whole 128-byte rows.
 #include <cuda_bf16.h>
 
@@ -17,54 +17,57 @@ namespace ffgpu {
 
 namespace {
 
-__device__ __forceinline__ unsigned short bf16_bits_of_int(int v) {
-    // |v| <= 256: exact in bf16
-    const __nv_bfloat16 b = __float2bfloat16_rn((float)v);
-    return *reinterpret_cast<const unsigned short*>(&b);
-}
-
 // Residues of 8 words in every channel, packed 8 x bf16 per channel and
 // stored at dst[c * stride16].
+//   x mod p: 32-bit Barrett (quotient estimate umulhi(x, floor((2^32-1)/p)) is
+//            at most one below, one correction);
+//   centring: x~ = x mod p if <= floor(p/2), else -(p - x mod p); kept as a
+//            magnitude y and a sign;
+//   balanced residue of y mod m: q = floor((y + (m-1)/2) / m) by a 32-bit
+//            magic multiply (magic = ceil(2^39/m), exact for y < 2^31 and
+//            m <= 255), r = y - q m in [-(m-1)/2, (m-1)/2]; the sign of x~ is
+//            applied to the bf16 pattern (negation flips its sign bit).
 __device__ __forceinline__ void residues8(const ConvertParams& cp, const uint32_t (&x)[8],
                                           uint4* __restrict__ dst, size_t stride16) {
-    uint32_t xr[8];
-    bool neg[8];
+    uint32_t y[8];
+    uint32_t sign[4];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        xr[e] = mod_u64(x[e], cp.p, cp.mu);
-        neg[e] = xr[e] > cp.half_p;
+        const uint32_t q = __umulhi(x[e], cp.mu32);
+        uint32_t r = x[e] - q * cp.p;
+        if (r >= cp.p) r -= cp.p;
+        const bool neg = r > cp.half_p;
+        y[e] = neg ? cp.p - r : r;
+        if ((e & 1) == 0) sign[e >> 1] = neg ? 0x8000u : 0u;
+        else sign[e >> 1] |= neg ? 0x80000000u : 0u;
     }
     if (cp.direct) {
         uint32_t w[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int v0 = neg[2 * i] ? (int)xr[2 * i] - (int)cp.p : (int)xr[2 * i];
-            const int v1 = neg[2 * i + 1] ? (int)xr[2 * i + 1] - (int)cp.p : (int)xr[2 * i + 1];
-            w[i] = (uint32_t)bf16_bits_of_int(v0) | ((uint32_t)bf16_bits_of_int(v1) << 16);
+            const __nv_bfloat162 b = __floats2bfloat162_rn((float)y[2 * i], (float)y[2 * i + 1]);
+            w[i] = *reinterpret_cast<const uint32_t*>(&b) ^ sign[i];
         }
         dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
         return;
     }
 #pragma unroll 1
     for (int c = 0; c < cp.nch; ++c) {
-        const uint32_t m = cp.mod[c], pm = cp.pmod[c];
-        const unsigned long long mg = cp.magic[c];
-        const int halfm = (int)(m - 1) / 2;
-        unsigned short h[8];
+        const uint32_t m = cp.mod[c], mg = cp.magic32[c], h = (m - 1) >> 1;
+        uint32_t w[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            // floor(xr / m) exactly: xr < 2^31, m <= 256, magic = ceil(2^40 / m)
-            const uint32_t q = (uint32_t)(((unsigned long long)xr[e] * mg) >> 40);
-            int r = (int)(xr[e] - q * m);
-            if (neg[e]) {  // x~ = xr - p
-                r -= (int)pm;
-                if (r < 0) r += (int)m;
+        for (int i = 0; i < 4; ++i) {
+            float f[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t v = y[2 * i + t];
+                const uint32_t q = __umulhi(v + h, mg) >> 7;
+                f[t] = (float)(int)(v - q * m);
             }
-            if (r > halfm) r -= (int)m;
-            h[e] = bf16_bits_of_int(r);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(f[0], f[1]);
+            w[i] = *reinterpret_cast<const uint32_t*>(&b) ^ sign[i];
         }
-        dst[(size_t)c * stride16] = make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
-                            (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
+        dst[(size_t)c * stride16] = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 

@@ -306,13 +306,12 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
         std::memset(&cp, 0, sizeof(cp));
         cp.p = p;
         cp.half_p = p / 2;
-        cp.mu = mu;
+        cp.mu32 = 0xFFFFFFFFu / cp.p;
         cp.nch = pl.nch;
         cp.direct = pl.mode == 1;
         for (int c = 0; c < pl.nch; ++c) {
             cp.mod[c] = pl.mod[c];
-            cp.pmod[c] = p % pl.mod[c];
-            cp.magic[c] = ((1ull << 40) + pl.mod[c] - 1) / pl.mod[c];
+            cp.magic32[c] = (uint32_t)(((1ull << 39) + pl.mod[c] - 1) / pl.mod[c]);
         }
         if (launch("convert_rows", [&] {
                 return launch_convert_rows(A + k0, lda, (int)m, (int)ks, (int)kp, cp, wsb + L.planesA, s);

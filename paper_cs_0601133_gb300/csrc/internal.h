@@ -102,12 +102,11 @@ constexpr int kSlotsPerCta = 2;  // double buffered: residues of one tile, recon
 struct ConvertParams {
     uint32_t p;
     uint32_t half_p;                 // floor(p/2): residues above it are centred to x - p
-    unsigned long long mu;           // floor((2^64-1)/p)
+    uint32_t mu32;                   // floor((2^32-1)/p)
     int nch;
     int direct;
-    uint32_t mod[kMaxChannels];
-    uint32_t pmod[kMaxChannels];     // p mod m_c
-    unsigned long long magic[kMaxChannels];  // ceil(2^40 / m_c)
+    uint32_t mod[kMaxChannels];      // odd moduli <= 255
+    uint32_t magic32[kMaxChannels];  // ceil(2^39 / m_c) < 2^32
 };
 
 // One matrix of a grouped conversion.  A (rows mode): X is rows (= m) x cols
