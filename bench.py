@@ -194,6 +194,27 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (one process per GPU; weak scaling, replicas only)
+# ---------------------------------------------------------------------------
+def max_over_ranks(ms: float, device) -> float:
+    """The slowest rank's time (every rank gets it); the local time without a
+    process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, steps: int, ops_per_step: float, max_ms: float) -> float:
+    """Whole-job throughput in GOPS: every rank ran `steps` steps of the same
+    size, the job took the slowest rank's time."""
+    return world * steps * ops_per_step / (max_ms / 1e3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_own(args):
@@ -244,15 +265,11 @@ def run_own(args):
     clocks = sampler.stop()
     kernels = ff.profile_read()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
     if ff.last_device_error() != 0:
         raise RuntimeError("device error word set during the timed region")
     flop_step = 2.0 * n * n * n
-    value = world * args.steps * flop_step / (ms / 1e3) / 1e9
+    value = weak_scaling_value(world, args.steps, flop_step, ms)
 
     plan = ff.fgemm_plan(n, n, n, p)
     launches = sum(v[0] for v in kernels.values())
@@ -333,13 +350,8 @@ def run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    return {"value": world * args.steps * 2.0 * n ** 3 / (ms / 1e3) / 1e9, "unit": "GOPS",
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
+    return {"value": weak_scaling_value(world, args.steps, 2.0 * n ** 3, ms), "unit": "GOPS",
             "h2d_bytes_per_step": 3 * n * n * 4, "d2h_bytes_per_step": n * n * 4,
             "ms_per_step": ms / args.steps}
 

@@ -284,6 +284,16 @@ typedef struct {
 FFGPU_API ffgpu_status ffgpu_profile_enable(int on);
 FFGPU_API ffgpu_status ffgpu_profile_read(ffgpu_kernel_time* out, int cap, int* count);
 
+/*
+ * Self-test of failure detection (not in the paper): launches on `stream` a
+ * kernel whose single wait targets a barrier that nothing completes, with a
+ * limit of `limit_cycles` SM clock cycles (1 .. 2e9).  The wait gives up, the
+ * kernel records a timeout and returns; ffgpu_last_device_error(stream) then
+ * reports FFGPU_ERR_TIMEOUT and the context stays usable.  Every wait in the
+ * library's kernels uses the same bounded mechanism (limit about one second).
+ */
+FFGPU_API ffgpu_status ffgpu_selftest_wait_timeout(int64_t limit_cycles, void* stream);
+
 /* Frees every workspace pool of the calling process (synchronizes the device). */
 FFGPU_API ffgpu_status ffgpu_release_workspaces(void);
 

@@ -5,9 +5,9 @@ The computation lives in the CUDA library ``libffgpu.so`` (C ABI declared in
 draws the seeded synthetic inputs.
 """
 from .ffgpu import (FFGPUError, fgemm, fgemm_noalloc_ptr, fgemm_plan, fgemm_ptr, fgemm_workspace_size, fgemm_ws, ftrsm,
-                    fgemm_batched, fgemm_ex, Server,
+                    fgemm_batched, fgemm_ex, Server, selftest_wait_timeout,
                     profile_enable, profile_read,
                     last_device_error, lib, release_workspaces, status_string, version)
 
-__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex", "Server",
+__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex", "Server", "selftest_wait_timeout",
            "last_device_error", "lib", "release_workspaces", "status_string", "version"]

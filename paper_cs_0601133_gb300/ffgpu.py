@@ -108,6 +108,7 @@ SIGNATURES = {
     "ffgpu_server_destroy": [_VP],
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
+    "ffgpu_selftest_wait_timeout": [_I64, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
 }
@@ -267,6 +268,11 @@ def fgemm_plan(m: int, n: int, k: int, p: int) -> dict:
 
 def last_device_error(stream=None) -> int:
     return lib().ffgpu_last_device_error(_stream_ptr(stream))
+
+
+def selftest_wait_timeout(limit_cycles: int = 2_000_000, stream=None) -> None:
+    """Launch the bounded-wait self-test kernel (see include/ffgpu.h)."""
+    check(lib().ffgpu_selftest_wait_timeout(limit_cycles, _stream_ptr(stream)), "selftest_wait_timeout")
 
 
 def release_workspaces() -> None:
