@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve", "ftrsm", "batched"],
+                    default="headline",
                     help="headline: the driver's line; the others print one line per configuration point")
     return ap.parse_args()
 
@@ -435,6 +436,62 @@ def run_precision(args):
     return 0
 
 
+def run_ftrsm(args):
+    """Triangular solves (section 4, Tables 5-6: p = 65521, square right-hand
+    side m = n): effective GOPS = n^3 / t (classic count m^2 n), and the time
+    ratio ftrsm / fgemm at the same n (the paper observes 0.5-0.666)."""
+    import torch
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+    p = 65521
+    for n in (2048, 4096, 8192):
+        rng = W.rng_for("ftrsm", 1000, n)
+        for uplo, diag in (("L", "U"), ("U", "N")):
+            T = W.triangular(rng, n, p, uplo, diag == "U")
+            B = W.uniform_residues(rng, (n, n), p)
+            dT = torch.from_numpy(T.view(np.int32)).cuda()
+            dB0 = torch.from_numpy(B.view(np.int32)).cuda()
+            dB = dB0.clone()
+            steps = 3 if n < 8192 else 2
+            ms = time_call(lambda: (dB.copy_(dB0), ff.ftrsm(dT, dB, p, 1, "L", uplo, diag)), torch, steps, 1)
+            copy_ms = time_call(lambda: dB.copy_(dB0), torch, steps, 1)
+            dC = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+            gemm_ms = time_call(lambda: ff.fgemm(dT, dB0, p, 1, 0, dC), torch, steps, 1)
+            t = ms - copy_ms
+            print(json.dumps({"workload": "ftrsm", "n": n, "p": p, "side": "L", "uplo": uplo, "diag": diag,
+                              "ms": t, "GOPS": n ** 3 / (t / 1e3) / 1e9, "fgemm_ms": gemm_ms,
+                              "ftrsm_over_fgemm": t / gemm_ms}), flush=True)
+            del dT, dB0, dB, dC
+    return 0
+
+
+def run_batched(args):
+    """Batched multi-modular fgemm: instances with m, n, k log-uniform in
+    [16, 1024], one integer matrix pair per instance (entries in [-2^20, 2^20])
+    reduced modulo each of the 32 primes just below 2^31, all through one
+    ffgpu_fgemm_batched call.  Effective GOPS = sum 2mnk / t."""
+    import torch
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+    count = int(os.environ.get("FFGPU_BATCH_INSTANCES", "1024"))
+    shapes, primes = W.multimodular_instances(count=count, nprimes=32)
+    problems, flops = [], 0.0
+    for i, (m, n, k) in enumerate(shapes):
+        Ai, Bi = W.multimodular_integers(i, int(m), int(n), int(k))
+        dAi = torch.from_numpy(Ai).cuda()
+        dBi = torch.from_numpy(Bi).cuda()
+        for p in primes:  # per-prime residues prepared on the device (input preparation)
+            dA = torch.remainder(dAi, p).to(torch.int32)
+            dB = torch.remainder(dBi, p).to(torch.int32)
+            dC = torch.zeros((int(m), int(n)), dtype=torch.int32, device="cuda")
+            problems.append((dA, dB, dC, p, 1, 0))
+            flops += 2.0 * m * n * k
+    ms = time_call(lambda: ff.fgemm_batched(problems), torch, 3, 1)
+    print(json.dumps({"workload": "batched", "instances": count, "primes": len(primes),
+                      "fgemms": len(problems), "ms": ms, "GOPS": flops / (ms / 1e3) / 1e9}), flush=True)
+    return 0
+
+
 def run_serve_full(args):
     from paper_cs_0601133_gb300 import serving
     r = serving.serve_benchmark(n_requests=2000, fracs=(0.5, 0.8, 0.95), streams=4)
@@ -452,6 +509,10 @@ def main():
         return run_precision(args)
     if args.workload == "serve":
         return run_serve_full(args)
+    if args.workload == "ftrsm":
+        return run_ftrsm(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_own(args)
 
 

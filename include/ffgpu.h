@@ -103,6 +103,37 @@ FFGPU_API ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t 
                                       uint32_t beta, uint32_t* C, int64_t ldc, const ffgpu_options* opt,
                                       void* stream);
 
+/*
+ * Autotuner (the paper tunes its Winograd threshold experimentally, section
+ * 3.2.1, and names self-adapting thresholds as further development, section
+ * 7).  For a problem shape (bucketed to multiples of 256), modulus class
+ * (number of channels) and path, ffgpu_autotune times every candidate
+ * configuration on the device (tensor-core kernel variant, Winograd levels,
+ * chunk length) on scratch data it allocates, and stores the fastest in an
+ * in-memory plan cache.  ffgpu_fgemm_auto computes like ffgpu_fgemm_ex with the
+ * cached plan (tuning first on a miss).  The cache can be saved to and loaded
+ * from a JSON file.  Results never depend on the plan (every plan is exact).
+ */
+typedef struct {
+    int32_t kernel;            /* 0 = one-CTA 128x256 tiles, 1 = CTA-pair 256x256 tiles */
+    int32_t winograd_levels;
+    int32_t chunk_steps;       /* 64-long k-steps between in-place reductions */
+    int32_t reserved[5];
+    double ms;                 /* measured time of the plan */
+} ffgpu_tuned;
+
+FFGPU_API ffgpu_status ffgpu_autotune(int64_t m, int64_t n, int64_t k, uint32_t p, int path, void* stream,
+                                      ffgpu_tuned* out);
+/* FFGPU_OK and *out if the cache holds a plan for the problem's bucket, else FFGPU_ERR_INVALID. */
+FFGPU_API ffgpu_status ffgpu_autotune_lookup(int64_t m, int64_t n, int64_t k, uint32_t p, int path,
+                                             ffgpu_tuned* out);
+FFGPU_API ffgpu_status ffgpu_autotune_save(const char* json_path);
+FFGPU_API ffgpu_status ffgpu_autotune_load(const char* json_path);
+FFGPU_API ffgpu_status ffgpu_autotune_clear(void);
+FFGPU_API ffgpu_status ffgpu_fgemm_auto(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                                        const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                                        uint32_t beta, uint32_t* C, int64_t ldc, int path, void* stream);
+
 /* Bytes of device workspace ffgpu_fgemm_ws needs for this problem. */
 FFGPU_API ffgpu_status ffgpu_fgemm_workspace_size(int64_t m, int64_t n, int64_t k, uint32_t p,
                                         size_t* bytes);

@@ -6,8 +6,10 @@ draws the seeded synthetic inputs.
 """
 from .ffgpu import (FFGPUError, fgemm, fgemm_noalloc_ptr, fgemm_plan, fgemm_ptr, fgemm_workspace_size, fgemm_ws, ftrsm,
                     fgemm_batched, fgemm_ex, Server, selftest_wait_timeout,
+                    autotune, autotune_lookup, autotune_save, autotune_load, autotune_clear, fgemm_auto,
                     profile_enable, profile_read,
                     last_device_error, lib, release_workspaces, status_string, version)
 
-__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex", "Server", "selftest_wait_timeout",
+__all__ = ["FFGPUError", "fgemm", "fgemm_noalloc_ptr", "fgemm_plan", "fgemm_ptr", "fgemm_workspace_size", "fgemm_ws", "ftrsm", "fgemm_batched", "fgemm_ex", "Server", "selftest_wait_timeout", "autotune", "autotune_lookup", "autotune_save",
+           "autotune_load", "autotune_clear", "fgemm_auto",
            "last_device_error", "lib", "release_workspaces", "status_string", "version"]

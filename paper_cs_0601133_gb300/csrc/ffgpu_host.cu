@@ -89,6 +89,8 @@ int chunk_steps_for(const RnsPlan& pl) {
         const long long want = std::atoll(e);
         if (want >= 1 && (unsigned long long)want < steps) steps = (unsigned long long)want;
     }
+    if (g_tune_override.chunk_steps > 0 && (unsigned long long)g_tune_override.chunk_steps < steps)
+        steps = (unsigned long long)g_tune_override.chunk_steps;
     return (int)steps;
 }
 
@@ -254,9 +256,11 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
 // Kernel choice: the CTA-pair kernel for problems with more than one 128-row
 // block (and a grid of at least one pair); FFGPU_KERNEL=single|pair forces one.
 bool use_pair_kernel(int64_t m, int grid) {
+    if (g_tune_override.kernel == 0) return false;
     const char* f = std::getenv("FFGPU_KERNEL");
     if (f && std::strcmp(f, "single") == 0) return false;
     if (grid < 2 || rns_gemm_pair_max_clusters() < 1) return false;
+    if (g_tune_override.kernel == 1) return true;
     if (f && std::strcmp(f, "pair") == 0) return true;
     return m > kTileM;
 }

@@ -144,6 +144,14 @@ cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaSt
 cudaError_t launch_rns_gemm_pair(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
                                  int grid, cudaStream_t s);
 bool use_pair_kernel(int64_t m, int grid);
+
+// Autotuner overrides for the calling thread (autotune.cu): kernel 0 = one-CTA,
+// 1 = CTA pair, -1 = default choice; chunk_steps > 0 caps the chunk length.
+struct TuneOverride {
+    int kernel = -1;
+    int chunk_steps = 0;
+};
+extern thread_local TuneOverride g_tune_override;
 int rns_gemm_pair_max_clusters();
 size_t rns_gemm_smem_bytes();
 

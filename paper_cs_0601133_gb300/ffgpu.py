@@ -76,6 +76,11 @@ class ServerStats(ctypes.Structure):
                                                "used_bytes")]
 
 
+class Tuned(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("winograd_levels", ctypes.c_int32),
+                ("chunk_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5), ("ms", ctypes.c_double)]
+
+
 class FgemmDesc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
                 ("p", ctypes.c_uint32), ("alpha", ctypes.c_uint32), ("beta", ctypes.c_uint32),
@@ -109,6 +114,12 @@ SIGNATURES = {
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_selftest_wait_timeout": [_I64, _VP],
+    "ffgpu_autotune": [_I64, _I64, _I64, _U32, _I32, _VP, ctypes.POINTER(Tuned)],
+    "ffgpu_autotune_lookup": [_I64, _I64, _I64, _U32, _I32, ctypes.POINTER(Tuned)],
+    "ffgpu_autotune_save": [ctypes.c_char_p],
+    "ffgpu_autotune_load": [ctypes.c_char_p],
+    "ffgpu_autotune_clear": [],
+    "ffgpu_fgemm_auto": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _I32, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
 }
@@ -349,3 +360,51 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _tuned(t: "Tuned") -> dict:
+    return dict(kernel=("single", "pair")[t.kernel] if t.kernel in (0, 1) else t.kernel,
+                winograd_levels=t.winograd_levels, chunk_steps=t.chunk_steps, ms=t.ms)
+
+
+def autotune(m: int, n: int, k: int, p: int, path: str = "rns", stream=None) -> dict:
+    """Time the candidate plans for this problem class on the device; cache and return the best."""
+    t = Tuned()
+    check(lib().ffgpu_autotune(m, n, k, p, PATHS[path], _stream_ptr(stream), ctypes.byref(t)), "autotune")
+    return _tuned(t)
+
+
+def autotune_lookup(m: int, n: int, k: int, p: int, path: str = "rns"):
+    """The cached plan for this problem class, or None."""
+    t = Tuned()
+    if lib().ffgpu_autotune_lookup(m, n, k, p, PATHS[path], ctypes.byref(t)) != 0:
+        return None
+    return _tuned(t)
+
+
+def autotune_save(path: str) -> None:
+    check(lib().ffgpu_autotune_save(path.encode()), "autotune_save")
+
+
+def autotune_load(path: str) -> None:
+    check(lib().ffgpu_autotune_load(path.encode()), "autotune_load")
+
+
+def autotune_clear() -> None:
+    check(lib().ffgpu_autotune_clear(), "autotune_clear")
+
+
+def fgemm_auto(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "rns", stream=None):
+    """fgemm with the autotuned plan for its problem class (tuning on a cache miss)."""
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    if C is None:
+        C = torch.zeros((m, n), dtype=torch.uint32, device=A.device)
+        beta = 0
+    a, lda = _mat(A, "A")
+    b, ldb = _mat(B, "B")
+    c, ldc = _mat(C, "C")
+    check(lib().ffgpu_fgemm_auto(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
+                                 PATHS[path], _stream_ptr(stream)), "ffgpu_fgemm_auto")
+    return C
