@@ -45,7 +45,10 @@ constexpr uint32_t kBBytes = kTileN * kTileK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
-constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + 256;
+// reconstruction tables of the combine warps (see combine_block): per channel
+// and residue value, b*(M/m_c) mod p and b/m_c
+constexpr size_t kTabBytes = size_t(kMaxChannels) * 256 * 8;
+constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kTabBytes + 256;
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
     const int per_group = kGroupM * tiles_n;
@@ -78,91 +81,137 @@ __device__ __forceinline__ uint32_t f32_residue(float x, float m, float inv_m, i
     return (uint32_t)r;
 }
 
-// Reconstruction of X mod p for four adjacent outputs from their residues
-// (w[c] holds the four residues of channel c, one per byte).  With
-// M = prod m_c and b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c) - q M
-// where q = round(sum_c b_c / m_c), valid because the plan guarantees
-// |X| <= M/4 (the fraction is within 1/4 of an integer, far above f32 error).
-__device__ __forceinline__ void crt4(const InstInfo& I, const uint32_t (&w)[kMaxChannels], uint32_t (&X)[4]) {
-    unsigned long long S[4] = {0ull, 0ull, 0ull, 0ull};
-    float G[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int c = 0; c < kMaxChannels; ++c) {
-        if (c < I.nch) {
-            const uint32_t uc = I.u[c], mc = I.modu[c], Wc = I.W[c];
-            const float im = I.inv_m[c];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int t = (int)(((w[c] >> (8 * e)) & 255u) * uc);
-                const int qf = (int)floorf((float)t * im);
-                int b = t - qf * (int)mc;
-                if (b < 0) b += (int)mc;
-                if (b >= (int)mc) b -= (int)mc;
-                G[e] = fmaf((float)b, im, G[e]);
-                S[e] += (unsigned long long)b * Wc;
+// Reconstruction of X mod p from the residues r_c of the channels, and the C
+// update, for the 128 x 256 block of one CTA.  With M = prod m_c and
+// b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c) - q M where
+// q = round(sum_c b_c / m_c), valid because the plan guarantees |X| <= M/4 (the
+// fraction is within 1/4 of an integer, far above f32 error); then X mod p =
+// (sum_c b_c (M/m_c mod p) + q (p - M mod p)) mod p in 64-bit integers.
+// b_c depends on r_c only, so for every channel the combine warps tabulate,
+// for each of the 256 residue values, tabW = b_c (M/m_c mod p) mod p and
+// tabF = b_c / m_c in shared memory (rebuilt when the tile's instance
+// changes); an output then costs two table reads and two additions per
+// channel.  Done by one of the kCombineWarps combine warps: warp cw takes rows
+// [32 cw, 32 cw + 32); the lanes of a warp cover 128 consecutive columns (4
+// each), so the residue loads (128 B per channel) and the C accesses (512 B)
+// are coalesced; a thread handles kCombineRows x 4 outputs at a time.
+constexpr int kCombineWarps = 4;
+constexpr int kCombineRows = 4;
+
+struct CombTables {
+    uint32_t w[kMaxChannels][256];
+    float f[kMaxChannels][256];
+};
+
+// Builds the tables of instance I (all combine warps, then a barrier among them).
+__device__ __forceinline__ void build_tables(const InstInfo& I, CombTables* T, int tid) {
+    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
+    if (!I.direct) {
+        for (int idx = tid; idx < I.nch * 256; idx += kCombineWarps * 32) {
+            const int c = idx >> 8, r = idx & 255;
+            const uint32_t m = I.modu[c];
+            if ((uint32_t)r < m) {
+                const uint32_t b = (uint32_t)((r * I.u[c]) % m);
+                T->w[c][r] = mod_u64((unsigned long long)b * I.W[c], I.p, I.mu);
+                T->f[c][r] = (float)b / (float)m;
             }
         }
     }
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const unsigned long long q = (unsigned long long)rintf(G[e]);
-        X[e] = mod_u64(S[e] + q * I.negMp, I.p, I.mu);
-    }
+    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
 }
 
-// Reconstruction and C update for the 128 x 256 block of one CTA, by one of
-// the kCombineWarps combine warps: warp cw takes rows [32 cw, 32 cw + 32); the
-// lanes of a warp cover 128 consecutive columns (4 each), so the residue loads
-// (128 B per channel) and the C accesses (512 B) are coalesced, and the loads of
-// all channels are issued before any arithmetic.
-constexpr int kCombineWarps = 4;
-
-__device__ __forceinline__ void combine_block(const InstInfo& I, int row0, int col0, const unsigned char* slot,
-                                              size_t chan_stride, int cw, int lane) {
-    for (int r = cw * 32; r < cw * 32 + 32; ++r) {
-        const int row = row0 + r;
-        if (row >= I.m) break;
-        uint32_t* crow = I.C + (long long)row * I.ldc;
+__device__ __forceinline__ void combine_block(const InstInfo& I, const CombTables* T, int row0, int col0,
+                                              const unsigned char* slot, size_t chan_stride, int cw, int lane) {
+    const int nch = I.nch, m = I.m, n = I.n;
+    const uint32_t p = I.p, negMp = I.negMp, alpha = I.alpha, beta = I.beta;
+    const unsigned long long mu = I.mu;
+    const bool direct = I.direct != 0, vec_ok = I.vec_ok != 0;
+    uint32_t* const C = I.C;
+    const long long ldc = I.ldc;
+#pragma unroll 1
+    for (int rg = cw * 32; rg < cw * 32 + 32; rg += kCombineRows) {
+        if (row0 + rg >= m) break;
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             const int lc = pass * 128 + 4 * lane;
             const int col = col0 + lc;
-            if (col >= I.n) continue;
-            const unsigned char* src = slot + size_t(r) * kTileN + lc;
-            uint32_t w[kMaxChannels];
+            if (col >= n) continue;
+            const bool full4 = col + 3 < n;
+            const unsigned char* src = slot + size_t(rg) * kTileN + lc;
+            uint32_t old[kCombineRows][4];
+            unsigned long long S[kCombineRows][4];
+            float G[kCombineRows][4];
 #pragma unroll
-            for (int c = 0; c < kMaxChannels; ++c)
-                w[c] = c < I.nch ? *reinterpret_cast<const uint32_t*>(src + size_t(c) * chan_stride) : 0u;
-            uint32_t X[4];
-            if (I.direct) {
+            for (int rr = 0; rr < kCombineRows; ++rr) {
+                const bool rok = row0 + rg + rr < m;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) X[e] = (w[0] >> (8 * e)) & 255u;
-            } else {
-                crt4(I, w, X);
+                for (int e = 0; e < 4; ++e) {
+                    old[rr][e] = 0u;
+                    S[rr][e] = 0ull;
+                    G[rr][e] = 0.f;
+                }
+                if (rok && beta != 0) {
+                    const uint32_t* crow = C + (long long)(row0 + rg + rr) * ldc;
+                    if (full4 && vec_ok) {
+                        const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
+                        old[rr][0] = v.x; old[rr][1] = v.y; old[rr][2] = v.z; old[rr][3] = v.w;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (col + e < n) old[rr][e] = crow[col + e];
+                    }
+                }
             }
-            const bool full4 = col + 3 < I.n;
-            uint32_t old[4] = {0u, 0u, 0u, 0u};
-            if (I.beta != 0) {
-                if (full4 && I.vec_ok) {
-                    const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
-                    old[0] = v.x; old[1] = v.y; old[2] = v.z; old[3] = v.w;
+            if (direct) {
+#pragma unroll
+                for (int rr = 0; rr < kCombineRows; ++rr) {
+                    const uint32_t w = *reinterpret_cast<const uint32_t*>(src + size_t(rr) * kTileN);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) S[rr][e] = (w >> (8 * e)) & 255u;
+                }
+            } else {
+#pragma unroll 1
+                for (int c = 0; c < nch; ++c) {
+                    uint32_t w[kCombineRows];
+#pragma unroll
+                    for (int rr = 0; rr < kCombineRows; ++rr)
+                        w[rr] = *reinterpret_cast<const uint32_t*>(src + size_t(c) * chan_stride + size_t(rr) * kTileN);
+                    const uint32_t* tw = T->w[c];
+                    const float* tf = T->f[c];
+#pragma unroll
+                    for (int rr = 0; rr < kCombineRows; ++rr)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t r = (w[rr] >> (8 * e)) & 255u;
+                            S[rr][e] += tw[r];
+                            G[rr][e] += tf[r];
+                        }
+                }
+            }
+#pragma unroll 1
+            for (int rr = 0; rr < kCombineRows; ++rr) {
+                const int row = row0 + rg + rr;
+                if (row >= m) continue;
+                uint32_t out[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    uint32_t X;
+                    if (direct) {
+                        X = (uint32_t)S[rr][e];
+                    } else {
+                        const unsigned long long q = (unsigned long long)rintf(G[rr][e]);
+                        X = mod_u64(S[rr][e] + q * negMp, p, mu);
+                    }
+                    out[e] = mod_u64((unsigned long long)alpha * X + (unsigned long long)beta * old[rr][e], p, mu);
+                }
+                uint32_t* crow = C + (long long)row * ldc;
+                if (full4 && vec_ok) {
+                    *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
-                        if (col + e < I.n) old[e] = crow[col + e];
+                        if (col + e < n) crow[col + e] = out[e];
                 }
-            }
-            uint32_t out[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                out[e] = mod_u64((unsigned long long)I.alpha * X[e] + (unsigned long long)I.beta * old[e], I.p,
-                                 I.mu);
-            if (full4 && I.vec_ok) {
-                *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (col + e < I.n) crow[col + e] = out[e];
             }
         }
     }
@@ -241,7 +290,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kStages * kABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kStages * kBBytes);
+    CombTables* tabs = reinterpret_cast<CombTables*>(sB + kStages * kBBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tabs) + kTabBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* acc_full = bars + 2 * kStages;
@@ -486,13 +536,19 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         const size_t sstride = S.slot_stride();
         unsigned char* slot_base = S.slots() + size_t(blockIdx.x) * 2 * sstride;
         uint32_t sfp[2] = {0u, 0u};
+        const InstInfo* loaded = nullptr;
         for (int j = 0; j < J; ++j) {
             Job d;
             S.job(j, d);
             if (d.c != d.inst->nch - 1) continue;  // one reconstruction per tile
+            if (d.inst != loaded) {
+                // every combine warp is done with the previous tables (barrier inside)
+                build_tables(*d.inst, tabs, cw * 32 + lane);
+                loaded = d.inst;
+            }
             if (!mbar_wait(&slot_full[d.slot], sfp[d.slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[d.slot] ^= 1u;
-            combine_block(*d.inst, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+            combine_block(*d.inst, tabs, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
                           size_t(kTileM) * kTileN, cw, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[d.slot]);
@@ -535,7 +591,7 @@ constexpr int kPStages = 6;
 constexpr uint32_t kPABytes = 128 * kTileK * 2;
 constexpr uint32_t kPBBytes = 128 * kTileK * 2;
 constexpr uint32_t kPStageBytes = kPABytes + kPBBytes;
-constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + 256;
+constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + kTabBytes + 256;
 constexpr int kPairTile = 256;
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -546,7 +602,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kPStages * kPABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sB + kPStages * kPBBytes);
+    CombTables* tabs = reinterpret_cast<CombTables*>(sB + kPStages * kPBBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tabs) + kTabBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kPStages;
     uint64_t* acc_full = bars + 2 * kPStages;
@@ -785,6 +842,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cw = warp - kFirstCombineWarp;
         unsigned char* slot_base = P.slots + size_t(blockIdx.x) * 2 * P.slot_stride;
         uint32_t sfp[2] = {0u, 0u};
+        if (my_tiles > 0) build_tables(I, tabs, cw * 32 + lane);
         for (int ti = 0; ti < my_tiles; ++ti) {
             const int slot = ti & 1;
             if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;
@@ -792,7 +850,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int tm, tn;
             tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
-            combine_block(I, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
+            combine_block(I, tabs, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
                           size_t(kTileM) * kTileN, cw, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[slot]);
