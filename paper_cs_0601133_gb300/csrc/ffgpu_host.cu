@@ -53,6 +53,9 @@ void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
         pl.mode = 1;
         pl.nch = 1;
         pl.mod[0] = p;
+        pl.u[0] = 1;  // M = p: X = b_0 - q p, so the general reconstruction applies with
+        pl.W[0] = 1;  // M/m_0 = 1 and M mod p = 0
+        pl.negMp = 0;
         pl.k_slice = INT64_MAX;
         return;
     }
@@ -240,16 +243,22 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
     I.p = pl.p;
     I.alpha = al;
     I.beta = be;
-    I.negMp = pl.negMp;
-    I.mu = barrett_mu(pl.p);
+    const unsigned long long p = pl.p;
+    I.negMpa = (uint32_t)((unsigned long long)al * pl.negMp % p);
+    I.R32 = (uint32_t)((1ull << 32) % p);
+    I.R32s = (uint32_t)(((unsigned long long)I.R32 << 32) / p);
+    I.one_s = (uint32_t)((1ull << 32) / p);
+    I.beta_s = (uint32_t)(((unsigned long long)be << 32) / p);
     I.C = C;
     I.ldc = ldc;
     for (int c = 0; c < pl.nch; ++c) {
-        I.modf[c] = (float)pl.mod[c];
-        I.inv_m[c] = 1.0f / (float)pl.mod[c];
-        I.modu[c] = pl.mod[c];
+        const uint32_t m = pl.mod[c];
+        I.modf[c] = (float)m;
+        I.inv_m[c] = 1.0f / (float)m;
+        I.modu[c] = m;
         I.u[c] = pl.u[c];
-        I.W[c] = pl.W[c];
+        I.Wa[c] = (uint32_t)((unsigned long long)al * pl.W[c] % p);
+        I.fr[c] = ((1u << 14) + m / 2) / m;
     }
 }
 

@@ -58,8 +58,10 @@ struct InstInfo {
     int vec_ok;                    // 16-byte vector access to C is legal
     uint32_t p;
     uint32_t alpha, beta;          // reduced mod p
-    uint32_t negMp;
-    unsigned long long mu;         // floor((2^64-1)/p)
+    uint32_t negMpa;               // alpha * (p - M mod p) mod p
+    uint32_t R32, R32s;            // 2^32 mod p and its Shoup quotient floor(R32 2^32 / p)
+    uint32_t one_s;                // floor(2^32 / p): Shoup quotient of 1
+    uint32_t beta_s;               // floor(beta 2^32 / p)
     uint32_t* C;
     long long ldc;
     int bucket;                    // grouped launch: tensor-map pair of this instance
@@ -67,8 +69,9 @@ struct InstInfo {
     float modf[kMaxChannels];
     float inv_m[kMaxChannels];
     uint32_t modu[kMaxChannels];
-    uint32_t u[kMaxChannels];
-    uint32_t W[kMaxChannels];
+    uint32_t u[kMaxChannels];      // (M/m_c)^{-1} mod m_c (1 in direct mode)
+    uint32_t Wa[kMaxChannels];     // alpha * (M/m_c) mod p
+    uint32_t fr[kMaxChannels];     // round(2^14 / m_c): fixed-point weight of b_c / m_c
 };
 
 // Parameters of the single-instance tensor-core kernel (passed by value).

@@ -13,15 +13,18 @@
 // gamma = 24).  After each chunk of that length the epilogue warps reduce the
 // accumulator mod m_c in place (tcgen05.ld -> fma -> tcgen05.st) and the MMAs
 // continue on top of it.
-// After the last chunk each channel yields S mod m_c; the last channel of a
-// tile triggers the reconstruction of S mod p from all residues (Chinese
-// remainder theorem, the multi-modular route to p > 2^26 the paper lists as
-// future work in section 7), then C = (alpha*S + beta*C) mod p.
+// After the last chunk each channel yields its CRT digit b_c (S mod m_c times
+// (M/m_c)^{-1} mod m_c, one byte per entry, written to a per-CTA residue slot);
+// the last channel of a tile hands the slot to the combine warps, which
+// reconstruct S mod p from all digits (Chinese remainder theorem, the
+// multi-modular route to p > 2^26 the paper lists as future work in section 7)
+// and write C = (alpha*S + beta*C) mod p.
 //
 // Roles (one CTA per SM, persistent over tiles):
 //   warp 0      TMA producer: channel tiles of A (128x64) and B (256x64), 4 stages
 //   warp 1      TMEM allocator and single-thread MMA issuer (M=128, N=256, K=16)
 //   warps 2..9  epilogue: lane quarter (warp % 4) x column half ((warp-2) / 4)
+//   warps 10-13 combine: reconstruction of the previous tile (two residue slots)
 // Two 256-column accumulators: the jobs (tile, channel) of a CTA are paired and
 // their chunks interleaved, so one accumulator is reduced while the tensor
 // cores fill the other.
@@ -45,10 +48,9 @@ constexpr uint32_t kBBytes = kTileN * kTileK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
-// reconstruction tables of the combine warps (see combine_block): per channel
-// and residue value, b*(M/m_c) mod p and b/m_c
-constexpr size_t kTabBytes = size_t(kMaxChannels) * 256 * 8;
-constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kTabBytes + 256;
+// per-instance constants of the combine warps (see stage_consts)
+constexpr size_t kConstBytes = size_t(kMaxChannels) * 8;
+constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kConstBytes + 256;
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
     const int per_group = kGroupM * tiles_n;
@@ -72,149 +74,165 @@ __device__ __forceinline__ void mbar_drain_wait(uint64_t* bar, uint32_t parity, 
     }
 }
 
-// Exact residue in [0, m) of an f32 holding an integer of magnitude < 2^24.
-__device__ __forceinline__ uint32_t f32_residue(float x, float m, float inv_m, int mi) {
-    const float q = rintf(x * inv_m);
-    int r = (int)fmaf(-q, m, x);
-    if (r < 0) r += mi;
-    if (r >= mi) r -= mi;
-    return (uint32_t)r;
+// CRT digit of one accumulator entry: with r = x mod m_c (x an f32 integer,
+// |x| < 2^24), b = r u_c mod m_c, returned as the f32 bit pattern of 2^23 + b,
+// whose low byte is b.  b lands in [0, m_c]: floor() of the rounded quotient
+// may give m_c in place of 0 for an exact multiple, a representative the
+// reconstruction accepts (b_c and b_c + m_c change sum_c b_c/m_c by exactly 1,
+// so the rounded quotient q absorbs it).  Exactness: |r| <= 129, so r u_c and
+// 2^23 + r u_c (|r u_c| < 2^15) are exact in f32; the quotient r u_c / m_c is
+// below 166 in magnitude and is computed with relative error < 2^-22, far
+// inside the 1/m_c gap to the next integer.
+__device__ __forceinline__ uint32_t crt_digit_bits(float x, float mf, float im, float uf, float uim) {
+    const float r = fmaf(-rintf(x * im), mf, x);
+    const float fl = floorf(r * uim);
+    return __float_as_uint(fmaf(-fl, mf, fmaf(r, uf, 8388608.f)));
 }
 
-// Reconstruction of X mod p from the residues r_c of the channels, and the C
-// update, for the 128 x 256 block of one CTA.  With M = prod m_c and
-// b_c = r_c * (M/m_c)^{-1} mod m_c, X = sum_c b_c (M/m_c) - q M where
-// q = round(sum_c b_c / m_c), valid because the plan guarantees |X| <= M/4 (the
-// fraction is within 1/4 of an integer, far above f32 error); then X mod p =
-// (sum_c b_c (M/m_c mod p) + q (p - M mod p)) mod p in 64-bit integers.
-// b_c depends on r_c only, so for every channel the combine warps tabulate,
-// for each of the 256 residue values, tabW = b_c (M/m_c mod p) mod p and
-// tabF = b_c / m_c in shared memory (rebuilt when the tile's instance
-// changes); an output then costs two table reads and two additions per
-// channel.  Done by one of the kCombineWarps combine warps: warp cw takes rows
-// [32 cw, 32 cw + 32); the lanes of a warp cover 128 consecutive columns (4
-// each), so the residue loads (128 B per channel) and the C accesses (512 B)
-// are coalesced; a thread handles kCombineRows x 4 outputs at a time.
-constexpr int kCombineWarps = 4;
-constexpr int kCombineRows = 4;
+// Low bytes of four digit patterns, packed.
+__device__ __forceinline__ uint32_t pack_digits(uint32_t d0, uint32_t d1, uint32_t d2, uint32_t d3) {
+    return __byte_perm(__byte_perm(d0, d1, 0x0040u), __byte_perm(d2, d3, 0x0040u), 0x5410u);
+}
 
-struct CombTables {
-    uint32_t w[kMaxChannels][256];
-    float f[kMaxChannels][256];
+// [0, 2p) -> [0, p) (unsigned wrap-around makes t - p huge when t < p).
+__device__ __forceinline__ uint32_t fold_p(uint32_t t, uint32_t p) { return min(t, t - p); }
+
+// x w mod p up to one p (result in [0, 2p)) for any x < 2^32 and w < p < 2^31,
+// given ws = floor(w 2^32 / p): Shoup's precomputed-quotient product, all in
+// 32-bit arithmetic (x w / p - floor(x ws / 2^32) lies in [0, 2)).
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p) {
+    return x * w - __umulhi(x, ws) * p;
+}
+
+// Reconstruction of alpha X + beta C mod p from the CRT digits, for the
+// 128 x 256 block of one CTA.  With M = prod m_c and b_c = r_c (M/m_c)^{-1}
+// mod m_c (the epilogue stores b_c, see crt_digit_bits), X = sum_c b_c M/m_c
+// - q M where q = round(sum_c b_c / m_c), valid because the plan guarantees
+// |X| <= M/4.  q comes from a 14-bit fixed-point sum F = sum_c b_c fr_c with
+// fr_c = round(2^14/m_c): each term is off by at most 255/2 units of 2^-14,
+// twelve of them by < 0.1, so F / 2^14 stays within 0.35 of q.  Then
+// alpha X mod p = (sum_c b_c Wa_c + q negMpa) mod p with Wa_c = alpha (M/m_c)
+// mod p and negMpa = alpha (-M) mod p: a 64-bit sum Y < 2^44 accumulated with
+// one wide multiply-add per channel, reduced as Y_hi (2^32 mod p) + Y_lo with
+// Shoup products; beta C mod p likewise.  Per output and channel: one byte
+// extraction and two integer multiply-adds.
+//
+// Done by the kCombineWarps combine warps: warp cw takes rows cw, cw + 4, ...;
+// lane l takes columns [8 l, 8 l + 8), so a warp reads 256 contiguous digit
+// bytes per channel and row and 1 KB of C.  The next row's digits and C entries
+// are loaded while the current row is reduced (two register buffers).
+constexpr int kCombineWarps = 4;
+
+struct CombRow {
+    uint2 w[kMaxChannels];  // digits of columns 8l .. 8l+7, per channel
+    uint32_t o[8];          // the old entries of C
 };
 
-// Builds the tables of instance I (all combine warps, then a barrier among them).
-__device__ __forceinline__ void build_tables(const InstInfo& I, CombTables* T, int tid) {
-    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
-    if (!I.direct) {
-        for (int idx = tid; idx < I.nch * 256; idx += kCombineWarps * 32) {
-            const int c = idx >> 8, r = idx & 255;
-            const uint32_t m = I.modu[c];
-            if ((uint32_t)r < m) {
-                const uint32_t b = (uint32_t)((r * I.u[c]) % m);
-                T->w[c][r] = mod_u64((unsigned long long)b * I.W[c], I.p, I.mu);
-                T->f[c][r] = (float)b / (float)m;
-            }
+__device__ __forceinline__ void comb_load(const unsigned char* src, size_t chan_stride, int nch,
+                                          const uint32_t* crow, int col, int n, bool full8, bool ldo,
+                                          CombRow& R) {
+#pragma unroll
+    for (int c = 0; c < kMaxChannels; ++c)
+        if (c < nch) R.w[c] = *reinterpret_cast<const uint2*>(src + size_t(c) * chan_stride);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) R.o[e] = 0u;
+    if (ldo) {
+        if (full8) {
+            const uint4 v0 = *reinterpret_cast<const uint4*>(crow + col);
+            const uint4 v1 = *reinterpret_cast<const uint4*>(crow + col + 4);
+            R.o[0] = v0.x; R.o[1] = v0.y; R.o[2] = v0.z; R.o[3] = v0.w;
+            R.o[4] = v1.x; R.o[5] = v1.y; R.o[6] = v1.z; R.o[7] = v1.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if (col + e < n) R.o[e] = crow[col + e];
         }
     }
-    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
 }
 
-__device__ __forceinline__ void combine_block(const InstInfo& I, const CombTables* T, int row0, int col0,
-                                              const unsigned char* slot, size_t chan_stride, int cw, int lane) {
-    const int nch = I.nch, m = I.m, n = I.n;
-    const uint32_t p = I.p, negMp = I.negMp, alpha = I.alpha, beta = I.beta;
-    const unsigned long long mu = I.mu;
-    const bool direct = I.direct != 0, vec_ok = I.vec_ok != 0;
-    uint32_t* const C = I.C;
-    const long long ldc = I.ldc;
-#pragma unroll 1
-    for (int rg = cw * 32; rg < cw * 32 + 32; rg += kCombineRows) {
-        if (row0 + rg >= m) break;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            const int lc = pass * 128 + 4 * lane;
-            const int col = col0 + lc;
-            if (col >= n) continue;
-            const bool full4 = col + 3 < n;
-            const unsigned char* src = slot + size_t(rg) * kTileN + lc;
-            uint32_t old[kCombineRows][4];
-            unsigned long long S[kCombineRows][4];
-            float G[kCombineRows][4];
+__device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int nch, const CombRow& R,
+                                         uint32_t* crow, int col, int n, bool full8) {
+    unsigned long long S[8];
+    uint32_t F[8];
 #pragma unroll
-            for (int rr = 0; rr < kCombineRows; ++rr) {
-                const bool rok = row0 + rg + rr < m;
+    for (int e = 0; e < 8; ++e) {
+        S[e] = 0ull;
+        F[e] = 0u;
+    }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    old[rr][e] = 0u;
-                    S[rr][e] = 0ull;
-                    G[rr][e] = 0.f;
-                }
-                if (rok && beta != 0) {
-                    const uint32_t* crow = C + (long long)(row0 + rg + rr) * ldc;
-                    if (full4 && vec_ok) {
-                        const uint4 v = *reinterpret_cast<const uint4*>(crow + col);
-                        old[rr][0] = v.x; old[rr][1] = v.y; old[rr][2] = v.z; old[rr][3] = v.w;
-                    } else {
+    for (int c = 0; c < kMaxChannels; ++c) {
+        if (c < nch) {
+            const uint2 k = kc[c];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (col + e < n) old[rr][e] = crow[col + e];
-                    }
-                }
-            }
-            if (direct) {
-#pragma unroll
-                for (int rr = 0; rr < kCombineRows; ++rr) {
-                    const uint32_t w = *reinterpret_cast<const uint32_t*>(src + size_t(rr) * kTileN);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) S[rr][e] = (w >> (8 * e)) & 255u;
-                }
-            } else {
-#pragma unroll 1
-                for (int c = 0; c < nch; ++c) {
-                    uint32_t w[kCombineRows];
-#pragma unroll
-                    for (int rr = 0; rr < kCombineRows; ++rr)
-                        w[rr] = *reinterpret_cast<const uint32_t*>(src + size_t(c) * chan_stride + size_t(rr) * kTileN);
-                    const uint32_t* tw = T->w[c];
-                    const float* tf = T->f[c];
-#pragma unroll
-                    for (int rr = 0; rr < kCombineRows; ++rr)
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const uint32_t r = (w[rr] >> (8 * e)) & 255u;
-                            S[rr][e] += tw[r];
-                            G[rr][e] += tf[r];
-                        }
-                }
-            }
-#pragma unroll 1
-            for (int rr = 0; rr < kCombineRows; ++rr) {
-                const int row = row0 + rg + rr;
-                if (row >= m) continue;
-                uint32_t out[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    uint32_t X;
-                    if (direct) {
-                        X = (uint32_t)S[rr][e];
-                    } else {
-                        const unsigned long long q = (unsigned long long)rintf(G[rr][e]);
-                        X = mod_u64(S[rr][e] + q * negMp, p, mu);
-                    }
-                    out[e] = mod_u64((unsigned long long)alpha * X + (unsigned long long)beta * old[rr][e], p, mu);
-                }
-                uint32_t* crow = C + (long long)row * ldc;
-                if (full4 && vec_ok) {
-                    *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (col + e < n) crow[col + e] = out[e];
-                }
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t b = __byte_perm(e < 4 ? R.w[c].x : R.w[c].y, 0u, 0x4440u | (uint32_t)(e & 3));
+                S[e] += (unsigned long long)b * k.x;
+                F[e] += b * k.y;
             }
         }
     }
+    const uint32_t p = I.p, negMpa = I.negMpa, R32 = I.R32, R32s = I.R32s, one_s = I.one_s;
+    const uint32_t beta = I.beta, beta_s = I.beta_s;
+    uint32_t out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t q = (F[e] + 8192u) >> 14;
+        const unsigned long long Y = S[e] + (unsigned long long)q * negMpa;
+        const uint32_t t1 = fold_p(mul_shoup((uint32_t)(Y >> 32), R32, R32s, p), p);
+        const uint32_t lo = (uint32_t)Y;
+        const uint32_t t2 = fold_p(lo - __umulhi(lo, one_s) * p, p);
+        const uint32_t x = fold_p(t1 + t2, p);
+        const uint32_t t3 = fold_p(mul_shoup(R.o[e], beta, beta_s, p), p);
+        out[e] = fold_p(x + t3, p);
+    }
+    if (full8) {
+        *reinterpret_cast<uint4*>(crow + col) = make_uint4(out[0], out[1], out[2], out[3]);
+        *reinterpret_cast<uint4*>(crow + col + 4) = make_uint4(out[4], out[5], out[6], out[7]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (col + e < n) crow[col + e] = out[e];
+    }
+}
+
+__device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc, int row0, int col0,
+                                              const unsigned char* slot, size_t chan_stride, int cw, int lane) {
+    const int rows = min(kTileM, I.m - row0);
+    const int n = I.n;
+    const int col = col0 + 8 * lane;
+    if (cw >= rows || col >= n) return;  // nothing below is warp-collective
+    const int nch = I.nch;
+    const bool full8 = (col + 7 < n) && I.vec_ok;
+    const bool ldo = I.beta != 0;
+    const long long ldc = I.ldc;
+    uint32_t* const C = I.C + (long long)row0 * ldc;
+    const unsigned char* const src = slot + 8 * lane;
+    CombRow A, B;
+    int r = cw;
+    comb_load(src + size_t(r) * kTileN, chan_stride, nch, C + r * ldc, col, n, full8, ldo, A);
+#pragma unroll 1
+    while (true) {
+        if (r + kCombineWarps < rows)
+            comb_load(src + size_t(r + kCombineWarps) * kTileN, chan_stride, nch, C + (r + kCombineWarps) * ldc,
+                      col, n, full8, ldo, B);
+        comb_row(I, kc, nch, A, C + r * ldc, col, n, full8);
+        r += kCombineWarps;
+        if (r >= rows) break;
+        if (r + kCombineWarps < rows)
+            comb_load(src + size_t(r + kCombineWarps) * kTileN, chan_stride, nch, C + (r + kCombineWarps) * ldc,
+                      col, n, full8, ldo, A);
+        comb_row(I, kc, nch, B, C + r * ldc, col, n, full8);
+        r += kCombineWarps;
+        if (r >= rows) break;
+    }
+}
+
+// Per-instance constants of the reconstruction, {Wa_c, fr_c}, staged in shared
+// memory by the combine warps (barriers among them on both sides).
+__device__ __forceinline__ void stage_consts(const InstInfo& I, uint2* kc, int tid) {
+    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
+    if (tid < I.nch) kc[tid] = make_uint2(I.Wa[tid], I.fr[tid]);
+    asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
 }
 
 // A job of the kernel: one channel of one output tile of one instance.
@@ -290,8 +308,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kStages * kABytes;
-    CombTables* tabs = reinterpret_cast<CombTables*>(sB + kStages * kBBytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tabs) + kTabBytes);
+    uint2* kc = reinterpret_cast<uint2*>(sB + kStages * kBBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(kc) + kConstBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
     uint64_t* acc_full = bars + 2 * kStages;
@@ -473,7 +491,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     const uint32_t tbase =
                         tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
                     const float mf = I.modf[c], im = I.inv_m[c];
-                    const int mi = (int)I.modu[c];
+                    const float uf = (float)I.u[c], uim = uf * im;
                     if (!last_chunk) {
 #pragma unroll 1
                         for (int cc = 0; cc < 4; ++cc) {
@@ -507,14 +525,11 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                             tc_wait_ld();
                             uint32_t w[8];
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                uint32_t packed = 0;
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    packed |= f32_residue(__uint_as_float(v[4 * i + e]), mf, im, mi)
-                                              << (8 * e);
-                                w[i] = packed;
-                            }
+                            for (int i = 0; i < 8; ++i)
+                                w[i] = pack_digits(crt_digit_bits(__uint_as_float(v[4 * i]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 1]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 2]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 3]), mf, im, uf, uim));
                             uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
                             d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
                             d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -542,13 +557,13 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             S.job(j, d);
             if (d.c != d.inst->nch - 1) continue;  // one reconstruction per tile
             if (d.inst != loaded) {
-                // every combine warp is done with the previous tables (barrier inside)
-                build_tables(*d.inst, tabs, cw * 32 + lane);
+                // every combine warp is done with the previous constants (barrier inside)
+                stage_consts(*d.inst, kc, cw * 32 + lane);
                 loaded = d.inst;
             }
             if (!mbar_wait(&slot_full[d.slot], sfp[d.slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[d.slot] ^= 1u;
-            combine_block(*d.inst, tabs, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+            combine_block(*d.inst, kc, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
                           size_t(kTileM) * kTileN, cw, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[d.slot]);
@@ -591,7 +606,7 @@ constexpr int kPStages = 6;
 constexpr uint32_t kPABytes = 128 * kTileK * 2;
 constexpr uint32_t kPBBytes = 128 * kTileK * 2;
 constexpr uint32_t kPStageBytes = kPABytes + kPBBytes;
-constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + kTabBytes + 256;
+constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + kConstBytes + 256;
 constexpr int kPairTile = 256;
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -602,8 +617,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kPStages * kPABytes;
-    CombTables* tabs = reinterpret_cast<CombTables*>(sB + kPStages * kPBBytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(tabs) + kTabBytes);
+    uint2* kc = reinterpret_cast<uint2*>(sB + kPStages * kPBBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(kc) + kConstBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kPStages;
     uint64_t* acc_full = bars + 2 * kPStages;
@@ -780,7 +795,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t tbase =
                         tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
                     const float mf = I.modf[c], im = I.inv_m[c];
-                    const int mi = (int)I.modu[c];
+                    const float uf = (float)I.u[c], uim = uf * im;
                     if (!last_chunk) {
 #pragma unroll 1
                         for (int cc = 0; cc < 4; ++cc) {
@@ -812,13 +827,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             tc_wait_ld();
                             uint32_t w[8];
 #pragma unroll
-                            for (int i = 0; i < 8; ++i) {
-                                uint32_t packed = 0;
-#pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    packed |= f32_residue(__uint_as_float(v[4 * i + e]), mf, im, mi) << (8 * e);
-                                w[i] = packed;
-                            }
+                            for (int i = 0; i < 8; ++i)
+                                w[i] = pack_digits(crt_digit_bits(__uint_as_float(v[4 * i]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 1]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 2]), mf, im, uf, uim),
+                                                   crt_digit_bits(__uint_as_float(v[4 * i + 3]), mf, im, uf, uim));
                             uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
                             d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
                             d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
@@ -842,7 +855,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cw = warp - kFirstCombineWarp;
         unsigned char* slot_base = P.slots + size_t(blockIdx.x) * 2 * P.slot_stride;
         uint32_t sfp[2] = {0u, 0u};
-        if (my_tiles > 0) build_tables(I, tabs, cw * 32 + lane);
+        if (my_tiles > 0) stage_consts(I, kc, cw * 32 + lane);
         for (int ti = 0; ti < my_tiles; ++ti) {
             const int slot = ti & 1;
             if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;
@@ -850,7 +863,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int tm, tn;
             tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
-            combine_block(I, tabs, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
+            combine_block(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
                           size_t(kTileM) * kTileN, cw, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[slot]);
