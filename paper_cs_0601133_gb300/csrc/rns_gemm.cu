@@ -48,8 +48,9 @@ constexpr uint32_t kBBytes = kTileN * kTileK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
-// per-instance constants of the combine warps (see stage_consts)
-constexpr size_t kConstBytes = size_t(kMaxChannels) * 8;
+// per-instance constants of the reconstruction (see stage_consts): one copy for
+// the combine warps, one per epilogue warp
+constexpr size_t kConstBytes = size_t(1 + kEpiWarps) * kMaxChannels * 8;
 constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kConstBytes + 256;
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
@@ -117,10 +118,12 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 // Shoup products; beta C mod p likewise.  Per output and channel: one byte
 // extraction and two integer multiply-adds.
 //
-// Done by the kCombineWarps combine warps: warp cw takes rows cw, cw + 4, ...;
-// lane l takes columns [8 l, 8 l + 8), so a warp reads 256 contiguous digit
-// bytes per channel and row and 1 KB of C.  The next row's digits and C entries
-// are loaded while the current row is reduced (two register buffers).
+// Done by the kCombineWarps combine warps, joined for a CTA's last tile by the
+// kEpiWarps epilogue warps (then idle): of nw participating warps, warp vw takes
+// rows vw, vw + nw, ...; lane l takes columns [8 l, 8 l + 8), so a warp reads
+// 256 contiguous digit bytes per channel and row and 1 KB of C.  The next
+// row's digits and C entries are loaded while the current row is reduced (two
+// register buffers); the loads are latency-bound, hence the extra warps.
 constexpr int kCombineWarps = 4;
 
 struct CombRow {
@@ -196,11 +199,12 @@ __device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int
 }
 
 __device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc, int row0, int col0,
-                                              const unsigned char* slot, size_t chan_stride, int cw, int lane) {
+                                              const unsigned char* slot, size_t chan_stride, int vw, int nw,
+                                              int lane) {
     const int rows = min(kTileM, I.m - row0);
     const int n = I.n;
     const int col = col0 + 8 * lane;
-    if (cw >= rows || col >= n) return;  // nothing below is warp-collective
+    if (vw >= rows || col >= n) return;  // nothing below is warp-collective
     const int nch = I.nch;
     const bool full8 = (col + 7 < n) && I.vec_ok;
     const bool ldo = I.beta != 0;
@@ -208,23 +212,27 @@ __device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc
     uint32_t* const C = I.C + (long long)row0 * ldc;
     const unsigned char* const src = slot + 8 * lane;
     CombRow A, B;
-    int r = cw;
+    int r = vw;
     comb_load(src + size_t(r) * kTileN, chan_stride, nch, C + r * ldc, col, n, full8, ldo, A);
 #pragma unroll 1
     while (true) {
-        if (r + kCombineWarps < rows)
-            comb_load(src + size_t(r + kCombineWarps) * kTileN, chan_stride, nch, C + (r + kCombineWarps) * ldc,
-                      col, n, full8, ldo, B);
+        if (r + nw < rows)
+            comb_load(src + size_t(r + nw) * kTileN, chan_stride, nch, C + (r + nw) * ldc, col, n, full8, ldo, B);
         comb_row(I, kc, nch, A, C + r * ldc, col, n, full8);
-        r += kCombineWarps;
+        r += nw;
         if (r >= rows) break;
-        if (r + kCombineWarps < rows)
-            comb_load(src + size_t(r + kCombineWarps) * kTileN, chan_stride, nch, C + (r + kCombineWarps) * ldc,
-                      col, n, full8, ldo, A);
+        if (r + nw < rows)
+            comb_load(src + size_t(r + nw) * kTileN, chan_stride, nch, C + (r + nw) * ldc, col, n, full8, ldo, A);
         comb_row(I, kc, nch, B, C + r * ldc, col, n, full8);
-        r += kCombineWarps;
+        r += nw;
         if (r >= rows) break;
     }
+}
+
+// The constants for one warp's own use (an epilogue warp joining a reconstruction).
+__device__ __forceinline__ void stage_consts_warp(const InstInfo& I, uint2* kc, int lane) {
+    if (lane < I.nch) kc[lane] = make_uint2(I.Wa[lane], I.fr[lane]);
+    __syncwarp();
 }
 
 // Per-instance constants of the reconstruction, {Wa_c, fr_c}, staged in shared
@@ -233,6 +241,57 @@ __device__ __forceinline__ void stage_consts(const InstInfo& I, uint2* kc, int t
     asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
     if (tid < I.nch) kc[tid] = make_uint2(I.Wa[tid], I.fr[tid]);
     asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
+}
+
+// Epilogue of one warp on its 32 lanes x 128 columns of an accumulator, two
+// 32-column loads in flight per tensor-memory wait.
+// In-place reduction mod m_c (|result| <= m_c/2 + 1), between chunks.
+__device__ __forceinline__ void epi_reduce(uint32_t tbase, float mf, float im) {
+#pragma unroll 1
+    for (int cc = 0; cc < 4; cc += 2) {
+        uint32_t v[32], v2[32];
+        tc_ld32(tbase + cc * 32, v);
+        tc_ld32(tbase + cc * 32 + 32, v2);
+        tc_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            const float x = __uint_as_float(v[i]);
+            v[i] = __float_as_uint(fmaf(-rintf(x * im), mf, x));
+            const float y = __uint_as_float(v2[i]);
+            v2[i] = __float_as_uint(fmaf(-rintf(y * im), mf, y));
+        }
+        tc_st32(tbase + cc * 32, v);
+        tc_st32(tbase + cc * 32 + 32, v2);
+    }
+    tc_wait_st();
+}
+
+__device__ __forceinline__ void store_digits(const uint32_t* v, float mf, float im, float uf, float uim,
+                                             unsigned char* dst) {
+    uint32_t w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        w[i] = pack_digits(crt_digit_bits(__uint_as_float(v[4 * i]), mf, im, uf, uim),
+                           crt_digit_bits(__uint_as_float(v[4 * i + 1]), mf, im, uf, uim),
+                           crt_digit_bits(__uint_as_float(v[4 * i + 2]), mf, im, uf, uim),
+                           crt_digit_bits(__uint_as_float(v[4 * i + 3]), mf, im, uf, uim));
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// After the last chunk: CRT digits (one byte per entry) to the residue slot.
+__device__ __forceinline__ void epi_digits(uint32_t tbase, float mf, float im, float uf, float uim,
+                                           unsigned char* dst) {
+#pragma unroll 1
+    for (int cc = 0; cc < 4; cc += 2) {
+        uint32_t v[32], v2[32];
+        tc_ld32(tbase + cc * 32, v);
+        tc_ld32(tbase + cc * 32 + 32, v2);
+        tc_wait_ld();
+        store_digits(v, mf, im, uf, uim, dst + cc * 32);
+        store_digits(v2, mf, im, uf, uim, dst + cc * 32 + 32);
+    }
 }
 
 // A job of the kernel: one channel of one output tile of one instance.
@@ -467,6 +526,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         const size_t row_off = size_t(row_local) * kTileN + half * 128;
         uint32_t accp[2] = {0u, 0u};
         uint32_t sep[2] = {0u, 0u};  // slot_empty phases
+        int tiles_on[2] = {0, 0};    // tiles handed to each slot so far
         bool ok = true;
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
@@ -493,20 +553,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     const float mf = I.modf[c], im = I.inv_m[c];
                     const float uf = (float)I.u[c], uim = uf * im;
                     if (!last_chunk) {
-#pragma unroll 1
-                        for (int cc = 0; cc < 4; ++cc) {
-                            uint32_t v[32];
-                            tc_ld32(tbase + cc * 32, v);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                const float x = __uint_as_float(v[i]);
-                                const float qq = rintf(x * im);
-                                v[i] = __float_as_uint(fmaf(-qq, mf, x));
-                            }
-                            tc_st32(tbase + cc * 32, v);
-                        }
-                        tc_wait_st();
+                        epi_reduce(tbase, mf, im);
                     } else {
                         // the tile's first residues: wait until the combine warps released this slot
                         if (c == 0) {
@@ -518,22 +565,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                             sep[d.slot] ^= 1u;
                         }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
-#pragma unroll 1
-                        for (int cc = 0; cc < 4; ++cc) {
-                            uint32_t v[32];
-                            tc_ld32(tbase + cc * 32, v);
-                            tc_wait_ld();
-                            uint32_t w[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                w[i] = pack_digits(crt_digit_bits(__uint_as_float(v[4 * i]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 1]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 2]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 3]), mf, im, uf, uim));
-                            uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
-                            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                        }
+                        epi_digits(tbase, mf, im, uf, uim, dst);
                     }
                     tc_fence_before();
                     if (last_chunk && c == I.nch - 1) __threadfence_block();
@@ -542,8 +574,20 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                         mbar_arrive(&acc_empty[s]);
                         if (last_chunk && c == I.nch - 1) mbar_arrive(&slot_full[d.slot]);
                     }
+                    if (last_chunk && c == I.nch - 1) ++tiles_on[d.slot];
                 }
             }
+        }
+        if (ok && J > 0) {
+            // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
+            Job d;
+            S.job(J - 1, d);
+            uint2* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
+            stage_consts_warp(*d.inst, kcw, lane);
+            if (mbar_wait(&slot_full[d.slot], (uint32_t)(tiles_on[d.slot] - 1) & 1u, abort_flag, err,
+                          kDevTimeoutEpilogue))
+                combine_block(*d.inst, kcw, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+                              size_t(kTileM) * kTileN, kCombineWarps + (warp - 2), kCombineWarps + kEpiWarps, lane);
         }
     } else {
         // ------------------------------------------------------------ combine warps
@@ -563,14 +607,16 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             }
             if (!mbar_wait(&slot_full[d.slot], sfp[d.slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[d.slot] ^= 1u;
+            const bool last = j == J - 1;  // the epilogue warps join the last tile's reconstruction
             combine_block(*d.inst, kc, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
-                          size_t(kTileM) * kTileN, cw, lane);
+                          size_t(kTileM) * kTileN, cw, last ? kCombineWarps + kEpiWarps : kCombineWarps, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[d.slot]);
         }
     }
 
     tc_fence_before();
+    __syncwarp();  // warps 0 and 1 reconverge (lane 0 ran the producer / MMA loop) before the aligned barrier
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
@@ -797,20 +843,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float mf = I.modf[c], im = I.inv_m[c];
                     const float uf = (float)I.u[c], uim = uf * im;
                     if (!last_chunk) {
-#pragma unroll 1
-                        for (int cc = 0; cc < 4; ++cc) {
-                            uint32_t v[32];
-                            tc_ld32(tbase + cc * 32, v);
-                            tc_wait_ld();
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                const float x = __uint_as_float(v[i]);
-                                const float qq = rintf(x * im);
-                                v[i] = __float_as_uint(fmaf(-qq, mf, x));
-                            }
-                            tc_st32(tbase + cc * 32, v);
-                        }
-                        tc_wait_st();
+                        epi_reduce(tbase, mf, im);
                     } else {
                         if (c == 0) {
                             if (!mbar_wait(&slot_empty[slot], sep[slot] ^ 1u, abort_flag, err, kDevTimeoutEpilogue)) {
@@ -820,22 +853,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             sep[slot] ^= 1u;
                         }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
-#pragma unroll 1
-                        for (int cc = 0; cc < 4; ++cc) {
-                            uint32_t v[32];
-                            tc_ld32(tbase + cc * 32, v);
-                            tc_wait_ld();
-                            uint32_t w[8];
-#pragma unroll
-                            for (int i = 0; i < 8; ++i)
-                                w[i] = pack_digits(crt_digit_bits(__uint_as_float(v[4 * i]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 1]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 2]), mf, im, uf, uim),
-                                                   crt_digit_bits(__uint_as_float(v[4 * i + 3]), mf, im, uf, uim));
-                            uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
-                            d4[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                            d4[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                        }
+                        epi_digits(tbase, mf, im, uf, uim, dst);
                     }
                     tc_fence_before();
                     if (last_chunk && c == nch - 1) __threadfence_block();
@@ -849,6 +867,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             }
+        }
+        if (ok && my_tiles > 0) {
+            // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
+            const int ti = my_tiles - 1;
+            int tm, tn;
+            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
+            uint2* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
+            stage_consts_warp(I, kcw, lane);
+            if (mbar_wait(&slot_full[ti & 1], (uint32_t)(ti >> 1) & 1u, abort_flag, err, kDevTimeoutEpilogue))
+                combine_block(I, kcw, (2 * tm + (int)rank) * kTileM, tn * kTileN,
+                              slot_base + size_t(ti & 1) * P.slot_stride, size_t(kTileM) * kTileN,
+                              kCombineWarps + (warp - 2), kCombineWarps + kEpiWarps, lane);
         }
     } else {
         // ---------------------------------------------------- combine warps (both CTAs)
@@ -864,13 +894,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
             combine_block(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
-                          size_t(kTileM) * kTileN, cw, lane);
+                          size_t(kTileM) * kTileN, cw, ti == my_tiles - 1 ? kCombineWarps + kEpiWarps : kCombineWarps,
+                          lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[slot]);
         }
     }
 
     tc_fence_before();
+    __syncwarp();    // warps 0 and 1 reconverge before the aligned cluster barrier
     cluster_sync();  // no CTA leaves while its peer may still read its shared memory
     if (warp == 1) {
         tc_fence_after();
