@@ -3,8 +3,10 @@
 // wave.  Host side only: plans, placement of every instance's channel planes in
 // per-k pools, cost-balanced job lists, tables copied to the device.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <queue>
 #include <utility>
 #include <vector>
@@ -15,7 +17,65 @@ namespace ffgpu {
 
 namespace {
 
-constexpr size_t kWavePlaneBudget = size_t(4) << 30;  // channel-plane bytes per wave
+// Channel-plane bytes per wave (FFGPU_BATCH_WAVE_GB overrides): fewer, larger
+// waves mean fewer launch tails and table uploads.
+size_t wave_plane_budget() {
+    static size_t v = 0;
+    if (v == 0) {
+        size_t gb = 12;
+        if (const char* e = std::getenv("FFGPU_BATCH_WAVE_GB")) {
+            const long long x = std::atoll(e);
+            if (x >= 1 && x <= 200) gb = (size_t)x;
+        }
+        v = gb << 30;
+    }
+    return v;
+}
+
+// Pinned, double-buffered host staging for the per-wave tables: the copy of
+// wave w runs while the host fills wave w+1, and a buffer is rewritten only
+// after the event recorded behind its copy has completed.
+struct StageBuf {
+    unsigned char* p = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;
+    bool pending = false;
+};
+std::mutex g_stage_mu;  // held from stage_get to stage_done
+StageBuf g_stage[2];
+int g_stage_next = 0;
+
+unsigned char* stage_get(size_t bytes, int* idx) {
+    StageBuf& b = g_stage[g_stage_next];
+    if (b.pending) {
+        cudaEventSynchronize(b.ev);
+        b.pending = false;
+    }
+    if (!b.ev && cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        b.ev = nullptr;
+        return nullptr;
+    }
+    if (b.bytes < bytes) {
+        if (b.p) cudaFreeHost(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        const size_t want = std::max(bytes, size_t(1) << 20);
+        if (cudaHostAlloc(reinterpret_cast<void**>(&b.p), want, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            return nullptr;
+        }
+        b.bytes = want;
+    }
+    *idx = g_stage_next;
+    g_stage_next ^= 1;
+    return b.p;
+}
+
+void stage_done(int idx, cudaStream_t s) {
+    if (cudaEventRecord(g_stage[idx].ev, s) == cudaSuccess) g_stage[idx].pending = true;
+}
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
@@ -120,9 +180,18 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     if (st != FFGPU_OK) return st;
     unsigned char* ws = static_cast<unsigned char*>(pool->ptr);
 
-    // host image of the tables [t_maps, t_end)
-    std::vector<unsigned char> host(t_end - t_maps, 0);
-    auto at = [&](size_t o) { return host.data() + (o - t_maps); };
+    // host image of the tables [t_maps, t_end), in pinned staging when available
+    const size_t tab_bytes = t_end - t_maps;
+    std::unique_lock<std::mutex> stage_lk(g_stage_mu);
+    int stage_idx = -1;
+    std::vector<unsigned char> fallback;
+    unsigned char* host = stage_get(tab_bytes, &stage_idx);
+    if (!host) {
+        fallback.resize(tab_bytes);
+        host = fallback.data();
+    }
+    std::memset(host, 0, tab_bytes);
+    auto at = [&](size_t o) { return host + (o - t_maps); };
     CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(at(t_maps));
     for (size_t bi = 0; bi < buckets.size(); ++bi) {
         const Bucket& B = buckets[bi];
@@ -187,8 +256,10 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     bbB[n_inst] = nbB;
     std::memcpy(at(t_jobs), jobs.data(), jobs.size() * sizeof(GroupJob));
     std::memcpy(at(t_cta), cta_begin.data(), cta_begin.size() * sizeof(int));
-    if (cudaMemcpyAsync(ws + t_maps, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    if (cudaMemcpyAsync(ws + t_maps, host, tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return FFGPU_ERR_CUDA;
+    if (stage_idx >= 0) stage_done(stage_idx, s);
+    stage_lk.unlock();
 
     if (timed_launch("convert_rows_grouped", s, [&] {
             return launch_convert_rows_grouped(reinterpret_cast<const ConvJob*>(ws + t_convA),
@@ -241,7 +312,7 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         b.bucket = 0;
         b.rowA = b.rowB = 0;
         const size_t bytes = size_t(pl.nch) * (b.mpad + b.npad) * b.kp * 2;
-        if (!wave.empty() && wave_bytes + bytes > kWavePlaneBudget) {
+        if (!wave.empty() && wave_bytes + bytes > wave_plane_budget()) {
             ffgpu_status st = run_wave(wave, s, sms);
             if (st != FFGPU_OK) return st;
             wave.clear();

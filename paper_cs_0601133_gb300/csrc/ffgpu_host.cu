@@ -45,8 +45,46 @@ static int64_t k_capacity(uint32_t p, int c) {
     return cap > (u128)INT64_MAX ? INT64_MAX : (int64_t)cap;
 }
 
-// Plan for one launch summing `k` products.
+// Plan for one launch summing `k` products (computed by build_plan, cached
+// per modulus: the channel count is the only part that depends on k).
+static void build_plan(uint32_t p, int64_t k, RnsPlan& pl);
+
+namespace {
+struct PlanCacheEntry {
+    int64_t cap[kMaxChannels + 1];  // cap[c]: largest k that c channels sum exactly
+    RnsPlan plans[kMaxChannels + 1];
+    bool have[kMaxChannels + 1];
+};
+std::mutex g_plan_mu;
+std::map<uint32_t, PlanCacheEntry> g_plan_cache;
+}  // namespace
+
 void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
+    if (p <= kDirectMaxP) {
+        build_plan(p, k, pl);
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plan_cache.find(p);
+    if (it == g_plan_cache.end()) {
+        if (g_plan_cache.size() > 4096) g_plan_cache.clear();  // bounded
+        PlanCacheEntry e;
+        std::memset(&e, 0, sizeof(e));
+        for (int c = 1; c <= kMaxChannels; ++c) e.cap[c] = k_capacity(p, c);
+        it = g_plan_cache.emplace(p, e).first;
+    }
+    PlanCacheEntry& e = it->second;
+    const int64_t ks = std::min<int64_t>(std::max<int64_t>(k, 1), e.cap[kMaxChannels]);
+    int c = 1;
+    while (c < kMaxChannels && e.cap[c] < ks) ++c;
+    if (!e.have[c]) {
+        build_plan(p, e.cap[c], e.plans[c]);  // k = cap[c] selects exactly c channels
+        e.have[c] = true;
+    }
+    pl = e.plans[c];
+}
+
+static void build_plan(uint32_t p, int64_t k, RnsPlan& pl) {
     std::memset(&pl, 0, sizeof(pl));
     pl.p = p;
     if (p <= kDirectMaxP) {

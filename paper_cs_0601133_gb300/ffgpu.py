@@ -212,9 +212,10 @@ def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "r
     return C
 
 
-def fgemm_batched(problems, stream=None):
-    """problems: iterable of (A, B, C, p, alpha, beta) with CUDA tensors; every
-    C <- (alpha*A@B + beta*C) mod p, all in one batched call. Returns the Cs."""
+def batched_descs(problems):
+    """The host descriptor array (ffgpu_fgemm_desc[]) of a list of problems
+    (A, B, C, p, alpha, beta) on CUDA tensors; it stays valid while the tensors
+    live and can be passed to fgemm_batched_descs any number of times."""
     probs = list(problems)
     arr = (FgemmDesc * max(1, len(probs)))()
     for i, (A, B, C, p, alpha, beta) in enumerate(probs):
@@ -226,7 +227,20 @@ def fgemm_batched(problems, stream=None):
         b, ldb = _mat(B, "B")
         c, ldc = _mat(C, "C")
         arr[i] = FgemmDesc(m, n, k, p, alpha % 2**32, beta % 2**32, a, lda, b, ldb, c, ldc)
-    check(lib().ffgpu_fgemm_batched(len(probs), arr, _stream_ptr(stream)), "ffgpu_fgemm_batched")
+    return arr, len(probs)
+
+
+def fgemm_batched_descs(descs, count: int, stream=None):
+    """ffgpu_fgemm_batched on a prebuilt descriptor array (see batched_descs)."""
+    check(lib().ffgpu_fgemm_batched(count, descs, _stream_ptr(stream)), "ffgpu_fgemm_batched")
+
+
+def fgemm_batched(problems, stream=None):
+    """problems: iterable of (A, B, C, p, alpha, beta) with CUDA tensors; every
+    C <- (alpha*A@B + beta*C) mod p, all in one batched call. Returns the Cs."""
+    probs = list(problems)
+    arr, count = batched_descs(probs)
+    fgemm_batched_descs(arr, count, stream)
     return [pr[2] for pr in probs]
 
 
