@@ -24,7 +24,7 @@
 //   warp 0      TMA producer: channel tiles of A (128x64) and B (256x64), 4 stages
 //   warp 1      TMEM allocator and single-thread MMA issuer (M=128, N=256, K=16)
 //   warps 2..9  epilogue: lane quarter (warp % 4) x column half ((warp-2) / 4)
-//   warps 10-13 combine: reconstruction of the previous tile (two residue slots)
+//   warps 10-15 combine: reconstruction of the previous tile (two residue slots)
 // Two 256-column accumulators: the jobs (tile, channel) of a CTA are paired and
 // their chunks interleaved, so one accumulator is reduced while the tensor
 // cores fill the other.
@@ -40,8 +40,9 @@ namespace ffgpu {
 
 namespace {
 
-constexpr int kThreads = 448;   // 2 control warps, 8 epilogue warps, 4 combine warps
 constexpr int kEpiWarps = 8;
+constexpr int kCombineWarps = 6;
+constexpr int kThreads = 32 * (2 + kEpiWarps + kCombineWarps);  // 2 control warps
 constexpr int kFirstCombineWarp = 10;
 constexpr uint32_t kABytes = kTileM * kTileK * 2;
 constexpr uint32_t kBBytes = kTileN * kTileK * 2;
@@ -124,8 +125,6 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 // 256 contiguous digit bytes per channel and row and 1 KB of C.  The next
 // row's digits and C entries are loaded while the current row is reduced (two
 // register buffers); the loads are latency-bound, hence the extra warps.
-constexpr int kCombineWarps = 4;
-
 struct CombRow {
     uint2 w[kMaxChannels];  // digits of columns 8l .. 8l+7, per channel
     uint32_t o[8];          // the old entries of C
