@@ -8,6 +8,8 @@
 #include <functional>
 #include <mutex>
 #include <queue>
+#include <unordered_map>
+#include <unordered_set>
 #include <utility>
 #include <vector>
 
@@ -98,13 +100,16 @@ struct Bucket {
 ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     // buckets by padded inner length
     std::vector<Bucket> buckets;
+    std::unordered_map<int64_t, int> bucket_of;
     for (auto& b : w) {
-        int idx = -1;
-        for (size_t i = 0; i < buckets.size(); ++i)
-            if (buckets[i].kp == b.kp) idx = (int)i;
-        if (idx < 0) {
+        int idx;
+        auto it = bucket_of.find(b.kp);
+        if (it == bucket_of.end()) {
             buckets.push_back(Bucket{b.kp, 0, 0, 0, 0, 0});
             idx = (int)buckets.size() - 1;
+            bucket_of.emplace(b.kp, idx);
+        } else {
+            idx = it->second;
         }
         Bucket& B = buckets[idx];
         b.bucket = idx;
@@ -146,12 +151,25 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     std::vector<int> cta_begin(grid + 1, 0);
     for (int c = 0; c < grid; ++c) {
         cta_begin[c] = (int)jobs.size();
-        int parity = 0;
+        uint32_t parity = 0;
         for (int t : per_cta[c]) {
             const Tile& T = tiles[t];
-            for (int ch = 0; ch < w[T.inst].pl.nch; ++ch)
-                jobs.push_back(GroupJob{T.inst, T.tm, T.tn, ch | (parity << 8)});
-            parity ^= 1;
+            const BInst& b = w[T.inst];
+            const int ksteps = (int)(b.kp / kTileK);
+            const int cs = chunk_steps_for(b.pl);
+            for (int ch = 0; ch < b.pl.nch; ++ch) {
+                GroupJob g;
+                g.inst = T.inst;
+                g.tmtn = (uint32_t)T.tm | ((uint32_t)T.tn << 16);
+                g.cfg = (uint32_t)ch | (parity << 8) | ((uint32_t)b.pl.nch << 12) | ((uint32_t)b.bucket << 16);
+                g.modc = b.pl.mod[ch] | (b.pl.u[ch] << 8) | ((uint32_t)cs << 16);
+                g.ksteps = ksteps;
+                g.H = (ksteps + cs - 1) / cs;
+                g.rowA = (int)b.rowA + T.tm * kTileM;
+                g.rowB = (int)b.rowB + T.tn * kTileN;
+                jobs.push_back(g);
+            }
+            parity ^= 1u;
         }
     }
     cta_begin[grid] = (int)jobs.size();
@@ -292,7 +310,8 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
     const int sms = sm_count(dev);
     std::vector<BInst> wave;
-    std::vector<const ffgpu_fgemm_desc*> singles;  // k = 0 or k beyond one launch's capacity
+    std::unordered_set<int64_t> wave_k;
+    std::vector<const ffgpu_fgemm_desc*> singles;  // k = 0, k beyond one launch's capacity, huge m or n
     size_t wave_bytes = 0;
     for (int64_t i = 0; i < count; ++i) {
         const ffgpu_fgemm_desc& d = descs[i];
@@ -309,16 +328,24 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         b.kp = round_up(d.k, kTileK);
         b.mpad = round_up(d.m, kTileM);
         b.npad = round_up(d.n, kTileN);
+        if (b.mpad / kTileM > 0xFFFF || b.npad / kTileN > 0xFFFF) {  // tile indices are packed in 16 bits
+            singles.push_back(&d);
+            continue;
+        }
         b.bucket = 0;
         b.rowA = b.rowB = 0;
         const size_t bytes = size_t(pl.nch) * (b.mpad + b.npad) * b.kp * 2;
-        if (!wave.empty() && wave_bytes + bytes > wave_plane_budget()) {
+        // a wave holds at most 0xFFFF distinct inner lengths (k-bucket indices are packed in 16 bits)
+        const bool new_k = wave_k.find(b.kp) == wave_k.end();
+        if (!wave.empty() && (wave_bytes + bytes > wave_plane_budget() || (new_k && wave_k.size() >= 0xFFFF))) {
             ffgpu_status st = run_wave(wave, s, sms);
             if (st != FFGPU_OK) return st;
             wave.clear();
+            wave_k.clear();
             wave_bytes = 0;
         }
         wave.push_back(b);
+        wave_k.insert(b.kp);
         wave_bytes += bytes;
     }
     if (!wave.empty()) {

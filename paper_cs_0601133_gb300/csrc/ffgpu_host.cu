@@ -289,6 +289,8 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
     I.beta_s = (uint32_t)(((unsigned long long)be << 32) / p);
     I.C = C;
     I.ldc = ldc;
+    unsigned long long sumW = 0;
+    uint32_t sumF = 0;
     for (int c = 0; c < pl.nch; ++c) {
         const uint32_t m = pl.mod[c];
         I.modf[c] = (float)m;
@@ -297,7 +299,14 @@ void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl,
         I.u[c] = pl.u[c];
         I.Wa[c] = (uint32_t)((unsigned long long)al * pl.W[c] % p);
         I.fr[c] = ((1u << 14) + m / 2) / m;
+        sumW += I.Wa[c];
+        sumF += I.fr[c];
     }
+    // digits arrive as b_c + 128 (b_c balanced); the offsets, and the +6 that
+    // keeps the quotient non-negative, are undone by these start values
+    const unsigned long long neg = (128ull * (sumW % p) + 6ull * I.negMpa) % p;
+    I.Kfix = (uint32_t)((p - neg) % p);
+    I.Finit = 6u * (1u << 14) + (1u << 13) - 128u * sumF;
 }
 
 // Kernel choice: the CTA-pair kernel for problems with more than one 128-row

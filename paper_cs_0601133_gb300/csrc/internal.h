@@ -62,6 +62,8 @@ struct InstInfo {
     uint32_t R32, R32s;            // 2^32 mod p and its Shoup quotient floor(R32 2^32 / p)
     uint32_t one_s;                // floor(2^32 / p): Shoup quotient of 1
     uint32_t beta_s;               // floor(beta 2^32 / p)
+    uint32_t Kfix;                 // (-128 sum_c Wa_c - 6 negMpa) mod p: start value of the CRT sum
+    uint32_t Finit;                // 6 2^14 + 2^13 - 128 sum_c fr_c (mod 2^32): start value of the quotient sum
     uint32_t* C;
     long long ldc;
     int bucket;                    // grouped launch: tensor-map pair of this instance
@@ -83,10 +85,22 @@ struct RnsGemmParams {
     int* err;                      // device error word
 };
 
-// Grouped launch: jobs (instance, tile, channel), listed per CTA.  c holds
-// the channel in bits 0-7 and the tile's residue slot (0/1) in bit 8.
-struct GroupJob {
-    int inst, tm, tn, c;
+// Grouped launch: jobs (instance, tile, channel), listed per CTA, with
+// everything the producer, MMA and epilogue roles need packed in 32 bytes so
+// that one (prefetched) load per job suffices:
+//   tmtn = tile row (bits 0-15) | tile column (bits 16-31)
+//   cfg  = channel (bits 0-7) | residue slot of the tile (bit 8) |
+//          channel count (bits 12-15) | k-bucket of the instance (bits 16-31)
+//   modc = modulus m_c (bits 0-7) | (M/m_c)^{-1} mod m_c (bits 8-15) |
+//          chunk length in k-steps (bits 16-23)
+struct alignas(32) GroupJob {
+    int inst;
+    uint32_t tmtn;
+    uint32_t cfg;
+    uint32_t modc;
+    int ksteps;        // k-steps of the instance
+    int H;             // chunks
+    int rowA, rowB;    // first plane rows of the tile's A and B blocks in the bucket's pools
 };
 struct GroupGemmParams {
     const InstInfo* insts;

@@ -76,19 +76,27 @@ __device__ __forceinline__ void mbar_drain_wait(uint64_t* bar, uint32_t parity, 
     }
 }
 
+// Rounding to the nearest integer without the (slow) float-to-integral
+// conversion: for |z| < 2^22, z + 1.5 2^23 lands in [2^23, 2^24), where the
+// float spacing is 1, so the fused add rounds z (taken exactly, before any
+// rounding of a product inside the fma) to an integer.
+constexpr float kRoundMagic = 12582912.f;  // 1.5 * 2^23
+
 // CRT digit of one accumulator entry: with r = x mod m_c (x an f32 integer,
-// |x| < 2^24), b = r u_c mod m_c, returned as the f32 bit pattern of 2^23 + b,
-// whose low byte is b.  b lands in [0, m_c]: floor() of the rounded quotient
-// may give m_c in place of 0 for an exact multiple, a representative the
-// reconstruction accepts (b_c and b_c + m_c change sum_c b_c/m_c by exactly 1,
-// so the rounded quotient q absorbs it).  Exactness: |r| <= 129, so r u_c and
-// 2^23 + r u_c (|r u_c| < 2^15) are exact in f32; the quotient r u_c / m_c is
-// below 166 in magnitude and is computed with relative error < 2^-22, far
-// inside the 1/m_c gap to the next integer.
+// |x| / m_c < 2^22), b = r u_c mod m_c in balanced form, |b| <= 127, returned
+// as the f32 bit pattern of 1.5 2^23 + 128 + b, whose low byte is b + 128.
+// Exactness: |r| <= 129 (the quotient x/m_c is rounded from a product with
+// relative error < 2^-24 of a value below 2^22), so r u_c (< 2^15) and every
+// intermediate below are integers exact in f32; r u_c / m_c is rounded from a
+// value within 2^-14 of it, while for odd m_c its fractional part, a multiple
+// of 1/m_c, stays 1/(2 m_c) away from 1/2, so b = r u_c - m_c round(r u_c /
+// m_c) is the balanced residue (for even moduli, direct mode only, a tie may
+// give +-m_c/2 <= 127).  Seven full-rate float operations, no conversion.
 __device__ __forceinline__ uint32_t crt_digit_bits(float x, float mf, float im, float uf, float uim) {
-    const float r = fmaf(-rintf(x * im), mf, x);
-    const float fl = floorf(r * uim);
-    return __float_as_uint(fmaf(-fl, mf, fmaf(r, uf, 8388608.f)));
+    const float q1 = fmaf(x, im, kRoundMagic) - kRoundMagic;
+    const float r = fmaf(-q1, mf, x);
+    const float q2 = fmaf(r, uim, kRoundMagic) - kRoundMagic;
+    return __float_as_uint(fmaf(r, uf, fmaf(-q2, mf, kRoundMagic + 128.f)));
 }
 
 // Low bytes of four digit patterns, packed.
@@ -108,16 +116,20 @@ __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t w
 
 // Reconstruction of alpha X + beta C mod p from the CRT digits, for the
 // 128 x 256 block of one CTA.  With M = prod m_c and b_c = r_c (M/m_c)^{-1}
-// mod m_c (the epilogue stores b_c, see crt_digit_bits), X = sum_c b_c M/m_c
-// - q M where q = round(sum_c b_c / m_c), valid because the plan guarantees
-// |X| <= M/4.  q comes from a 14-bit fixed-point sum F = sum_c b_c fr_c with
-// fr_c = round(2^14/m_c): each term is off by at most 255/2 units of 2^-14,
-// twelve of them by < 0.1, so F / 2^14 stays within 0.35 of q.  Then
-// alpha X mod p = (sum_c b_c Wa_c + q negMpa) mod p with Wa_c = alpha (M/m_c)
-// mod p and negMpa = alpha (-M) mod p: a 64-bit sum Y < 2^44 accumulated with
-// one wide multiply-add per channel, reduced as Y_hi (2^32 mod p) + Y_lo with
-// Shoup products; beta C mod p likewise.  Per output and channel: one byte
-// extraction and two integer multiply-adds.
+// mod m_c in balanced form (the epilogue stores b_c + 128, see
+// crt_digit_bits), X = sum_c b_c M/m_c - q M where q = round(sum_c b_c / m_c),
+// valid because the plan guarantees |X| <= M/4; |q| <= 6.  q comes from a
+// 14-bit fixed-point sum F = sum_c b_c fr_c with fr_c = round(2^14/m_c): each
+// term is off by at most 128/2 units of 2^-14, twelve of them by < 0.05, so
+// F / 2^14 stays within 0.3 of q.  Then alpha X mod p = (sum_c b_c Wa_c +
+// q negMpa) mod p with Wa_c = alpha (M/m_c) mod p and negMpa = alpha (-M)
+// mod p.  Both sums run over the stored bytes b_c + 128 in unsigned
+// arithmetic, started at Kfix and Finit, which cancel the offsets mod p and
+// make the quotient sum yield q + 6 >= 0: Y = S + (q + 6) negMpa < 2^44,
+// congruent to alpha X, accumulated with one wide multiply-add per channel and
+// reduced as Y_hi (2^32 mod p) + Y_lo with Shoup products; beta C mod p
+// likewise.  Per output and channel: one byte extraction and two integer
+// multiply-adds.
 //
 // Done by the kCombineWarps combine warps, joined for a CTA's last tile by the
 // kEpiWarps epilogue warps (then idle): of nw participating warps, warp vw takes
@@ -156,10 +168,11 @@ __device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int
                                          uint32_t* crow, int col, int n, bool full8) {
     unsigned long long S[8];
     uint32_t F[8];
+    const uint32_t Kfix = I.Kfix, Finit = I.Finit;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        S[e] = 0ull;
-        F[e] = 0u;
+        S[e] = Kfix;
+        F[e] = Finit;
     }
 #pragma unroll
     for (int c = 0; c < kMaxChannels; ++c) {
@@ -178,7 +191,7 @@ __device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int
     uint32_t out[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const uint32_t q = (F[e] + 8192u) >> 14;
+        const uint32_t q = F[e] >> 14;  // q + 6
         const unsigned long long Y = S[e] + (unsigned long long)q * negMpa;
         const uint32_t t1 = fold_p(mul_shoup((uint32_t)(Y >> 32), R32, R32s, p), p);
         const uint32_t lo = (uint32_t)Y;
@@ -244,7 +257,8 @@ __device__ __forceinline__ void stage_consts(const InstInfo& I, uint2* kc, int t
 
 // Epilogue of one warp on its 32 lanes x 128 columns of an accumulator, two
 // 32-column loads in flight per tensor-memory wait.
-// In-place reduction mod m_c (|result| <= m_c/2 + 1), between chunks.
+// In-place reduction mod m_c (|result| <= m_c/2 + 1), between chunks; |x| / m_c
+// < 2^22 (chunk lengths keep |x| < 2^24, and m_c >= 4 unless |residues| <= 1).
 __device__ __forceinline__ void epi_reduce(uint32_t tbase, float mf, float im) {
 #pragma unroll 1
     for (int cc = 0; cc < 4; cc += 2) {
@@ -255,9 +269,9 @@ __device__ __forceinline__ void epi_reduce(uint32_t tbase, float mf, float im) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             const float x = __uint_as_float(v[i]);
-            v[i] = __float_as_uint(fmaf(-rintf(x * im), mf, x));
+            v[i] = __float_as_uint(fmaf(-(fmaf(x, im, kRoundMagic) - kRoundMagic), mf, x));
             const float y = __uint_as_float(v2[i]);
-            v2[i] = __float_as_uint(fmaf(-rintf(y * im), mf, y));
+            v2[i] = __float_as_uint(fmaf(-(fmaf(y, im, kRoundMagic) - kRoundMagic), mf, y));
         }
         tc_st32(tbase + cc * 32, v);
         tc_st32(tbase + cc * 32 + 32, v2);
@@ -293,14 +307,22 @@ __device__ __forceinline__ void epi_digits(uint32_t tbase, float mf, float im, f
     }
 }
 
-// A job of the kernel: one channel of one output tile of one instance.
+// A job of the kernel: one channel of one output tile of one instance.  Every
+// role walks its CTA's jobs in the same order with its own iterator, so the
+// per-job work on the single-thread producer and MMA paths is a few moves:
+// those threads share their SM sub-partitions with the epilogue warps' dense
+// float code and get few issue slots while it runs.
 struct Job {
     const InstInfo* inst;
     const CUtensorMap* mapA;
     const CUtensorMap* mapB;
-    int tm, tn, c;
-    int H;        // chunks of kChunkSteps k-steps
-    int slot;     // residue slot of the job's tile
+    int tm, tn;
+    int c, nch;
+    int H;           // chunks of cs k-steps
+    int cs, ksteps;
+    int rowA, rowB;  // first plane rows of the tile's A and B blocks
+    int slot;        // residue slot of the job's tile
+    float mf, im, uf;  // m_c, 1/m_c, (M/m_c)^{-1} mod m_c
 };
 
 // Single instance, tiles dealt round-robin to the CTAs, channels in order.
@@ -308,51 +330,90 @@ struct SingleSched {
     const RnsGemmParams& P;
     const CUtensorMap* mA;
     const CUtensorMap* mB;
-    int my_tiles;
+    int my_tiles, H;
+    int ti, c, tm, tn;  // iteration state
     __device__ SingleSched(const RnsGemmParams& p, const CUtensorMap* a, const CUtensorMap* b)
-        : P(p), mA(a), mB(b) {
+        : P(p), mA(a), mB(b), ti(0), c(0), tm(0), tn(0) {
         my_tiles = (int)blockIdx.x < P.num_tiles
                        ? (P.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
                        : 0;
+        H = (P.inst.ksteps + P.inst.chunk_steps - 1) / P.inst.chunk_steps;
+        if (my_tiles > 0) tile_coords((int)blockIdx.x, P.tiles_m, P.tiles_n, tm, tn);
     }
     __device__ int num_jobs() const { return my_tiles * P.inst.nch; }
-    __device__ void job(int j, Job& d) const {
-        const int nch = P.inst.nch;
-        const int t = (int)blockIdx.x + (j / nch) * (int)gridDim.x;
-        d.inst = &P.inst;
+    __device__ void fill(Job& d, int tile_ord, int ch, int tm_, int tn_) const {
+        const InstInfo& I = P.inst;
+        d.inst = &I;
         d.mapA = mA;
         d.mapB = mB;
-        d.c = j % nch;
-        tile_coords(t, P.tiles_m, P.tiles_n, d.tm, d.tn);
-        d.H = (P.inst.ksteps + P.inst.chunk_steps - 1) / P.inst.chunk_steps;
-        d.slot = (j / nch) & 1;  // tiles alternate the two residue slots
+        d.tm = tm_;
+        d.tn = tn_;
+        d.c = ch;
+        d.nch = I.nch;
+        d.H = H;
+        d.cs = I.chunk_steps;
+        d.ksteps = I.ksteps;
+        d.rowA = I.rowA + tm_ * kTileM;
+        d.rowB = I.rowB + tn_ * kTileN;
+        d.slot = tile_ord & 1;  // tiles alternate the two residue slots
+        d.mf = I.modf[ch];
+        d.im = I.inv_m[ch];
+        d.uf = (float)I.u[ch];
+    }
+    __device__ void next(Job& d) {
+        fill(d, ti, c, tm, tn);
+        if (++c == P.inst.nch) {
+            c = 0;
+            if (++ti < my_tiles) tile_coords((int)blockIdx.x + ti * (int)gridDim.x, P.tiles_m, P.tiles_n, tm, tn);
+        }
+    }
+    __device__ void last_job(Job& d) const {
+        int a, b;
+        tile_coords((int)blockIdx.x + (my_tiles - 1) * (int)gridDim.x, P.tiles_m, P.tiles_n, a, b);
+        fill(d, my_tiles - 1, P.inst.nch - 1, a, b);
     }
     __device__ unsigned char* slots() const { return P.slots; }
     __device__ size_t slot_stride() const { return P.slot_stride; }
     __device__ int* err() const { return P.err; }
 };
 
-// Grouped launch: the host lists every CTA's jobs.
+// Grouped launch: the host lists every CTA's jobs; the next record is loaded
+// one job ahead.
 struct GroupSched {
     const GroupGemmParams& P;
-    int begin, count;
-    __device__ GroupSched(const GroupGemmParams& p, const CUtensorMap*, const CUtensorMap*) : P(p) {
+    int begin, count, j;
+    GroupJob nxt;
+    __device__ GroupSched(const GroupGemmParams& p, const CUtensorMap*, const CUtensorMap*) : P(p), j(0) {
         begin = P.cta_begin[blockIdx.x];
         count = P.cta_begin[blockIdx.x + 1] - begin;
+        if (count > 0) nxt = P.jobs[begin];
     }
     __device__ int num_jobs() const { return count; }
-    __device__ void job(int j, Job& d) const {
-        const GroupJob g = P.jobs[begin + j];
-        const InstInfo* I = P.insts + g.inst;
-        d.inst = I;
-        d.mapA = P.maps + 2 * I->bucket;
-        d.mapB = P.maps + 2 * I->bucket + 1;
-        d.tm = g.tm;
-        d.tn = g.tn;
-        d.c = g.c & 0xFF;
-        d.H = (I->ksteps + I->chunk_steps - 1) / I->chunk_steps;
-        d.slot = (g.c >> 8) & 1;  // tiles alternate the two residue slots
+    __device__ void decode(const GroupJob& g, Job& d) const {
+        d.inst = P.insts + g.inst;
+        const int bucket = (int)(g.cfg >> 16);
+        d.mapA = P.maps + 2 * bucket;
+        d.mapB = P.maps + 2 * bucket + 1;
+        d.tm = (int)(g.tmtn & 0xFFFFu);
+        d.tn = (int)(g.tmtn >> 16);
+        d.c = (int)(g.cfg & 0xFFu);
+        d.slot = (int)((g.cfg >> 8) & 1u);
+        d.nch = (int)((g.cfg >> 12) & 0xFu);
+        d.H = g.H;
+        d.cs = (int)((g.modc >> 16) & 0xFFu);
+        d.ksteps = g.ksteps;
+        d.rowA = g.rowA;
+        d.rowB = g.rowB;
+        d.mf = (float)(g.modc & 0xFFu);
+        d.im = __frcp_rn(d.mf);
+        d.uf = (float)((g.modc >> 8) & 0xFFu);
     }
+    __device__ void next(Job& d) {
+        const GroupJob g = nxt;
+        if (++j < count) nxt = P.jobs[begin + j];
+        decode(g, d);
+    }
+    __device__ void last_job(Job& d) const { decode(P.jobs[begin + count - 1], d); }
     __device__ unsigned char* slots() const { return P.slots; }
     __device__ size_t slot_stride() const { return P.slot_stride; }
     __device__ int* err() const { return P.err; }
@@ -381,7 +442,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
 
-    const Sched S(P, mapA, mapB);
+    Sched S(P, mapA, mapB);       // per-thread iterator over this CTA's jobs
     const int J = S.num_jobs();   // jobs (tile, channel) of this CTA
     int* err = S.err();
 
@@ -420,18 +481,18 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
                 Job jb[2];
-                S.job(2 * pi, jb[0]);
-                if (nj > 1) S.job(2 * pi + 1, jb[1]);
+                S.next(jb[0]);
+                if (nj > 1) S.next(jb[1]);
                 const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
                 for (int h = 0; h < Hmax && ok; ++h) {
                     for (int s = 0; s < nj && ok; ++s) {
                         const Job& d = jb[s];
                         if (h >= d.H) continue;
-                        const int cs = d.inst->chunk_steps;
+                        const int cs = d.cs;
                         const int k0 = h * cs;
-                        const int steps = min(cs, d.inst->ksteps - k0);
-                        const int rowA = d.inst->rowA + d.tm * kTileM;
-                        const int rowB = d.inst->rowB + d.tn * kTileN;
+                        const int steps = min(cs, d.ksteps - k0);
+                        const int rowA = d.rowA;
+                        const int rowB = d.rowB;
                         for (int st = 0; st < steps; ++st) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err, kDevTimeoutProducer)) {
                                 ok = false;
@@ -467,15 +528,15 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
                 Job jb[2];
-                S.job(2 * pi, jb[0]);
-                if (nj > 1) S.job(2 * pi + 1, jb[1]);
+                S.next(jb[0]);
+                if (nj > 1) S.next(jb[1]);
                 const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
                 for (int h = 0; h < Hmax && ok; ++h) {
                     for (int s = 0; s < nj && ok; ++s) {
                         const Job& d = jb[s];
                         if (h >= d.H) continue;
-                        const int cs = d.inst->chunk_steps;
-                        const int steps = min(cs, d.inst->ksteps - h * cs);
+                        const int cs = d.cs;
+                        const int steps = min(cs, d.ksteps - h * cs);
                         if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
                             ok = false;
                             break;
@@ -530,15 +591,14 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
             Job jb[2];
-            S.job(2 * pi, jb[0]);
-            if (nj > 1) S.job(2 * pi + 1, jb[1]);
+            S.next(jb[0]);
+            if (nj > 1) S.next(jb[1]);
             const int Hmax = nj > 1 ? max(jb[0].H, jb[1].H) : jb[0].H;
             for (int h = 0; h < Hmax && ok; ++h) {
                 for (int s = 0; s < nj; ++s) {
                     const Job& d = jb[s];
                     if (h >= d.H) continue;
                     const bool last_chunk = (h == d.H - 1);
-                    const InstInfo& I = *d.inst;
                     const int c = d.c;
                     unsigned char* slot_row = slot_base + size_t(d.slot) * sstride + row_off;
                     if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
@@ -549,8 +609,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                     tc_fence_after();
                     const uint32_t tbase =
                         tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * kTileN + half * 128);
-                    const float mf = I.modf[c], im = I.inv_m[c];
-                    const float uf = (float)I.u[c], uim = uf * im;
+                    const float mf = d.mf, im = d.im;
+                    const float uf = d.uf, uim = uf * im;
                     if (!last_chunk) {
                         epi_reduce(tbase, mf, im);
                     } else {
@@ -567,20 +627,20 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                         epi_digits(tbase, mf, im, uf, uim, dst);
                     }
                     tc_fence_before();
-                    if (last_chunk && c == I.nch - 1) __threadfence_block();
+                    if (last_chunk && c == d.nch - 1) __threadfence_block();
                     __syncwarp();
                     if (lane == 0) {
                         mbar_arrive(&acc_empty[s]);
-                        if (last_chunk && c == I.nch - 1) mbar_arrive(&slot_full[d.slot]);
+                        if (last_chunk && c == d.nch - 1) mbar_arrive(&slot_full[d.slot]);
                     }
-                    if (last_chunk && c == I.nch - 1) ++tiles_on[d.slot];
+                    if (last_chunk && c == d.nch - 1) ++tiles_on[d.slot];
                 }
             }
         }
         if (ok && J > 0) {
             // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
             Job d;
-            S.job(J - 1, d);
+            S.last_job(d);
             uint2* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(*d.inst, kcw, lane);
             if (mbar_wait(&slot_full[d.slot], (uint32_t)(tiles_on[d.slot] - 1) & 1u, abort_flag, err,
@@ -597,8 +657,8 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         const InstInfo* loaded = nullptr;
         for (int j = 0; j < J; ++j) {
             Job d;
-            S.job(j, d);
-            if (d.c != d.inst->nch - 1) continue;  // one reconstruction per tile
+            S.next(d);
+            if (d.c != d.nch - 1) continue;  // one reconstruction per tile
             if (d.inst != loaded) {
                 // every combine warp is done with the previous constants (barrier inside)
                 stage_consts(*d.inst, kc, cw * 32 + lane);
@@ -720,19 +780,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued = 0, last_parity = 0;
             bool ok = true;
+            int it_t = 0, it_c = 0, tm = 0, tn = 0;  // job iterator: tile ordinal, channel
+            if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, tm, tn);
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
+                int jc[2], jrA[2], jrB[2];
+                for (int s = 0; s < nj; ++s) {
+                    jc[s] = it_c;
+                    jrA[s] = tm * kPairTile + (int)rank * 128;
+                    jrB[s] = tn * kPairTile + (int)rank * 128;
+                    if (++it_c == nch) {
+                        it_c = 0;
+                        if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, tm, tn);
+                    }
+                }
                 for (int h = 0; h < H && ok; ++h) {
                     const int k0 = h * CS;
                     const int steps = min(CS, I.ksteps - k0);
                     for (int s = 0; s < nj && ok; ++s) {
-                        const int j = 2 * pi + s;
-                        const int t = pair + (j / nch) * npairs;
-                        const int c = j % nch;
-                        int tm, tn;
-                        tile_coords(t, P.tiles_m, P.tiles_n, tm, tn);
-                        const int rowA = tm * kPairTile + (int)rank * 128;
-                        const int rowB = tn * kPairTile + (int)rank * 128;
+                        const int c = jc[s];
+                        const int rowA = jrA[s];
+                        const int rowB = jrB[s];
                         for (int st = 0; st < steps; ++st) {
                             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag, err, kDevTimeoutProducer)) {
                                 ok = false;
@@ -822,14 +890,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t accp[2] = {0u, 0u};
         uint32_t sep[2] = {0u, 0u};
         bool ok = true;
+        int it_t = 0, it_c = 0;  // job iterator: tile ordinal, channel
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
+            int jc[2], jslot[2];
+            for (int s = 0; s < nj; ++s) {
+                jc[s] = it_c;
+                jslot[s] = it_t & 1;
+                if (++it_c == nch) {
+                    it_c = 0;
+                    ++it_t;
+                }
+            }
             for (int h = 0; h < H && ok; ++h) {
                 const bool last_chunk = (h == H - 1);
                 for (int s = 0; s < nj; ++s) {
-                    const int j = 2 * pi + s;
-                    const int c = j % nch;
-                    const int slot = (j / nch) & 1;
+                    const int c = jc[s];
+                    const int slot = jslot[s];
                     unsigned char* slot_row = slot_base + size_t(slot) * P.slot_stride + row_off;
                     if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
                         ok = false;
