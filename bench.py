@@ -504,10 +504,21 @@ def run_batched(args):
     ff.profile_enable(False)
     kern = {name: {"launches": v[0], "total_ms": round(v[1], 3)} for name, v in ff.profile_read().items()}
     dev_ms = sum(v["total_ms"] for v in kern.values())
+    # the same batch as a plan captured once in a CUDA graph: one graph launch per step
+    t0 = time.perf_counter()
+    plan = ff.BatchedPlan(problems)
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    graph_ms = time_call(plan.run, torch, max(1, min(args.steps, 10)), max(1, args.warmup))
+    assert plan.error() == 0
+    info = plan.info()
+    plan.close()
     print(json.dumps({"workload": "batched", "instances": count, "primes": len(primes),
                       "fgemms": len(problems), "ms": ms, "GOPS": flops / (ms / 1e3) / 1e9,
                       "kernel_ms": dev_ms, "kernel_GOPS": flops / (dev_ms / 1e3) / 1e9,
-                      "host_enqueue_ms": host_ms, "python_descs_ms": marshal_ms, "kernels": kern}), flush=True)
+                      "host_enqueue_ms": host_ms, "python_descs_ms": marshal_ms,
+                      "graph": {"ms": graph_ms, "GOPS": flops / (graph_ms / 1e3) / 1e9, "plan_create_ms": plan_ms,
+                                **info},
+                      "kernels": kern}), flush=True)
     return 0
 
 

@@ -227,6 +227,46 @@ typedef struct {
 FFGPU_API ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream);
 
 /*
+ * Batched plan: the launch sequence of ffgpu_fgemm_batched for one fixed
+ * batch, laid out once and captured in a CUDA graph (the repeated-batch use of
+ * the multi-modular products the paper's section 7 points to: the same shapes
+ * and buffers, new contents each time).
+ *
+ * ffgpu_fgemm_batched_plan_create validates the descriptors (host array,
+ * copied; the matrices are device memory on the current device), plans the
+ * waves, allocates the plan's device memory (the largest wave's channel
+ * planes and residue slots, every wave's tables, a workspace for products that
+ * run outside the grouped launch, an error word), uploads the tables and
+ * captures the conversions and tensor-core launches of every wave into a
+ * graph.  It synchronizes the device.  Errors: FFGPU_ERR_INVALID /
+ * FFGPU_ERR_UNSUPPORTED_P for a bad descriptor, FFGPU_ERR_NOMEM, FFGPU_ERR_CUDA;
+ * *plan is NULL on failure.
+ *
+ * ffgpu_fgemm_batched_plan_run enqueues the graph on `stream` (current device
+ * must be the plan's, else FFGPU_ERR_INVALID): every C of the batch becomes
+ * (alpha*A*B + beta*C) mod p from the CURRENT contents of its A, B and C.
+ * The pointers in the descriptors must stay valid while the plan lives.  Runs
+ * of one plan share its workspace: two runs must not overlap (same stream, or
+ * ordered by events).
+ *
+ * ffgpu_fgemm_batched_plan_error synchronizes the device and returns (and
+ * clears) the plan's device error word: FFGPU_ERR_TIMEOUT after a bounded
+ * wait expired in a run.  ffgpu_fgemm_batched_plan_info reports the wave
+ * count, the products run outside the grouped launch, the graph's node count
+ * and the plan's device bytes (any pointer may be NULL).
+ * ffgpu_fgemm_batched_plan_destroy synchronizes the device and frees the plan
+ * (NULL is accepted).
+ */
+typedef struct ffgpu_batched_plan ffgpu_batched_plan;
+FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs,
+                                                       ffgpu_batched_plan** plan);
+FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_run(ffgpu_batched_plan* plan, void* stream);
+FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_error(ffgpu_batched_plan* plan);
+FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_info(const ffgpu_batched_plan* plan, int* waves, int* singles,
+                                                     size_t* graph_nodes, size_t* device_bytes);
+FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_destroy(ffgpu_batched_plan* plan);
+
+/*
  * Request server (continuous batching).  Not in the paper: the deployment of
  * fgemm / ftrsm as a service.  Requests carry HOST operands (pinned memory
  * for overlap) and a host output buffer.  An engine thread admits pending

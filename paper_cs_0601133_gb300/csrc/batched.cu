@@ -94,24 +94,36 @@ struct Bucket {
     int64_t kp;
     int nch;
     int64_t rowsA, rowsB;
-    size_t offA, offB;  // byte offsets of the pools in the workspace
+    size_t offA, offB;  // byte offsets of the pools from the plane base
 };
 
-ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
-    // buckets by padded inner length
+// Host plan of one wave: pools by padded inner length, cost-balanced job
+// lists, and the layout of the two device regions it needs -- the planes
+// (residue slots, then the pools) and the tables (tensor maps, instances, jobs,
+// conversion jobs, block prefix sums).
+struct WaveLayout {
     std::vector<Bucket> buckets;
+    std::vector<GroupJob> jobs;
+    std::vector<int> cta_begin;
+    int grid = 1;
+    size_t plane_bytes = 0;
+    size_t t_inst = 0, t_jobs = 0, t_cta = 0, t_convA = 0, t_convB = 0, t_bbA = 0, t_bbB = 0, tab_bytes = 0;
+    long long nbA = 0, nbB = 0;  // conversion blocks
+};
+
+void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L) {
     std::unordered_map<int64_t, int> bucket_of;
     for (auto& b : w) {
         int idx;
         auto it = bucket_of.find(b.kp);
         if (it == bucket_of.end()) {
-            buckets.push_back(Bucket{b.kp, 0, 0, 0, 0, 0});
-            idx = (int)buckets.size() - 1;
+            L.buckets.push_back(Bucket{b.kp, 0, 0, 0, 0, 0});
+            idx = (int)L.buckets.size() - 1;
             bucket_of.emplace(b.kp, idx);
         } else {
             idx = it->second;
         }
-        Bucket& B = buckets[idx];
+        Bucket& B = L.buckets[idx];
         b.bucket = idx;
         B.nch = std::max(B.nch, b.pl.nch);
         b.rowA = B.rowsA;
@@ -132,13 +144,13 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
         for (int tm = 0; tm < tmn; ++tm)
             for (int tn = 0; tn < tnn; ++tn) tiles.push_back(Tile{(int)i, tm, tn, cost});
     }
-    const int grid = (int)std::max<size_t>(1, std::min<size_t>(tiles.size(), (size_t)sms));
+    L.grid = (int)std::max<size_t>(1, std::min<size_t>(tiles.size(), (size_t)sms));
     std::stable_sort(tiles.begin(), tiles.end(), [](const Tile& a, const Tile& b) { return a.cost > b.cost; });
-    std::vector<std::vector<int>> per_cta(grid);
+    std::vector<std::vector<int>> per_cta(L.grid);
     {
         typedef std::pair<double, int> Load;
         std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-        for (int c = 0; c < grid; ++c) heap.push(Load(0.0, c));
+        for (int c = 0; c < L.grid; ++c) heap.push(Load(0.0, c));
         for (size_t t = 0; t < tiles.size(); ++t) {
             Load l = heap.top();
             heap.pop();
@@ -147,10 +159,9 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
             heap.push(l);
         }
     }
-    std::vector<GroupJob> jobs;
-    std::vector<int> cta_begin(grid + 1, 0);
-    for (int c = 0; c < grid; ++c) {
-        cta_begin[c] = (int)jobs.size();
+    L.cta_begin.assign(L.grid + 1, 0);
+    for (int c = 0; c < L.grid; ++c) {
+        L.cta_begin[c] = (int)L.jobs.size();
         uint32_t parity = 0;
         for (int t : per_cta[c]) {
             const Tile& T = tiles[t];
@@ -167,66 +178,56 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
                 g.H = (ksteps + cs - 1) / cs;
                 g.rowA = (int)b.rowA + T.tm * kTileM;
                 g.rowB = (int)b.rowB + T.tn * kTileN;
-                jobs.push_back(g);
+                L.jobs.push_back(g);
             }
             parity ^= 1u;
         }
     }
-    cta_begin[grid] = (int)jobs.size();
+    L.cta_begin[L.grid] = (int)L.jobs.size();
 
-    // workspace layout: slots | pools | tables
-    size_t off = align_up(size_t(grid) * kSlotsPerCta * kSlotBytesPerCta, 256);
-    for (auto& B : buckets) {
+    // planes: slots | pools
+    size_t off = align_up(size_t(L.grid) * kSlotsPerCta * kSlotBytesPerCta, 256);
+    for (auto& B : L.buckets) {
         B.offA = off;
         off = align_up(off + size_t(B.nch) * B.rowsA * B.kp * 2, 256);
         B.offB = off;
         off = align_up(off + size_t(B.nch) * B.rowsB * B.kp * 2, 256);
     }
+    L.plane_bytes = off;
+    // tables: maps | instances | jobs | cta_begin | conversion jobs | prefix sums
     const size_t n_inst = w.size();
-    const size_t t_maps = align_up(off, 128);
-    const size_t t_inst = align_up(t_maps + 2 * buckets.size() * sizeof(CUtensorMap), 64);
-    const size_t t_jobs = align_up(t_inst + n_inst * sizeof(InstInfo), 64);
-    const size_t t_cta = align_up(t_jobs + jobs.size() * sizeof(GroupJob), 64);
-    const size_t t_convA = align_up(t_cta + cta_begin.size() * sizeof(int), 64);
-    const size_t t_convB = align_up(t_convA + n_inst * sizeof(ConvJob), 64);
-    const size_t t_bbA = align_up(t_convB + n_inst * sizeof(ConvJob), 64);
-    const size_t t_bbB = align_up(t_bbA + (n_inst + 1) * sizeof(long long), 64);
-    const size_t t_end = align_up(t_bbB + (n_inst + 1) * sizeof(long long), 256);
+    L.t_inst = align_up(2 * L.buckets.size() * sizeof(CUtensorMap), 64);
+    L.t_jobs = align_up(L.t_inst + n_inst * sizeof(InstInfo), 64);
+    L.t_cta = align_up(L.t_jobs + L.jobs.size() * sizeof(GroupJob), 64);
+    L.t_convA = align_up(L.t_cta + L.cta_begin.size() * sizeof(int), 64);
+    L.t_convB = align_up(L.t_convA + n_inst * sizeof(ConvJob), 64);
+    L.t_bbA = align_up(L.t_convB + n_inst * sizeof(ConvJob), 64);
+    L.t_bbB = align_up(L.t_bbA + (n_inst + 1) * sizeof(long long), 64);
+    L.tab_bytes = align_up(L.t_bbB + (n_inst + 1) * sizeof(long long), 256);
+}
 
-    Pool* pool = nullptr;
-    ffgpu_status st = pool_get(s, t_end, &pool);
-    if (st != FFGPU_OK) return st;
-    unsigned char* ws = static_cast<unsigned char*>(pool->ptr);
-
-    // host image of the tables [t_maps, t_end), in pinned staging when available
-    const size_t tab_bytes = t_end - t_maps;
-    std::unique_lock<std::mutex> stage_lk(g_stage_mu);
-    int stage_idx = -1;
-    std::vector<unsigned char> fallback;
-    unsigned char* host = stage_get(tab_bytes, &stage_idx);
-    if (!host) {
-        fallback.resize(tab_bytes);
-        host = fallback.data();
-    }
-    std::memset(host, 0, tab_bytes);
-    auto at = [&](size_t o) { return host + (o - t_maps); };
-    CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(at(t_maps));
-    for (size_t bi = 0; bi < buckets.size(); ++bi) {
-        const Bucket& B = buckets[bi];
-        if (!encode_planes(&maps[2 * bi], ws + B.offA, B.kp, B.rowsA, B.nch, kTileM) ||
-            !encode_planes(&maps[2 * bi + 1], ws + B.offB, B.kp, B.rowsB, B.nch, kTileN))
+// Host image of the tables (L.tab_bytes at `host`, zeroed by the caller) for
+// planes at `planes` on the device.
+ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsigned char* planes,
+                              unsigned char* host) {
+    CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host);
+    for (size_t bi = 0; bi < L.buckets.size(); ++bi) {
+        const Bucket& B = L.buckets[bi];
+        if (!encode_planes(&maps[2 * bi], planes + B.offA, B.kp, B.rowsA, B.nch, kTileM) ||
+            !encode_planes(&maps[2 * bi + 1], planes + B.offB, B.kp, B.rowsB, B.nch, kTileN))
             return FFGPU_ERR_CUDA;
     }
-    InstInfo* infos = reinterpret_cast<InstInfo*>(at(t_inst));
-    ConvJob* convA = reinterpret_cast<ConvJob*>(at(t_convA));
-    ConvJob* convB = reinterpret_cast<ConvJob*>(at(t_convB));
-    long long* bbA = reinterpret_cast<long long*>(at(t_bbA));
-    long long* bbB = reinterpret_cast<long long*>(at(t_bbB));
+    const size_t n_inst = w.size();
+    InstInfo* infos = reinterpret_cast<InstInfo*>(host + L.t_inst);
+    ConvJob* convA = reinterpret_cast<ConvJob*>(host + L.t_convA);
+    ConvJob* convB = reinterpret_cast<ConvJob*>(host + L.t_convB);
+    long long* bbA = reinterpret_cast<long long*>(host + L.t_bbA);
+    long long* bbB = reinterpret_cast<long long*>(host + L.t_bbB);
     long long nbA = 0, nbB = 0;
     for (size_t i = 0; i < n_inst; ++i) {
         const BInst& b = w[i];
         const ffgpu_fgemm_desc& d = *b.d;
-        const Bucket& B = buckets[b.bucket];
+        const Bucket& B = L.buckets[b.bucket];
         fill_inst(infos[i], d.m, d.n, b.kp, b.pl, d.alpha % d.p, d.beta % d.p, d.C, d.ldc);
         infos[i].bucket = b.bucket;
         infos[i].rowA = (int)b.rowA;
@@ -251,7 +252,7 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
         a.rows_pad = (int)b.mpad;
         a.kp = (int)b.kp;
         a.vec_ok = ((reinterpret_cast<uintptr_t>(d.A) & 15) == 0) && (d.lda % 4 == 0);
-        a.dst = reinterpret_cast<uint4*>(ws + B.offA + size_t(b.rowA) * b.kp * 2);
+        a.dst = reinterpret_cast<uint4*>(planes + B.offA + size_t(b.rowA) * b.kp * 2);
         a.plane16 = size_t(B.rowsA) * b.kp / 8;
         a.cp = cp;
         ConvJob& c2 = convB[i];
@@ -262,7 +263,7 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
         c2.rows_pad = (int)b.npad;
         c2.kp = (int)b.kp;
         c2.vec_ok = 0;
-        c2.dst = reinterpret_cast<uint4*>(ws + B.offB + size_t(b.rowB) * b.kp * 2);
+        c2.dst = reinterpret_cast<uint4*>(planes + B.offB + size_t(b.rowB) * b.kp * 2);
         c2.plane16 = size_t(B.rowsB) * b.kp / 8;
         c2.cp = cp;
         bbA[i] = nbA;
@@ -272,46 +273,75 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     }
     bbA[n_inst] = nbA;
     bbB[n_inst] = nbB;
-    std::memcpy(at(t_jobs), jobs.data(), jobs.size() * sizeof(GroupJob));
-    std::memcpy(at(t_cta), cta_begin.data(), cta_begin.size() * sizeof(int));
-    if (cudaMemcpyAsync(ws + t_maps, host, tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return FFGPU_ERR_CUDA;
-    if (stage_idx >= 0) stage_done(stage_idx, s);
-    stage_lk.unlock();
+    L.nbA = nbA;
+    L.nbB = nbB;
+    std::memcpy(host + L.t_jobs, L.jobs.data(), L.jobs.size() * sizeof(GroupJob));
+    std::memcpy(host + L.t_cta, L.cta_begin.data(), L.cta_begin.size() * sizeof(int));
+    return FFGPU_OK;
+}
 
+// The wave's three kernels, its tables already at `tabs` on the device.
+ffgpu_status launch_wave(const std::vector<BInst>& w, const WaveLayout& L, unsigned char* planes,
+                         unsigned char* tabs, int* err, cudaStream_t s) {
+    const int n_inst = (int)w.size();
     if (timed_launch("convert_rows_grouped", s, [&] {
-            return launch_convert_rows_grouped(reinterpret_cast<const ConvJob*>(ws + t_convA),
-                                               reinterpret_cast<const long long*>(ws + t_bbA), (int)n_inst, nbA, s);
+            return launch_convert_rows_grouped(reinterpret_cast<const ConvJob*>(tabs + L.t_convA),
+                                               reinterpret_cast<const long long*>(tabs + L.t_bbA), n_inst, L.nbA,
+                                               s);
         }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
     if (timed_launch("convert_transpose_grouped", s, [&] {
-            return launch_convert_transpose_grouped(reinterpret_cast<const ConvJob*>(ws + t_convB),
-                                                    reinterpret_cast<const long long*>(ws + t_bbB), (int)n_inst,
-                                                    nbB, s);
+            return launch_convert_transpose_grouped(reinterpret_cast<const ConvJob*>(tabs + L.t_convB),
+                                                    reinterpret_cast<const long long*>(tabs + L.t_bbB), n_inst,
+                                                    L.nbB, s);
         }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
     GroupGemmParams P;
-    P.insts = reinterpret_cast<const InstInfo*>(ws + t_inst);
-    P.jobs = reinterpret_cast<const GroupJob*>(ws + t_jobs);
-    P.cta_begin = reinterpret_cast<const int*>(ws + t_cta);
-    P.maps = reinterpret_cast<const CUtensorMap*>(ws + t_maps);
-    P.slots = ws;
+    P.insts = reinterpret_cast<const InstInfo*>(tabs + L.t_inst);
+    P.jobs = reinterpret_cast<const GroupJob*>(tabs + L.t_jobs);
+    P.cta_begin = reinterpret_cast<const int*>(tabs + L.t_cta);
+    P.maps = reinterpret_cast<const CUtensorMap*>(tabs);
+    P.slots = planes;
     P.slot_stride = kSlotBytesPerCta;
-    P.err = pool->err;
-    if (timed_launch("rns_gemm_grouped", s, [&] { return launch_rns_gemm_grouped(P, grid, s); }) != cudaSuccess)
+    P.err = err;
+    if (timed_launch("rns_gemm_grouped", s, [&] { return launch_rns_gemm_grouped(P, L.grid, s); }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
     return FFGPU_OK;
 }
 
-}  // namespace
+// Immediate execution of one wave: workspace from the stream's pool (planes,
+// then tables), table image staged in pinned memory and copied in stream order.
+ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
+    WaveLayout L;
+    layout_wave(w, sms, L);
+    const size_t t0 = align_up(L.plane_bytes, 128);
+    Pool* pool = nullptr;
+    ffgpu_status st = pool_get(s, t0 + L.tab_bytes, &pool);
+    if (st != FFGPU_OK) return st;
+    unsigned char* ws = static_cast<unsigned char*>(pool->ptr);
+    std::unique_lock<std::mutex> stage_lk(g_stage_mu);
+    int stage_idx = -1;
+    std::vector<unsigned char> fallback;
+    unsigned char* host = stage_get(L.tab_bytes, &stage_idx);
+    if (!host) {
+        fallback.resize(L.tab_bytes);
+        host = fallback.data();
+    }
+    std::memset(host, 0, L.tab_bytes);
+    st = fill_wave_tables(w, L, ws, host);
+    if (st != FFGPU_OK) return st;
+    if (cudaMemcpyAsync(ws + t0, host, L.tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FFGPU_ERR_CUDA;
+    if (stage_idx >= 0) stage_done(stage_idx, s);
+    stage_lk.unlock();
+    return launch_wave(w, L, ws, ws + t0, pool->err, s);
+}
 
-ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStream_t s) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const int sms = sm_count(dev);
+// Splits a batch into waves (bounded plane bytes, at most 0xFFFF inner lengths)
+// and single products (k = 0, k beyond one launch's capacity, huge m or n).
+void split_batch(int64_t count, const ffgpu_fgemm_desc* descs, std::vector<std::vector<BInst>>& waves,
+                 std::vector<const ffgpu_fgemm_desc*>& singles) {
     std::vector<BInst> wave;
     std::unordered_set<int64_t> wave_k;
-    std::vector<const ffgpu_fgemm_desc*> singles;  // k = 0, k beyond one launch's capacity, huge m or n
     size_t wave_bytes = 0;
     for (int64_t i = 0; i < count; ++i) {
         const ffgpu_fgemm_desc& d = descs[i];
@@ -328,18 +358,16 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         b.kp = round_up(d.k, kTileK);
         b.mpad = round_up(d.m, kTileM);
         b.npad = round_up(d.n, kTileN);
+        b.bucket = 0;
+        b.rowA = b.rowB = 0;
         if (b.mpad / kTileM > 0xFFFF || b.npad / kTileN > 0xFFFF) {  // tile indices are packed in 16 bits
             singles.push_back(&d);
             continue;
         }
-        b.bucket = 0;
-        b.rowA = b.rowB = 0;
         const size_t bytes = size_t(pl.nch) * (b.mpad + b.npad) * b.kp * 2;
-        // a wave holds at most 0xFFFF distinct inner lengths (k-bucket indices are packed in 16 bits)
         const bool new_k = wave_k.find(b.kp) == wave_k.end();
         if (!wave.empty() && (wave_bytes + bytes > wave_plane_budget() || (new_k && wave_k.size() >= 0xFFFF))) {
-            ffgpu_status st = run_wave(wave, s, sms);
-            if (st != FFGPU_OK) return st;
+            waves.push_back(std::move(wave));
             wave.clear();
             wave_k.clear();
             wave_bytes = 0;
@@ -348,8 +376,20 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         wave_k.insert(b.kp);
         wave_bytes += bytes;
     }
-    if (!wave.empty()) {
-        ffgpu_status st = run_wave(wave, s, sms);
+    if (!wave.empty()) waves.push_back(std::move(wave));
+}
+
+}  // namespace
+
+ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    const int sms = sm_count(dev);
+    std::vector<std::vector<BInst>> waves;
+    std::vector<const ffgpu_fgemm_desc*> singles;
+    split_batch(count, descs, waves, singles);
+    for (auto& w : waves) {
+        ffgpu_status st = run_wave(w, s, sms);
         if (st != FFGPU_OK) return st;
     }
     for (const ffgpu_fgemm_desc* d : singles) {
@@ -361,6 +401,165 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         if (st != FFGPU_OK) return st;
     }
     return FFGPU_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched plan: the same batch laid out once, its tables uploaded once, and
+// its whole launch sequence captured in a CUDA graph; a run is one graph
+// launch.  The plan owns one plane region (the largest wave's), the tables of
+// every wave, a workspace for the single products, and its error word.
+// ---------------------------------------------------------------------------
+struct BatchedPlan {
+    int dev = 0;
+    void* planes = nullptr;
+    void* tabs = nullptr;
+    void* single_ws = nullptr;
+    size_t plane_bytes = 0, tab_bytes = 0, single_bytes = 0;
+    int* err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int waves = 0, singles = 0;
+    size_t nodes = 0;
+};
+
+namespace {
+void plan_free(BatchedPlan* P) {
+    if (!P) return;
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->planes) cudaFree(P->planes);
+    if (P->tabs) cudaFree(P->tabs);
+    if (P->single_ws) cudaFree(P->single_ws);
+    if (P->err) cudaFree(P->err);
+    delete P;
+}
+}  // namespace
+
+ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, BatchedPlan** out) {
+    *out = nullptr;
+    BatchedPlan* P = new BatchedPlan();
+    if (cudaGetDevice(&P->dev) != cudaSuccess) {
+        delete P;
+        return FFGPU_ERR_CUDA;
+    }
+    const int sms = sm_count(P->dev);
+    std::vector<std::vector<BInst>> waves;
+    std::vector<const ffgpu_fgemm_desc*> singles;
+    split_batch(count, descs, waves, singles);
+    std::vector<WaveLayout> layouts(waves.size());
+    std::vector<size_t> tab_off(waves.size());
+    for (size_t i = 0; i < waves.size(); ++i) {
+        layout_wave(waves[i], sms, layouts[i]);
+        P->plane_bytes = std::max(P->plane_bytes, layouts[i].plane_bytes);
+        tab_off[i] = P->tab_bytes;
+        P->tab_bytes = align_up(P->tab_bytes + layouts[i].tab_bytes, 256);
+    }
+    for (const ffgpu_fgemm_desc* d : singles)
+        P->single_bytes = std::max(P->single_bytes, fgemm_ws_bytes(d->m, d->n, d->k, d->p, sms));
+    ffgpu_status st = FFGPU_OK;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (bytes == 0) return true;
+        if (cudaMalloc(ptr, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return false;
+        }
+        return true;
+    };
+    if (!alloc(&P->planes, P->plane_bytes) || !alloc(&P->tabs, P->tab_bytes) ||
+        !alloc(&P->single_ws, P->single_bytes) || !alloc(reinterpret_cast<void**>(&P->err), sizeof(int))) {
+        plan_free(P);
+        return FFGPU_ERR_NOMEM;
+    }
+    cudaMemset(P->err, 0, sizeof(int));
+    // every wave's tables, uploaded once
+    std::vector<unsigned char> host(P->tab_bytes, 0);
+    unsigned char* planes = static_cast<unsigned char*>(P->planes);
+    unsigned char* tabs = static_cast<unsigned char*>(P->tabs);
+    for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
+        st = fill_wave_tables(waves[i], layouts[i], planes, host.data() + tab_off[i]);
+    if (st == FFGPU_OK && P->tab_bytes > 0 &&
+        cudaMemcpy(tabs, host.data(), P->tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = FFGPU_ERR_CUDA;
+    if (st != FFGPU_OK) {
+        plan_free(P);
+        return st;
+    }
+    // capture the launch sequence on a private stream
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(P);
+        return FFGPU_ERR_CUDA;
+    }
+    g_capturing = true;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = FFGPU_ERR_CUDA;
+    for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
+        st = launch_wave(waves[i], layouts[i], planes, tabs + tab_off[i], P->err, cs);
+    for (size_t i = 0; i < singles.size() && st == FFGPU_OK; ++i) {
+        const ffgpu_fgemm_desc* d = singles[i];
+        st = fgemm_run(d->m, d->n, d->k, d->p, d->alpha, d->A, d->lda, d->B, d->ldb, d->beta, d->C, d->ldc,
+                       P->single_ws, P->single_bytes, P->err, cs, 0, true);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    g_capturing = false;
+    cudaStreamDestroy(cs);
+    if (st == FFGPU_OK && (ce != cudaSuccess || g == nullptr)) st = FFGPU_ERR_CUDA;
+    if (st != FFGPU_OK) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        plan_free(P);
+        return st;
+    }
+    P->graph = g;
+    if (cudaGraphInstantiate(&P->exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(P);
+        return FFGPU_ERR_CUDA;
+    }
+    cudaGraphGetNodes(g, nullptr, &P->nodes);
+    P->waves = (int)waves.size();
+    P->singles = (int)singles.size();
+    *out = P;
+    return FFGPU_OK;
+}
+
+ffgpu_status batched_plan_run(BatchedPlan* P, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    if (dev != P->dev) return FFGPU_ERR_INVALID;
+    if (cudaGraphLaunch(P->exec, s) != cudaSuccess) {
+        cudaGetLastError();
+        return FFGPU_ERR_CUDA;
+    }
+    return FFGPU_OK;
+}
+
+ffgpu_status batched_plan_error(BatchedPlan* P) {
+    int v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return FFGPU_ERR_CUDA;
+    }
+    if (cudaMemcpy(&v, P->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return FFGPU_ERR_CUDA;
+    if (v != 0) {
+        cudaMemset(P->err, 0, sizeof(int));
+        return v == kDevSingular ? FFGPU_ERR_INVALID : FFGPU_ERR_TIMEOUT;
+    }
+    return FFGPU_OK;
+}
+
+void batched_plan_destroy(BatchedPlan* P) {
+    if (!P) return;
+    cudaDeviceSynchronize();  // no graph launch of this plan may still be running
+    plan_free(P);
+}
+
+void batched_plan_info(const BatchedPlan* P, int* waves, int* singles, size_t* nodes, size_t* device_bytes) {
+    if (waves) *waves = P->waves;
+    if (singles) *singles = P->singles;
+    if (nodes) *nodes = P->nodes;
+    if (device_bytes) *device_bytes = P->plane_bytes + P->tab_bytes + P->single_bytes + sizeof(int);
 }
 
 }  // namespace ffgpu

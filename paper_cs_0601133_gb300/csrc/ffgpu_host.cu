@@ -147,6 +147,7 @@ static bool g_prof_on = false;
 static std::vector<ProfEntry> g_prof;
 
 bool profiling_on() { return g_prof_on; }
+thread_local bool g_capturing = false;
 
 void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
@@ -544,6 +545,43 @@ ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uin
     ffgpu_status st = pool_get(s, ftrsm_ws_bytes(side, m, n, p, sm_count(dev)), &pool);
     if (st != FFGPU_OK) return st;
     return ftrsm_run(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, pool->ptr, pool->bytes, pool->err, s);
+}
+
+ffgpu_status ffgpu_fgemm_batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs,
+                                             ffgpu_batched_plan** plan) {
+    if (!plan || count < 0 || (count > 0 && !descs)) return FFGPU_ERR_INVALID;
+    for (int64_t i = 0; i < count; ++i) {
+        const ffgpu_fgemm_desc& d = descs[i];
+        if (d.p < 2 || d.p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
+        const ffgpu_status st = check_args(d.m, d.n, d.k, d.p, d.A, d.lda, d.B, d.ldb, d.C, d.ldc);
+        if (st != FFGPU_OK) return st;
+    }
+    BatchedPlan* p = nullptr;
+    const ffgpu_status st = batched_plan_create(count, descs, &p);
+    *plan = reinterpret_cast<ffgpu_batched_plan*>(p);
+    return st;
+}
+
+ffgpu_status ffgpu_fgemm_batched_plan_run(ffgpu_batched_plan* plan, void* stream) {
+    if (!plan) return FFGPU_ERR_INVALID;
+    return batched_plan_run(reinterpret_cast<BatchedPlan*>(plan), static_cast<cudaStream_t>(stream));
+}
+
+ffgpu_status ffgpu_fgemm_batched_plan_error(ffgpu_batched_plan* plan) {
+    if (!plan) return FFGPU_ERR_INVALID;
+    return batched_plan_error(reinterpret_cast<BatchedPlan*>(plan));
+}
+
+ffgpu_status ffgpu_fgemm_batched_plan_info(const ffgpu_batched_plan* plan, int* waves, int* singles,
+                                           size_t* graph_nodes, size_t* device_bytes) {
+    if (!plan) return FFGPU_ERR_INVALID;
+    batched_plan_info(reinterpret_cast<const BatchedPlan*>(plan), waves, singles, graph_nodes, device_bytes);
+    return FFGPU_OK;
+}
+
+ffgpu_status ffgpu_fgemm_batched_plan_destroy(ffgpu_batched_plan* plan) {
+    batched_plan_destroy(reinterpret_cast<BatchedPlan*>(plan));
+    return FFGPU_OK;
 }
 
 ffgpu_status ffgpu_last_device_error(void* stream) {

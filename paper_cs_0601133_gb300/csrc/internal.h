@@ -207,6 +207,12 @@ ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t 
 
 // batched fgemm (batched.cu)
 ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* d, cudaStream_t s);
+struct BatchedPlan;
+ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* d, BatchedPlan** out);
+ffgpu_status batched_plan_run(BatchedPlan* plan, cudaStream_t s);
+ffgpu_status batched_plan_error(BatchedPlan* plan);
+void batched_plan_destroy(BatchedPlan* plan);
+void batched_plan_info(const BatchedPlan* plan, int* waves, int* singles, size_t* nodes, size_t* device_bytes);
 
 // ftrsm (ftrsm.cu)
 size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);
@@ -218,9 +224,13 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint3
 bool profiling_on();
 void profile_record(const char* name, cudaEvent_t start, cudaEvent_t stop);
 
+// Set while this thread captures a launch sequence into a CUDA graph: launches
+// are then recorded without the profiling events.
+extern thread_local bool g_capturing;
+
 template <class F>
 cudaError_t timed_launch(const char* name, cudaStream_t s, F&& launch) {
-    if (!profiling_on()) return launch();
+    if (!profiling_on() || g_capturing) return launch();
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return cudaErrorUnknown;
     cudaEventRecord(a, s);

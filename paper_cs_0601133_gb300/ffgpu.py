@@ -112,6 +112,12 @@ SIGNATURES = {
     "ffgpu_server_get_stats": [_VP, ctypes.POINTER(ServerStats)],
     "ffgpu_server_destroy": [_VP],
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
+    "ffgpu_fgemm_batched_plan_create": [_I64, ctypes.POINTER(FgemmDesc), ctypes.POINTER(_VP)],
+    "ffgpu_fgemm_batched_plan_run": [_VP, _VP],
+    "ffgpu_fgemm_batched_plan_error": [_VP],
+    "ffgpu_fgemm_batched_plan_info": [_VP, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                      ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
+    "ffgpu_fgemm_batched_plan_destroy": [_VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_selftest_wait_timeout": [_I64, _VP],
     "ffgpu_autotune": [_I64, _I64, _I64, _U32, _I32, _VP, ctypes.POINTER(Tuned)],
@@ -324,6 +330,50 @@ def profile_read() -> dict:
     cnt = ctypes.c_int(0)
     check(lib().ffgpu_profile_read(arr, cap, ctypes.byref(cnt)), "profile_read")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(cnt.value, cap))}
+
+
+class BatchedPlan:
+    """A fixed batch of fgemms captured once in a CUDA graph
+    (ffgpu_fgemm_batched_plan_*): run() recomputes every C from the current
+    contents of its A, B and C.  The tensors are kept alive by the plan."""
+
+    def __init__(self, problems):
+        self._problems = list(problems)
+        self._descs, n = batched_descs(self._problems)
+        self._h = _VP()
+        check(lib().ffgpu_fgemm_batched_plan_create(n, self._descs, ctypes.byref(self._h)),
+              "ffgpu_fgemm_batched_plan_create")
+
+    def run(self, stream=None):
+        check(lib().ffgpu_fgemm_batched_plan_run(self._h, _stream_ptr(stream)), "ffgpu_fgemm_batched_plan_run")
+
+    def error(self) -> int:
+        """Synchronizes; the plan's device error word (0 = none), cleared."""
+        return int(lib().ffgpu_fgemm_batched_plan_error(self._h))
+
+    def info(self) -> dict:
+        w, sg = _I32(0), _I32(0)
+        nodes, nbytes = ctypes.c_size_t(0), ctypes.c_size_t(0)
+        check(lib().ffgpu_fgemm_batched_plan_info(self._h, ctypes.byref(w), ctypes.byref(sg), ctypes.byref(nodes),
+                                                  ctypes.byref(nbytes)), "ffgpu_fgemm_batched_plan_info")
+        return {"waves": w.value, "singles": sg.value, "graph_nodes": nodes.value, "device_bytes": nbytes.value}
+
+    def close(self):
+        if self._h:
+            lib().ffgpu_fgemm_batched_plan_destroy(self._h)
+            self._h = _VP()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

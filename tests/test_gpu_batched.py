@@ -112,3 +112,66 @@ def test_many_instances_several_waves_sampled():
             r = rng.integers(0, A.shape[0], 16)
             c = rng.integers(0, B.shape[1], 16)
             assert np.array_equal(got[r, c], oracle.fgemm_entries(A, B, p, al, be, C, r, c))
+
+
+def test_batched_plan_graph_runs_track_inputs():
+    """A captured plan (CUDA graph) gives the oracle's result, and a second run
+    after the inputs change in place gives the new result: the graph reads the
+    buffers, not a snapshot.  The batch mixes moduli of every size class and a
+    k = 0 member (run outside the grouped launch)."""
+    rng = W.rng_for("multimodular", 103)
+    primes = [3, 251, 65521, 8388593, 2147483647]
+    host, dev = [], []
+    for i in range(25):
+        m, n, k = (int(v) for v in W.log_uniform_int(rng, 16, 500, 3))
+        if i == 7:
+            k = 0
+        p = primes[i % len(primes)]
+        A = W.uniform_words(rng, (m, k))
+        B = W.uniform_words(rng, (k, n))
+        C = W.uniform_words(rng, (m, n))
+        al, be = int(rng.integers(0, 2**32)), int(rng.integers(0, 2**32))
+        host.append((A, B, C, p, al, be))
+        dev.append((to_dev(A), to_dev(B), to_dev(C), p, al, be))
+    with ff.BatchedPlan(dev) as plan:
+        info = plan.info()
+        assert info["waves"] >= 1 and info["singles"] == 1 and info["graph_nodes"] >= 3
+        plan.run()
+        assert plan.error() == 0
+        for (A, B, C, p, al, be), d in zip(host, dev):
+            assert np.array_equal(from_dev(d[2]), oracle.fgemm(A, B, p, al, be, C)), (A.shape, B.shape, p)
+        # new contents, same buffers: C holds the first result, A and B are redrawn
+        expect = []
+        for i, ((A, B, C, p, al, be), d) in enumerate(zip(host, dev)):
+            A2 = W.uniform_words(rng, A.shape)
+            B2 = W.uniform_words(rng, B.shape)
+            d[0].copy_(to_dev(A2))
+            d[1].copy_(to_dev(B2))
+            C1 = from_dev(d[2])
+            expect.append(oracle.fgemm(A2, B2, p, al, be, C1))
+        plan.run()
+        assert plan.error() == 0
+        for e, d in zip(expect, dev):
+            assert np.array_equal(from_dev(d[2]), e)
+
+
+def test_batched_plan_equals_immediate_on_multimodular_batch():
+    shapes, primes = W.multimodular_instances(count=64, nprimes=32)
+    use = primes[::8]
+    dev_a, dev_b = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        Ai, Bi = W.multimodular_integers(i, int(m), int(n), int(k))
+        for p in use:
+            A = to_dev(W.reduce_signed(Ai, p))
+            B = to_dev(W.reduce_signed(Bi, p))
+            dev_a.append((A, B, torch.zeros((int(m), int(n)), dtype=torch.int32, device="cuda"), p, 1, 0))
+            dev_b.append((A, B, torch.zeros((int(m), int(n)), dtype=torch.int32, device="cuda"), p, 1, 0))
+    ff.fgemm_batched(dev_a)
+    plan = ff.BatchedPlan(dev_b)
+    plan.run()
+    plan.run()  # idempotent with beta = 0
+    assert plan.error() == 0
+    plan.close()
+    torch.cuda.synchronize()
+    for x, y in zip(dev_a, dev_b):
+        assert torch.equal(x[2], y[2])
