@@ -309,16 +309,26 @@ ffgpu_status launch_wave(const std::vector<BInst>& w, const WaveLayout& L, unsig
     return FFGPU_OK;
 }
 
-// Immediate execution of one wave: workspace from the stream's pool (planes,
-// then tables), table image staged in pinned memory and copied in stream order.
-ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
+// Immediate execution of one wave: workspace (planes, then tables) from the
+// caller (ws != nullptr) or the stream's pool, table image staged in pinned
+// memory and copied in stream order.
+ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_in, size_t ws_bytes, int* err_in) {
     WaveLayout L;
     layout_wave(w, sms, L);
     const size_t t0 = align_up(L.plane_bytes, 128);
-    Pool* pool = nullptr;
-    ffgpu_status st = pool_get(s, t0 + L.tab_bytes, &pool);
-    if (st != FFGPU_OK) return st;
-    unsigned char* ws = static_cast<unsigned char*>(pool->ptr);
+    unsigned char* ws = nullptr;
+    int* errw = err_in;
+    if (ws_in) {
+        if (ws_bytes < t0 + L.tab_bytes) return FFGPU_ERR_NOMEM;
+        ws = static_cast<unsigned char*>(ws_in);
+    } else {
+        Pool* pool = nullptr;
+        ffgpu_status st = pool_get(s, t0 + L.tab_bytes, &pool);
+        if (st != FFGPU_OK) return st;
+        ws = static_cast<unsigned char*>(pool->ptr);
+        errw = pool->err;
+    }
+    ffgpu_status st;
     std::unique_lock<std::mutex> stage_lk(g_stage_mu);
     int stage_idx = -1;
     std::vector<unsigned char> fallback;
@@ -333,7 +343,7 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms) {
     if (cudaMemcpyAsync(ws + t0, host, L.tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FFGPU_ERR_CUDA;
     if (stage_idx >= 0) stage_done(stage_idx, s);
     stage_lk.unlock();
-    return launch_wave(w, L, ws, ws + t0, pool->err, s);
+    return launch_wave(w, L, ws, ws + t0, errw, s);
 }
 
 // Splits a batch into waves (bounded plane bytes, at most 0xFFFF inner lengths)
@@ -389,7 +399,7 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
     std::vector<const ffgpu_fgemm_desc*> singles;
     split_batch(count, descs, waves, singles);
     for (auto& w : waves) {
-        ffgpu_status st = run_wave(w, s, sms);
+        ffgpu_status st = run_wave(w, s, sms, nullptr, 0, nullptr);
         if (st != FFGPU_OK) return st;
     }
     for (const ffgpu_fgemm_desc* d : singles) {
@@ -401,6 +411,43 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
         if (st != FFGPU_OK) return st;
     }
     return FFGPU_OK;
+}
+
+// The same with a caller workspace (for library-internal batches that must
+// stay inside a workspace sized by batched_ws_bytes, e.g. ftrsm's inversion).
+ffgpu_status batched_run_ws(int64_t count, const ffgpu_fgemm_desc* descs, void* ws, size_t ws_bytes, int* err,
+                            cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    const int sms = sm_count(dev);
+    std::vector<std::vector<BInst>> waves;
+    std::vector<const ffgpu_fgemm_desc*> singles;
+    split_batch(count, descs, waves, singles);
+    for (auto& w : waves) {
+        ffgpu_status st = run_wave(w, s, sms, ws, ws_bytes, err);
+        if (st != FFGPU_OK) return st;
+    }
+    for (const ffgpu_fgemm_desc* d : singles) {
+        ffgpu_status st = fgemm_run(d->m, d->n, d->k, d->p, d->alpha, d->A, d->lda, d->B, d->ldb, d->beta, d->C,
+                                    d->ldc, ws, ws_bytes, err, s, 0, false);
+        if (st != FFGPU_OK) return st;
+    }
+    return FFGPU_OK;
+}
+
+// Workspace batched_run_ws needs for a batch (shapes and moduli only).
+size_t batched_ws_bytes(int64_t count, const ffgpu_fgemm_desc* descs, int sms) {
+    std::vector<std::vector<BInst>> waves;
+    std::vector<const ffgpu_fgemm_desc*> singles;
+    split_batch(count, descs, waves, singles);
+    size_t need = 0;
+    for (auto& w : waves) {
+        WaveLayout L;
+        layout_wave(w, sms, L);
+        need = std::max(need, align_up(L.plane_bytes, 128) + L.tab_bytes);
+    }
+    for (const ffgpu_fgemm_desc* d : singles) need = std::max(need, fgemm_ws_bytes(d->m, d->n, d->k, d->p, sms));
+    return need;
 }
 
 // ---------------------------------------------------------------------------

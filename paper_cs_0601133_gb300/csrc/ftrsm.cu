@@ -3,15 +3,23 @@
 // Block recursive algorithm (Algorithm 1, section 4.1): split the triangle in
 // two on a block boundary, solve the first half, update the other half of the
 // right-hand side with one fgemm (B2 <- B2 - T21 X1: alpha = p - 1, beta = 1),
-// solve the second half.  The recursion stops at diagonal blocks of kBlk rows.
-// All diagonal blocks are inverted up front by one kernel (one CTA per block,
+// solve the second half.  The recursion stops at diagonal blocks of L rows,
+// L between 128 and 1024 (about eight leaves), whose inverses are computed up
+// front: one kernel inverts every 128 x 128 diagonal block (one CTA per block,
 // one thread per column of the inverse, substitution mod p; non-unit
 // diagonals inverted by the extended Euclidean algorithm of section 2.1.1; a
-// non-invertible diagonal entry is recorded in the device error word).  A leaf
+// non-invertible diagonal entry is recorded in the device error word), then
+// each doubling level s -> 2s forms the off-diagonal block of every pair
+// [[A, 0], [C, D]] (lower; upper by symmetry) as -D^{-1} (C A^{-1}) with two
+// batched products over all pairs at once (one grouped launch each).  A leaf
 // is then itself a tensor-core product: X_j = T_jj^{-1} B_j (left) or
-// B_j T_jj^{-1} (right), written to a scratch panel and copied back.  alpha is
-// applied once up front.
+// B_j T_jj^{-1} (right), written to a scratch panel and copied back.  Fewer,
+// larger leaves keep the number of launches low (each product has a fixed
+// cost of tens of microseconds); the price is the leaf products, twice the
+// work of solving the leaves.  alpha is applied once up front.
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "devutil.cuh"
 #include "internal.h"
@@ -20,7 +28,15 @@ namespace ffgpu {
 
 namespace {
 
-constexpr int kBlk = 128;   // diagonal block (leaf) size
+constexpr int kBlk = 128;       // diagonal block inverted by substitution
+constexpr int kMaxLeaf = 1024;  // largest leaf
+
+// Leaf size for a triangle of size sz: about eight leaves, 128 to 1024 rows.
+int64_t leaf_size(int64_t sz) {
+    int64_t L = kBlk;
+    while (L < kMaxLeaf && L * 8 < sz) L *= 2;
+    return L;
+}
 
 __device__ uint32_t inv_mod_dev(uint32_t a, uint32_t p) {
     long long r0 = p, r1 = a % p, s0 = 0, s1 = 1;
@@ -52,12 +68,14 @@ struct Acc128 {
 };
 
 // Inverse of diagonal block b of T (rows/cols [b kBlk, b kBlk + tb)), written
-// densely to Inv[b] (kBlk x kBlk, row-major, zeros outside the triangle).
+// densely into the leaf-sized inverse that contains it (kBlk x kBlk, zeros
+// outside the triangle).
 // Thread j computes column j of the inverse: T x = e_j by forward (lower) or
 // back (upper) substitution mod p; x lives in shared memory.
 __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt, int size,
                                                            int upper, int unit, uint32_t p, unsigned long long mu,
-                                                           uint32_t two64p, uint32_t* __restrict__ Inv, int* err) {
+                                                           uint32_t two64p, uint32_t* __restrict__ Inv, int leaf,
+                                                           int* err) {
     extern __shared__ uint32_t sm[];
     uint32_t* sX = sm;                 // [kBlk][kBlk]: x of thread j at sX[i*kBlk + j]
     uint32_t* sD = sm + kBlk * kBlk;   // [kBlk] inverse diagonal
@@ -76,7 +94,9 @@ __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __res
     }
     __syncthreads();
     const int j = threadIdx.x;
-    uint32_t* out = Inv + (size_t)b * kBlk * kBlk;
+    // the block's place on the diagonal of its leaf-sized inverse (row-major, leading dimension `leaf`)
+    const int per = leaf / kBlk;
+    uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
     if (j < tb) {
         for (int s = 0; s < tb; ++s) {
             const int i = upper ? tb - 1 - s : s;
@@ -102,14 +122,15 @@ __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __res
     // dense kBlk x kBlk block (zero padding beyond tb)
     for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) {
         const int r = idx / kBlk, c = idx % kBlk;
-        out[idx] = (r < tb && c < tb) ? sX[r * kBlk + c] : 0u;
+        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[r * kBlk + c] : 0u;
     }
 }
 
 struct TrsmCtx {
     int side, uplo, diag;
     uint32_t p;
-    const uint32_t* inv;   // inverted diagonal blocks, kBlk x kBlk each
+    int64_t L;             // leaf size
+    const uint32_t* inv;   // inverted diagonal leaves, L x L each (leading dimension L)
     uint32_t* panel;       // scratch for one leaf's result
     void* ws;
     size_t ws_bytes;
@@ -123,34 +144,34 @@ ffgpu_status gemm(const TrsmCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al
     return fgemm_run(m, n, k, c.p, alpha, X, ldx, Y, ldy, beta, C, ldc, c.ws, c.ws_bytes, c.err, c.s, 0, false);
 }
 
-// Leaf: diagonal block starting at row/column `off` (global block index off / kBlk) of size tb.
+// Leaf: diagonal block starting at row/column `off` (leaf index off / L) of size tb.
 ffgpu_status leaf(const TrsmCtx& c, int64_t off, int64_t tb, int64_t m, int64_t n, uint32_t* B, int64_t ldb) {
-    const uint32_t* Inv = c.inv + size_t(off / kBlk) * kBlk * kBlk;
+    const uint32_t* Inv = c.inv + size_t(off / c.L) * c.L * c.L;
     ffgpu_status st;
     if (c.side == 0) {  // X = Inv (tb x tb) * B (tb x n)
-        if ((st = gemm(c, tb, n, tb, 1, Inv, kBlk, B, ldb, 0, c.panel, n)) != FFGPU_OK) return st;
+        if ((st = gemm(c, tb, n, tb, 1, Inv, c.L, B, ldb, 0, c.panel, n)) != FFGPU_OK) return st;
         return cudaMemcpy2DAsync(B, ldb * 4, c.panel, n * 4, n * 4, tb, cudaMemcpyDeviceToDevice, c.s) == cudaSuccess
                    ? FFGPU_OK
                    : FFGPU_ERR_CUDA;
     }
     // X = B (m x tb) * Inv (tb x tb)
-    if ((st = gemm(c, m, tb, tb, 1, B, ldb, Inv, kBlk, 0, c.panel, tb)) != FFGPU_OK) return st;
+    if ((st = gemm(c, m, tb, tb, 1, B, ldb, Inv, c.L, 0, c.panel, tb)) != FFGPU_OK) return st;
     return cudaMemcpy2DAsync(B, ldb * 4, c.panel, tb * 4, tb * 4, m, cudaMemcpyDeviceToDevice, c.s) == cudaSuccess
                ? FFGPU_OK
                : FFGPU_ERR_CUDA;
 }
 
-// Split on a block boundary: the first half of the blocks.
-int64_t split(int64_t sz) {
-    const int64_t nb = (sz + kBlk - 1) / kBlk;
-    return (nb / 2) * kBlk;
+// Split on a leaf boundary: the first half of the leaves.
+int64_t split(int64_t sz, int64_t L) {
+    const int64_t nb = (sz + L - 1) / L;
+    return (nb / 2) * L;
 }
 
 // Solve on the diagonal range [off, off + sz) of T.  side L: B is sz x n; side R: B is m x sz.
 ffgpu_status rec(const TrsmCtx& c, int64_t off, int64_t sz, int64_t m, int64_t n, const uint32_t* T, int64_t ldt,
                  uint32_t* B, int64_t ldb) {
-    if (sz <= kBlk) return leaf(c, off, sz, m, n, B, ldb);
-    const int64_t h = split(sz), r = sz - h;
+    if (sz <= c.L) return leaf(c, off, sz, m, n, B, ldb);
+    const int64_t h = split(sz, c.L), r = sz - h;
     const uint32_t* T12 = T + h;
     const uint32_t* T21 = T + h * ldt;
     const uint32_t* T22 = T + h * ldt + h;
@@ -184,43 +205,120 @@ ffgpu_status rec(const TrsmCtx& c, int64_t off, int64_t sz, int64_t m, int64_t n
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-}  // namespace
+// The two batched products of doubling level s -> 2s (every pair of s-blocks
+// inside a leaf): step 0 forms C A^{-1} (lower) or C D^{-1} (upper) into tmp,
+// step 1 the off-diagonal block of the inverse, (p - 1) D^{-1} tmp (lower) or
+// (p - 1) A^{-1} tmp (upper).  With null pointers it gives the shapes only.
+void doubling_descs(int64_t sz, int64_t L, int64_t s, int uplo, uint32_t p, const uint32_t* T, int64_t ldt,
+                    uint32_t* inv, uint32_t* tmp, int step, std::vector<ffgpu_fgemm_desc>& out) {
+    const uint32_t* dummy = reinterpret_cast<const uint32_t*>(uintptr_t(256));  // shapes only: never dereferenced
+    int64_t pair = 0;
+    for (int64_t q0 = 0; q0 < sz; q0 += L) {
+        const int64_t Lq = std::min(L, sz - q0);
+        uint32_t* Iq = inv ? inv + size_t(q0 / L) * L * L : nullptr;
+        for (int64_t ps = 0; ps + s < Lq; ps += 2 * s, ++pair) {
+            const int64_t ds = std::min(s, Lq - ps - s);  // size of the second block
+            const int64_t g = q0 + ps;
+            uint32_t* tm = tmp ? tmp + size_t(pair) * s * s : nullptr;
+            ffgpu_fgemm_desc d;
+            std::memset(&d, 0, sizeof(d));
+            d.p = p;
+            d.beta = 0;
+            if (uplo == 0) {  // [[A, 0], [C, D]]: inverse block (1,0) = -D^{-1} C A^{-1}
+                if (step == 0) {
+                    d.m = ds; d.n = s; d.k = s; d.alpha = 1;
+                    d.A = T ? T + (g + s) * ldt + g : dummy; d.lda = ldt;
+                    d.B = Iq ? Iq + ps * L + ps : dummy; d.ldb = L;
+                    d.C = tm ? tm : const_cast<uint32_t*>(dummy); d.ldc = s;
+                } else {
+                    d.m = ds; d.n = s; d.k = ds; d.alpha = p - 1;
+                    d.A = Iq ? Iq + (ps + s) * L + ps + s : dummy; d.lda = L;
+                    d.B = tm ? tm : dummy; d.ldb = s;
+                    d.C = Iq ? Iq + (ps + s) * L + ps : const_cast<uint32_t*>(dummy); d.ldc = L;
+                }
+            } else {  // [[A, C], [0, D]]: inverse block (0,1) = -A^{-1} C D^{-1}
+                if (step == 0) {
+                    d.m = s; d.n = ds; d.k = ds; d.alpha = 1;
+                    d.A = T ? T + g * ldt + g + s : dummy; d.lda = ldt;
+                    d.B = Iq ? Iq + (ps + s) * L + ps + s : dummy; d.ldb = L;
+                    d.C = tm ? tm : const_cast<uint32_t*>(dummy); d.ldc = ds;
+                } else {
+                    d.m = s; d.n = ds; d.k = s; d.alpha = p - 1;
+                    d.A = Iq ? Iq + ps * L + ps : dummy; d.lda = L;
+                    d.B = tm ? tm : dummy; d.ldb = ds;
+                    d.C = Iq ? Iq + ps * L + ps + s : const_cast<uint32_t*>(dummy); d.ldc = L;
+                }
+            }
+            out.push_back(d);
+        }
+    }
+}
 
-// Workspace: inverted blocks | leaf panel | the largest fgemm's workspace.
-size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms) {
+struct TrsmLayout {
+    int64_t L, nl;
+    size_t inv, panel, tmp, rest;  // byte offsets; rest = start of the fgemm / batched workspace
+    size_t fg;                     // bytes the products need
+};
+
+TrsmLayout trsm_layout(int side, int64_t m, int64_t n, uint32_t p, int sms) {
+    TrsmLayout Y;
     const int64_t sz = side == 0 ? m : n, rhs = side == 0 ? n : m;
-    const int64_t nb = (sz + kBlk - 1) / kBlk;
-    size_t fg = fgemm_ws_bytes(side == 0 ? kBlk : rhs, side == 0 ? rhs : kBlk, kBlk, p, sms);
-    if (sz > kBlk) {
-        const int64_t h = split(sz), r = sz - h;
+    Y.L = leaf_size(sz);
+    Y.nl = (sz + Y.L - 1) / Y.L;
+    Y.inv = 0;
+    Y.panel = align256(size_t(Y.nl) * Y.L * Y.L * 4);
+    Y.tmp = Y.panel + align256(size_t(Y.L) * rhs * 4);
+    Y.rest = Y.tmp + align256(size_t(sz) * Y.L / 2 * 4 + 4);
+    size_t fg = fgemm_ws_bytes(side == 0 ? Y.L : rhs, side == 0 ? rhs : Y.L, Y.L, p, sms);
+    if (sz > Y.L) {
+        const int64_t h = split(sz, Y.L), r = sz - h;
         if (side == 0)
             fg = std::max(fg, std::max(fgemm_ws_bytes(r, n, h, p, sms), fgemm_ws_bytes(h, n, r, p, sms)));
         else
             fg = std::max(fg, std::max(fgemm_ws_bytes(m, r, h, p, sms), fgemm_ws_bytes(m, h, r, p, sms)));
     }
-    return align256(size_t(nb) * kBlk * kBlk * 4) + align256(size_t(kBlk) * rhs * 4) + align256(fg);
+    for (int64_t s = kBlk; s < Y.L; s *= 2)
+        for (int uplo = 0; uplo < 2; ++uplo)
+            for (int step = 0; step < 2; ++step) {
+                std::vector<ffgpu_fgemm_desc> d;
+                doubling_descs(sz, Y.L, s, uplo, p, nullptr, sz, nullptr, nullptr, step, d);
+                if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
+            }
+    Y.fg = fg;
+    return Y;
+}
+
+}  // namespace
+
+// Workspace: leaf inverses | leaf panel | doubling temporaries | the largest product's workspace.
+size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms) {
+    const TrsmLayout Y = trsm_layout(side, m, n, p, sms);
+    return Y.rest + align256(Y.fg);
 }
 
 ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
                        const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s) {
-    const int64_t sz = side == 0 ? m : n, rhs = side == 0 ? n : m;
-    const int64_t nb = (sz + kBlk - 1) / kBlk;
-    const size_t inv_bytes = align256(size_t(nb) * kBlk * kBlk * 4);
-    const size_t panel_bytes = align256(size_t(kBlk) * rhs * 4);
-    if (ws_bytes < inv_bytes + panel_bytes) return FFGPU_ERR_NOMEM;
+    const int64_t sz = side == 0 ? m : n;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const TrsmLayout Y = trsm_layout(side, m, n, p, sm_count(dev));
+    if (ws_bytes < Y.rest) return FFGPU_ERR_NOMEM;
     unsigned char* w = static_cast<unsigned char*>(ws);
     TrsmCtx c;
     c.side = side;
     c.uplo = uplo;
     c.diag = diag;
     c.p = p;
-    c.inv = reinterpret_cast<uint32_t*>(w);
-    c.panel = reinterpret_cast<uint32_t*>(w + inv_bytes);
-    c.ws = w + inv_bytes + panel_bytes;
-    c.ws_bytes = ws_bytes - inv_bytes - panel_bytes;
+    c.L = Y.L;
+    c.inv = reinterpret_cast<uint32_t*>(w + Y.inv);
+    c.panel = reinterpret_cast<uint32_t*>(w + Y.panel);
+    c.ws = w + Y.rest;
+    c.ws_bytes = ws_bytes - Y.rest;
     c.err = err;
     c.s = s;
+    uint32_t* inv = const_cast<uint32_t*>(c.inv);
+    uint32_t* tmp = reinterpret_cast<uint32_t*>(w + Y.tmp);
     const unsigned long long mu = ~0ull / p;
     const uint32_t two64p = (uint32_t)(((unsigned __int128)1 << 64) % p);
     const uint32_t al = alpha % p;
@@ -229,6 +327,8 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint3
             cudaSuccess)
             return FFGPU_ERR_CUDA;
     }
+    // leaf inverses: zero (the other triangle), 128-blocks by substitution, then doubling
+    if (cudaMemsetAsync(inv, 0, size_t(Y.nl) * Y.L * Y.L * 4, s) != cudaSuccess) return FFGPU_ERR_CUDA;
     const size_t smem = size_t(kBlk) * kBlk * 4 + kBlk * 4;
     static bool attr_set = false;
     if (!attr_set) {
@@ -237,12 +337,22 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint3
             return FFGPU_ERR_CUDA;
         attr_set = true;
     }
+    const int nb = (int)((sz + kBlk - 1) / kBlk);
     if (timed_launch("trsm_invert_blocks", s, [&] {
-            trsm_invert_blocks<<<(int)nb, kBlk, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p,
-                                                          const_cast<uint32_t*>(c.inv), err);
+            trsm_invert_blocks<<<nb, kBlk, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p, inv, (int)Y.L,
+                                                      err);
             return cudaGetLastError();
         }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
+    for (int64_t lv = kBlk; lv < Y.L; lv *= 2) {
+        for (int step = 0; step < 2; ++step) {
+            std::vector<ffgpu_fgemm_desc> d;
+            doubling_descs(sz, Y.L, lv, uplo, p, T, ldt, inv, tmp, step, d);
+            if (d.empty()) continue;
+            const ffgpu_status st = batched_run_ws((int64_t)d.size(), d.data(), c.ws, c.ws_bytes, err, s);
+            if (st != FFGPU_OK) return st;
+        }
+    }
     return rec(c, 0, sz, m, n, T, ldt, B, ldb);
 }
 

@@ -207,6 +207,9 @@ ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t 
 
 // batched fgemm (batched.cu)
 ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* d, cudaStream_t s);
+ffgpu_status batched_run_ws(int64_t count, const ffgpu_fgemm_desc* d, void* ws, size_t ws_bytes, int* err,
+                            cudaStream_t s);
+size_t batched_ws_bytes(int64_t count, const ffgpu_fgemm_desc* d, int sms);
 struct BatchedPlan;
 ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* d, BatchedPlan** out);
 ffgpu_status batched_plan_run(BatchedPlan* plan, cudaStream_t s);

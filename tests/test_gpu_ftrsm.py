@@ -1,7 +1,9 @@
 """GPU parity of ffgpu_ftrsm (section 4, Algorithm 1) against the CPU oracle.
 
-Sizes cross the 64-row leaf several times (recursion depth 2-4), with ragged
-splits, both sides, both triangles, unit and non-unit diagonals, and alpha.
+Sizes cross the leaf size several times (the leaves grow from 128 to 1024
+rows with the triangle, their inverses built by 128-block substitution and
+0-3 doubling levels of batched products), with ragged splits and ragged last
+leaves, both sides, both triangles, unit and non-unit diagonals, and alpha.
 A larger solve is checked by its residual op(T) X = alpha B with Freivalds'
 test (random vectors, exact matrix-vector products on the CPU)."""
 import numpy as np
@@ -81,3 +83,33 @@ def test_singular_diagonal_is_reported():
     assert rc == -1  # FFGPU_ERR_INVALID
     # the record is cleared once read
     assert ff.last_device_error() == 0
+
+
+@pytest.mark.parametrize("p", [65521, 2147483647])
+@pytest.mark.parametrize("side,uplo,diag", [("L", "L", "U"), ("L", "U", "N"), ("R", "U", "U"), ("R", "L", "N"),
+                                            ("L", "L", "N"), ("R", "U", "N")])
+def test_doubling_levels_and_ragged_leaves(p, side, uplo, diag):
+    """2500-row triangle: 512-row leaves (two doubling levels 128 -> 256 ->
+    512), the last leaf 452 rows, the last 128-block 68 rows."""
+    rng = W.rng_for("ftrsm", 8, p, ord(side), ord(uplo), ord(diag))
+    nt, nrhs = 2500, 96
+    m, n = (nt, nrhs) if side == "L" else (nrhs, nt)
+    T = W.triangular(rng, nt, p, uplo, diag == "U")
+    B = W.uniform_words(rng, (m, n))
+    alpha = int(rng.integers(1, p))
+    got, rc = solve(T, B, p, alpha, side, uplo, diag)
+    assert rc == 0
+    assert np.array_equal(got, oracle.ftrsm(T, B, p, alpha, side, uplo, diag))
+
+
+def test_three_doubling_levels_four_row_last_leaf():
+    """4100 rows: 1024-row leaves (doubling 128 -> ... -> 1024), a last leaf
+    of 4 rows."""
+    p = 2147483647
+    rng = W.rng_for("ftrsm", 9)
+    nt, nrhs = 4100, 40
+    T = W.triangular(rng, nt, p, "L", False)
+    B = W.uniform_residues(rng, (nt, nrhs), p)
+    got, rc = solve(T, B, p, 5, "L", "L", "N")
+    assert rc == 0
+    assert np.array_equal(got, oracle.ftrsm(T, B, p, 5, "L", "L", "N"))
