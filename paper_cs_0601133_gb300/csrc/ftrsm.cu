@@ -77,12 +77,17 @@ __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __res
                                                            uint32_t two64p, uint32_t* __restrict__ Inv, int leaf,
                                                            int* err) {
     extern __shared__ uint32_t sm[];
-    uint32_t* sX = sm;                 // [kBlk][kBlk]: x of thread j at sX[i*kBlk + j]
-    uint32_t* sD = sm + kBlk * kBlk;   // [kBlk] inverse diagonal
+    uint32_t* sX = sm;                     // [kBlk][kBlk]: x of thread j at sX[i*kBlk + j]
+    uint32_t* sT = sm + kBlk * kBlk;       // [kBlk][kBlk]: the block of T (read by every column's substitution)
+    uint32_t* sD = sm + 2 * kBlk * kBlk;   // [kBlk] inverse diagonal
     const int b = blockIdx.x;
     const int base = b * kBlk;
     const int tb = min(kBlk, size - base);
     const uint32_t* Tb = T + (long long)base * ldt + base;
+    for (int idx = threadIdx.x; idx < tb * kBlk; idx += blockDim.x) {
+        const int r = idx / kBlk, c = idx % kBlk;
+        sT[idx] = c < tb ? __ldg(Tb + (long long)r * ldt + c) : 0u;
+    }
     for (int i = threadIdx.x; i < tb; i += blockDim.x) {
         if (unit) {
             sD[i] = 1u;
@@ -108,8 +113,8 @@ __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __res
                 const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
                 // any 32-bit word times a residue < 2^31 stays below 2^63; the
                 // 128-bit sum of at most kBlk of them is reduced once
-                for (int l = lo; l < hi; ++l)
-                    acc.add((unsigned long long)__ldg(Tb + (long long)i * ldt + l) * sX[l * kBlk + j]);
+                const uint32_t* Ti = sT + i * kBlk;
+                for (int l = lo; l < hi; ++l) acc.add((unsigned long long)Ti[l] * sX[l * kBlk + j]);
                 const uint32_t sum = acc.mod(p, mu, two64p);
                 const uint32_t rhs = (i == j) ? 1u : 0u;
                 const uint32_t t = rhs >= sum ? rhs - sum : rhs + (p - sum);
@@ -329,7 +334,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint3
     }
     // leaf inverses: zero (the other triangle), 128-blocks by substitution, then doubling
     if (cudaMemsetAsync(inv, 0, size_t(Y.nl) * Y.L * Y.L * 4, s) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const size_t smem = size_t(kBlk) * kBlk * 4 + kBlk * 4;
+    const size_t smem = 2 * size_t(kBlk) * kBlk * 4 + kBlk * 4;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(trsm_invert_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
