@@ -257,6 +257,50 @@ FFGPU_API ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc
  * ffgpu_fgemm_batched_plan_destroy synchronizes the device and frees the plan
  * (NULL is accepted).
  */
+/*
+ * Multi-modular products from one exact integer product: for integer
+ * matrices A (m x k) and B (k x n), int32 row-major on the device, every entry
+ * of magnitude at most 2^bits (1 <= bits <= 30, and k 2^(2 bits) < 2^62 so
+ * that A B fits in int64), writes C_i = (A B) mod p_i in [0, p_i) for each of
+ * the nprimes moduli (1 <= nprimes <= 64, 2 <= p_i < 2^31; primes is a HOST
+ * array, C a HOST array of nprimes device pointers, each an m x n uint32
+ * matrix with leading dimension ldc).  Computes the integer product once
+ * (channel residues of A and B, the tensor-core channel products, the exact
+ * 64-bit reconstruction) and then reduces it modulo every p_i -- the
+ * multi-modular use the paper cites for its routines (introduction; section 7:
+ * the Chinese remainder algorithm) -- instead of one fgemm per prime.  Entries
+ * beyond 2^bits in magnitude give undefined results.  Asynchronous on
+ * `stream`; workspace from the stream's pool.  Errors: FFGPU_ERR_INVALID
+ * (shapes, bits, the int64 bound, null pointers), FFGPU_ERR_UNSUPPORTED_P,
+ * FFGPU_ERR_NOMEM, FFGPU_ERR_CUDA.  No C_i may overlap A, B or another C_j.
+ */
+FFGPU_API ffgpu_status ffgpu_fgemm_multimod(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda,
+                                            const int32_t* B, int64_t ldb, int nprimes, const uint32_t* primes,
+                                            uint32_t* const* C, int64_t ldc, void* stream);
+
+/*
+ * Batched multi-modular products (the configuration of many integer
+ * instances, each reduced modulo the same primes): for every descriptor,
+ * C[i] = (A B) mod primes[i] as ffgpu_fgemm_multimod would compute it, with
+ * the instances' exact products done in grouped launches (one grouped
+ * conversion per operand, one persistent integer-mode tensor-core launch and
+ * one grouped fan-out per wave of instances).  descs is a HOST array; each
+ * descriptor's C is a HOST array of nprimes device pointers (m x n uint32,
+ * leading dimension ldc).  Same bounds and errors as ffgpu_fgemm_multimod,
+ * checked for every descriptor before anything is enqueued.
+ */
+typedef struct {
+    int64_t m, n, k;
+    const int32_t* A;
+    int64_t lda;
+    const int32_t* B;
+    int64_t ldb;
+    uint32_t* const* C;
+    int64_t ldc;
+} ffgpu_multimod_desc;
+FFGPU_API ffgpu_status ffgpu_fgemm_multimod_batched(int64_t count, const ffgpu_multimod_desc* descs, int bits,
+                                                    int nprimes, const uint32_t* primes, void* stream);
+
 typedef struct ffgpu_batched_plan ffgpu_batched_plan;
 FFGPU_API ffgpu_status ffgpu_fgemm_batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs,
                                                        ffgpu_batched_plan** plan);

@@ -109,9 +109,15 @@ struct WaveLayout {
     size_t plane_bytes = 0;
     size_t t_inst = 0, t_jobs = 0, t_cta = 0, t_convA = 0, t_convB = 0, t_bbA = 0, t_bbB = 0, tab_bytes = 0;
     long long nbA = 0, nbB = 0;  // conversion blocks
+    // integer mode: per-instance int64 results (in the plane region) and the fan-out tables
+    std::vector<size_t> xoff;
+    size_t t_fan = 0, t_fanbb = 0, t_cptr = 0;
+    long long nbF = 0;
 };
 
-void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L) {
+int64_t x_ld(int64_t n) { return (n + 1) / 2 * 2; }
+
+void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L, const MultiCtx* mc) {
     std::unordered_map<int64_t, int> bucket_of;
     for (auto& b : w) {
         int idx;
@@ -193,8 +199,15 @@ void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L) {
         B.offB = off;
         off = align_up(off + size_t(B.nch) * B.rowsB * B.kp * 2, 256);
     }
+    if (mc) {  // exact int64 products
+        L.xoff.resize(w.size());
+        for (size_t i = 0; i < w.size(); ++i) {
+            L.xoff[i] = off;
+            off = align_up(off + size_t(w[i].d->m) * x_ld(w[i].d->n) * 8, 256);
+        }
+    }
     L.plane_bytes = off;
-    // tables: maps | instances | jobs | cta_begin | conversion jobs | prefix sums
+    // tables: maps | instances | jobs | cta_begin | conversion jobs | prefix sums [| fan-out tables]
     const size_t n_inst = w.size();
     L.t_inst = align_up(2 * L.buckets.size() * sizeof(CUtensorMap), 64);
     L.t_jobs = align_up(L.t_inst + n_inst * sizeof(InstInfo), 64);
@@ -204,12 +217,18 @@ void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L) {
     L.t_bbA = align_up(L.t_convB + n_inst * sizeof(ConvJob), 64);
     L.t_bbB = align_up(L.t_bbA + (n_inst + 1) * sizeof(long long), 64);
     L.tab_bytes = align_up(L.t_bbB + (n_inst + 1) * sizeof(long long), 256);
+    if (mc) {
+        L.t_fan = L.tab_bytes;
+        L.t_fanbb = align_up(L.t_fan + n_inst * sizeof(FanInst), 64);
+        L.t_cptr = align_up(L.t_fanbb + (n_inst + 1) * sizeof(long long), 64);
+        L.tab_bytes = align_up(L.t_cptr + n_inst * size_t(mc->nprimes) * sizeof(uint32_t*), 256);
+    }
 }
 
 // Host image of the tables (L.tab_bytes at `host`, zeroed by the caller) for
 // planes at `planes` on the device.
 ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsigned char* planes,
-                              unsigned char* host) {
+                              unsigned char* host, const MultiCtx* mc) {
     CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(host);
     for (size_t bi = 0; bi < L.buckets.size(); ++bi) {
         const Bucket& B = L.buckets[bi];
@@ -228,7 +247,10 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
         const BInst& b = w[i];
         const ffgpu_fgemm_desc& d = *b.d;
         const Bucket& B = L.buckets[b.bucket];
-        fill_inst(infos[i], d.m, d.n, b.kp, b.pl, d.alpha % d.p, d.beta % d.p, d.C, d.ldc);
+        if (mc)
+            fill_inst_int(infos[i], d.m, d.n, b.kp, b.pl, reinterpret_cast<long long*>(planes + L.xoff[i]), x_ld(d.n));
+        else
+            fill_inst(infos[i], d.m, d.n, b.kp, b.pl, d.alpha % d.p, d.beta % d.p, d.C, d.ldc);
         infos[i].bucket = b.bucket;
         infos[i].rowA = (int)b.rowA;
         infos[i].rowB = (int)b.rowB;
@@ -240,6 +262,7 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
         cp.mu32 = 0xFFFFFFFFu / cp.p;
         cp.nch = b.pl.nch;
         cp.direct = b.pl.mode == 1;
+        cp.signed_input = mc ? 1 : 0;
         for (int c = 0; c < b.pl.nch; ++c) {
             cp.mod[c] = b.pl.mod[c];
             cp.magic32[c] = (uint32_t)(((1ull << 39) + b.pl.mod[c] - 1) / b.pl.mod[c]);
@@ -275,6 +298,27 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
     bbB[n_inst] = nbB;
     L.nbA = nbA;
     L.nbB = nbB;
+    if (mc) {
+        FanInst* fan = reinterpret_cast<FanInst*>(host + L.t_fan);
+        long long* fbb = reinterpret_cast<long long*>(host + L.t_fanbb);
+        uint32_t** cp = reinterpret_cast<uint32_t**>(host + L.t_cptr);
+        long long nbF = 0;
+        for (size_t i = 0; i < n_inst; ++i) {
+            const ffgpu_fgemm_desc& d = *w[i].d;
+            const ffgpu_multimod_desc& md = mc->mdescs[w[i].d - mc->pseudo];
+            fan[i].X = reinterpret_cast<const long long*>(planes + L.xoff[i]);
+            fan[i].ldx = x_ld(d.n);
+            fan[i].ldc = md.ldc;
+            fan[i].m = (int)d.m;
+            fan[i].n = (int)d.n;
+            fan[i].cbase = (int)(i * mc->nprimes);
+            for (int q = 0; q < mc->nprimes; ++q) cp[i * mc->nprimes + q] = md.C[q];
+            fbb[i] = nbF;
+            nbF += multimod_fanout_blocks((int)d.m, (int)d.n);
+        }
+        fbb[n_inst] = nbF;
+        L.nbF = nbF;
+    }
     std::memcpy(host + L.t_jobs, L.jobs.data(), L.jobs.size() * sizeof(GroupJob));
     std::memcpy(host + L.t_cta, L.cta_begin.data(), L.cta_begin.size() * sizeof(int));
     return FFGPU_OK;
@@ -282,7 +326,7 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
 
 // The wave's three kernels, its tables already at `tabs` on the device.
 ffgpu_status launch_wave(const std::vector<BInst>& w, const WaveLayout& L, unsigned char* planes,
-                         unsigned char* tabs, int* err, cudaStream_t s) {
+                         unsigned char* tabs, int* err, cudaStream_t s, const MultiCtx* mc) {
     const int n_inst = (int)w.size();
     if (timed_launch("convert_rows_grouped", s, [&] {
             return launch_convert_rows_grouped(reinterpret_cast<const ConvJob*>(tabs + L.t_convA),
@@ -304,17 +348,35 @@ ffgpu_status launch_wave(const std::vector<BInst>& w, const WaveLayout& L, unsig
     P.slots = planes;
     P.slot_stride = kSlotBytesPerCta;
     P.err = err;
-    if (timed_launch("rns_gemm_grouped", s, [&] { return launch_rns_gemm_grouped(P, L.grid, s); }) != cudaSuccess)
+    if (timed_launch(mc ? "rns_gemm_grouped_int" : "rns_gemm_grouped", s,
+                     [&] { return launch_rns_gemm_grouped(P, L.grid, s, mc != nullptr); }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
+    if (mc) {
+        FanPrimes F;
+        std::memset(&F, 0, sizeof(F));
+        F.nprimes = mc->nprimes;
+        for (int q = 0; q < mc->nprimes; ++q) {
+            F.p[q] = mc->primes[q];
+            F.mu[q] = ~0ull / mc->primes[q];
+        }
+        if (timed_launch("multimod_fanout_grouped", s, [&] {
+                return launch_multimod_fanout_grouped(reinterpret_cast<const FanInst*>(tabs + L.t_fan),
+                                                      reinterpret_cast<const long long*>(tabs + L.t_fanbb), n_inst,
+                                                      L.nbF, reinterpret_cast<uint32_t* const*>(tabs + L.t_cptr), F,
+                                                      s);
+            }) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+    }
     return FFGPU_OK;
 }
 
 // Immediate execution of one wave: workspace (planes, then tables) from the
 // caller (ws != nullptr) or the stream's pool, table image staged in pinned
 // memory and copied in stream order.
-ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_in, size_t ws_bytes, int* err_in) {
+ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_in, size_t ws_bytes, int* err_in,
+                      const MultiCtx* mc = nullptr) {
     WaveLayout L;
-    layout_wave(w, sms, L);
+    layout_wave(w, sms, L, mc);
     const size_t t0 = align_up(L.plane_bytes, 128);
     unsigned char* ws = nullptr;
     int* errw = err_in;
@@ -338,12 +400,12 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_i
         host = fallback.data();
     }
     std::memset(host, 0, L.tab_bytes);
-    st = fill_wave_tables(w, L, ws, host);
+    st = fill_wave_tables(w, L, ws, host, mc);
     if (st != FFGPU_OK) return st;
     if (cudaMemcpyAsync(ws + t0, host, L.tab_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FFGPU_ERR_CUDA;
     if (stage_idx >= 0) stage_done(stage_idx, s);
     stage_lk.unlock();
-    return launch_wave(w, L, ws, ws + t0, errw, s);
+    return launch_wave(w, L, ws, ws + t0, errw, s, mc);
 }
 
 // Splits a batch into waves (bounded plane bytes, at most 0xFFFF inner lengths)
@@ -435,6 +497,54 @@ ffgpu_status batched_run_ws(int64_t count, const ffgpu_fgemm_desc* descs, void* 
     return FFGPU_OK;
 }
 
+// Integer-mode batch: the planner sees each instance as a product "mod" the
+// plan's magnitude modulus writing to an int64 result; the waves fan the
+// results out to the primes.
+ffgpu_status batched_multimod_run(int64_t count, const ffgpu_multimod_desc* md, int bits, int nprimes,
+                                  const uint32_t* primes, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    const int sms = sm_count(dev);
+    std::vector<ffgpu_fgemm_desc> pseudo((size_t)count);
+    const uint32_t pm = multimod_plan_modulus(bits);
+    for (int64_t i = 0; i < count; ++i) {
+        ffgpu_fgemm_desc& d = pseudo[i];
+        std::memset(&d, 0, sizeof(d));
+        d.m = md[i].m;
+        d.n = md[i].n;
+        d.k = md[i].k;
+        d.p = pm;
+        d.alpha = 1;
+        d.A = reinterpret_cast<const uint32_t*>(md[i].A);
+        d.lda = md[i].lda;
+        d.B = reinterpret_cast<const uint32_t*>(md[i].B);
+        d.ldb = md[i].ldb;
+    }
+    MultiCtx mc;
+    mc.bits = bits;
+    mc.nprimes = nprimes;
+    mc.primes = primes;
+    mc.mdescs = md;
+    mc.pseudo = pseudo.data();
+    std::vector<std::vector<BInst>> waves;
+    std::vector<const ffgpu_fgemm_desc*> singles;
+    split_batch(count, pseudo.data(), waves, singles);
+    for (auto& w : waves) {
+        ffgpu_status st = run_wave(w, s, sms, nullptr, 0, nullptr, &mc);
+        if (st != FFGPU_OK) return st;
+    }
+    for (const ffgpu_fgemm_desc* d : singles) {  // k = 0 or shapes beyond the grouped launch
+        const ffgpu_multimod_desc& x = md[d - pseudo.data()];
+        Pool* pool = nullptr;
+        ffgpu_status st = pool_get(s, multimod_ws_bytes(x.m, x.n, x.k, bits, sms), &pool);
+        if (st != FFGPU_OK) return st;
+        st = multimod_run(x.m, x.n, x.k, bits, x.A, x.lda, x.B, x.ldb, nprimes, primes, x.C, x.ldc, pool->ptr,
+                          pool->bytes, pool->err, s);
+        if (st != FFGPU_OK) return st;
+    }
+    return FFGPU_OK;
+}
+
 // Workspace batched_run_ws needs for a batch (shapes and moduli only).
 size_t batched_ws_bytes(int64_t count, const ffgpu_fgemm_desc* descs, int sms) {
     std::vector<std::vector<BInst>> waves;
@@ -443,7 +553,7 @@ size_t batched_ws_bytes(int64_t count, const ffgpu_fgemm_desc* descs, int sms) {
     size_t need = 0;
     for (auto& w : waves) {
         WaveLayout L;
-        layout_wave(w, sms, L);
+        layout_wave(w, sms, L, nullptr);
         need = std::max(need, align_up(L.plane_bytes, 128) + L.tab_bytes);
     }
     for (const ffgpu_fgemm_desc* d : singles) need = std::max(need, fgemm_ws_bytes(d->m, d->n, d->k, d->p, sms));
@@ -496,7 +606,7 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     std::vector<WaveLayout> layouts(waves.size());
     std::vector<size_t> tab_off(waves.size());
     for (size_t i = 0; i < waves.size(); ++i) {
-        layout_wave(waves[i], sms, layouts[i]);
+        layout_wave(waves[i], sms, layouts[i], nullptr);
         P->plane_bytes = std::max(P->plane_bytes, layouts[i].plane_bytes);
         tab_off[i] = P->tab_bytes;
         P->tab_bytes = align_up(P->tab_bytes + layouts[i].tab_bytes, 256);
@@ -524,7 +634,7 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     unsigned char* planes = static_cast<unsigned char*>(P->planes);
     unsigned char* tabs = static_cast<unsigned char*>(P->tabs);
     for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
-        st = fill_wave_tables(waves[i], layouts[i], planes, host.data() + tab_off[i]);
+        st = fill_wave_tables(waves[i], layouts[i], planes, host.data() + tab_off[i], nullptr);
     if (st == FFGPU_OK && P->tab_bytes > 0 &&
         cudaMemcpy(tabs, host.data(), P->tab_bytes, cudaMemcpyHostToDevice) != cudaSuccess)
         st = FFGPU_ERR_CUDA;
@@ -541,7 +651,7 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     g_capturing = true;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = FFGPU_ERR_CUDA;
     for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
-        st = launch_wave(waves[i], layouts[i], planes, tabs + tab_off[i], P->err, cs);
+        st = launch_wave(waves[i], layouts[i], planes, tabs + tab_off[i], P->err, cs, nullptr);
     for (size_t i = 0; i < singles.size() && st == FFGPU_OK; ++i) {
         const ffgpu_fgemm_desc* d = singles[i];
         st = fgemm_run(d->m, d->n, d->k, d->p, d->alpha, d->A, d->lda, d->B, d->ldb, d->beta, d->C, d->ldc,

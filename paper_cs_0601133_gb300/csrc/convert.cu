@@ -33,11 +33,18 @@ __device__ __forceinline__ void residues8(const ConvertParams& cp, const uint32_
     uint32_t sign[4];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-        const uint32_t q = __umulhi(x[e], cp.mu32);
-        uint32_t r = x[e] - q * cp.p;
-        if (r >= cp.p) r -= cp.p;
-        const bool neg = r > cp.half_p;
-        y[e] = neg ? cp.p - r : r;
+        bool neg;
+        if (cp.signed_input) {  // integer mode: the signed word itself, as magnitude and sign
+            const int32_t v = (int32_t)x[e];
+            neg = v < 0;
+            y[e] = neg ? 0u - x[e] : x[e];
+        } else {
+            const uint32_t q = __umulhi(x[e], cp.mu32);
+            uint32_t r = x[e] - q * cp.p;
+            if (r >= cp.p) r -= cp.p;
+            neg = r > cp.half_p;
+            y[e] = neg ? cp.p - r : r;
+        }
         if ((e & 1) == 0) sign[e >> 1] = neg ? 0x8000u : 0u;
         else sign[e >> 1] |= neg ? 0x80000000u : 0u;
     }

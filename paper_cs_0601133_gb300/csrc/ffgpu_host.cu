@@ -584,6 +584,33 @@ ffgpu_status ffgpu_fgemm_batched_plan_destroy(ffgpu_batched_plan* plan) {
     return FFGPU_OK;
 }
 
+ffgpu_status ffgpu_fgemm_multimod(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda,
+                                  const int32_t* B, int64_t ldb, int nprimes, const uint32_t* primes,
+                                  uint32_t* const* C, int64_t ldc, void* stream) {
+    ffgpu_status st = multimod_check(m, n, k, bits, A, lda, B, ldb, nprimes, primes, C, ldc);
+    if (st != FFGPU_OK || m == 0 || n == 0) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
+    Pool* pool = nullptr;
+    st = pool_get(s, multimod_ws_bytes(m, n, k, bits, sm_count(dev)), &pool);
+    if (st != FFGPU_OK) return st;
+    return multimod_run(m, n, k, bits, A, lda, B, ldb, nprimes, primes, C, ldc, pool->ptr, pool->bytes, pool->err, s);
+}
+
+ffgpu_status ffgpu_fgemm_multimod_batched(int64_t count, const ffgpu_multimod_desc* descs, int bits, int nprimes,
+                                          const uint32_t* primes, void* stream) {
+    if (count < 0 || (count > 0 && !descs)) return FFGPU_ERR_INVALID;
+    for (int64_t i = 0; i < count; ++i) {
+        const ffgpu_multimod_desc& d = descs[i];
+        const ffgpu_status st =
+            multimod_check(d.m, d.n, d.k, bits, d.A, d.lda, d.B, d.ldb, nprimes, primes, d.C, d.ldc);
+        if (st != FFGPU_OK) return st;
+    }
+    if (count == 0) return FFGPU_OK;
+    return batched_multimod_run(count, descs, bits, nprimes, primes, static_cast<cudaStream_t>(stream));
+}
+
 ffgpu_status ffgpu_last_device_error(void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(s) != cudaSuccess) {

@@ -64,6 +64,9 @@ struct InstInfo {
     uint32_t beta_s;               // floor(beta 2^32 / p)
     uint32_t Kfix;                 // (-128 sum_c Wa_c - 6 negMpa) mod p: start value of the CRT sum
     uint32_t Finit;                // 6 2^14 + 2^13 - 128 sum_c fr_c (mod 2^32): start value of the quotient sum
+    int int_out;                   // 1: integer mode -- C is an int64 array receiving the exact product
+    unsigned long long Mfull;      // integer mode: M = prod m_c
+    unsigned long long Xoff;       // integer mode: 128 sum_c M/m_c + 6 M (removed from the offset sums)
     uint32_t* C;
     long long ldc;
     int bucket;                    // grouped launch: tensor-map pair of this instance
@@ -72,8 +75,9 @@ struct InstInfo {
     float inv_m[kMaxChannels];
     uint32_t modu[kMaxChannels];
     uint32_t u[kMaxChannels];      // (M/m_c)^{-1} mod m_c (1 in direct mode)
-    uint32_t Wa[kMaxChannels];     // alpha * (M/m_c) mod p
+    uint32_t Wa[kMaxChannels];     // alpha * (M/m_c) mod p (integer mode: low 32 bits of M/m_c)
     uint32_t fr[kMaxChannels];     // round(2^14 / m_c): fixed-point weight of b_c / m_c
+    uint32_t Mhi[kMaxChannels];    // integer mode: high 32 bits of M/m_c
 };
 
 // Parameters of the single-instance tensor-core kernel (passed by value).
@@ -122,6 +126,7 @@ struct ConvertParams {
     uint32_t mu32;                   // floor((2^32-1)/p)
     int nch;
     int direct;
+    int signed_input;                // 1: words are int32 integers (|x| < 2^31), taken as they are, not mod p
     uint32_t mod[kMaxChannels];      // odd moduli <= 255
     uint32_t magic32[kMaxChannels];  // ceil(2^39 / m_c) < 2^32
 };
@@ -157,7 +162,9 @@ cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, u
                          unsigned long long mu, cudaStream_t s);
 cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s);
-cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s);
+cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s, bool int_out = false);
+cudaError_t launch_rns_gemm_int(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
+                                int grid, cudaStream_t s);
 cudaError_t launch_rns_gemm_pair(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
                                  int grid, cudaStream_t s);
 bool use_pair_kernel(int64_t m, int grid);
@@ -204,6 +211,55 @@ bool encode_planes(CUtensorMap* map, void* base, uint64_t kp, uint64_t rows, uin
 ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
                           int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
                           int path, int levels, cudaStream_t s);
+
+// multi-modular products from one exact integer product (multimod.cu)
+constexpr int kMaxFanoutPrimes = 64;
+struct FanoutParams {              // X mod p_i for every prime (passed by value)
+    int nprimes;
+    long long ldc;
+    uint32_t p[kMaxFanoutPrimes];
+    unsigned long long mu[kMaxFanoutPrimes];  // floor((2^64-1)/p_i)
+    uint32_t* C[kMaxFanoutPrimes];
+    unsigned char vec_ok[kMaxFanoutPrimes];   // 16-byte stores legal
+};
+void fill_inst_int(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, long long* X, int64_t ldx);
+ffgpu_status multimod_check(int64_t m, int64_t n, int64_t k, int bits, const void* A, int64_t lda, const void* B,
+                            int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc);
+size_t multimod_ws_bytes(int64_t m, int64_t n, int64_t k, int bits, int sms);
+void fanout_params(int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc, FanoutParams& F);
+cudaError_t launch_multimod_fanout(const long long* X, long long ldx, int m, int n, const FanoutParams& F,
+                                   cudaStream_t s);
+ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda, const int32_t* B,
+                          int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc,
+                          void* ws, size_t ws_bytes, int* err, cudaStream_t s);
+uint32_t multimod_plan_modulus(int bits);
+// grouped fan-out over the instances of a batch (one wave)
+struct FanInst {
+    const long long* X;
+    long long ldx, ldc;
+    int m, n;
+    int cbase;  // first of this instance's nprimes output pointers in the pointer table
+    int pad;
+};
+struct FanPrimes {
+    int nprimes;
+    uint32_t p[kMaxFanoutPrimes];
+    unsigned long long mu[kMaxFanoutPrimes];
+};
+long long multimod_fanout_blocks(int m, int n);
+cudaError_t launch_multimod_fanout_grouped(const FanInst* insts, const long long* block_begin, int n_inst,
+                                           long long nblocks, uint32_t* const* cptrs, const FanPrimes& P,
+                                           cudaStream_t s);
+// an integer-mode batch: every instance's exact product, fanned out to the primes
+struct MultiCtx {
+    int bits;
+    int nprimes;
+    const uint32_t* primes;
+    const ffgpu_multimod_desc* mdescs;
+    const ffgpu_fgemm_desc* pseudo;  // the planner's view: p = the plan's modulus, C = the int64 result
+};
+ffgpu_status batched_multimod_run(int64_t count, const ffgpu_multimod_desc* d, int bits, int nprimes,
+                                  const uint32_t* primes, cudaStream_t s);
 
 // batched fgemm (batched.cu)
 ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* d, cudaStream_t s);

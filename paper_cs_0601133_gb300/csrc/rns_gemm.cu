@@ -51,7 +51,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
 // per-instance constants of the reconstruction (see stage_consts): one copy for
 // the combine warps, one per epilogue warp
-constexpr size_t kConstBytes = size_t(1 + kEpiWarps) * kMaxChannels * 8;
+constexpr size_t kConstBytes = size_t(1 + kEpiWarps) * kMaxChannels * 16;
 constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kConstBytes + 256;
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
@@ -164,8 +164,59 @@ __device__ __forceinline__ void comb_load(const unsigned char* src, size_t chan_
     }
 }
 
-__device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int nch, const CombRow& R,
+// Integer mode: the exact product, X = sum_c d_c (M/m_c) - Xoff - (q + 6) M
+// over the stored bytes d_c = b_c + 128, all mod 2^64 (exact: |X| < 2^63 by
+// the plan), written as int64 (C points to an int64 array).
+__device__ __forceinline__ void comb_row_int(const InstInfo& I, const uint4* kc, int nch, const CombRow& R,
+                                         uint32_t* crow32, int col, int n, bool full8) {
+    unsigned long long X[8];
+    uint32_t F[8];
+    const uint32_t Finit = I.Finit;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        X[e] = 0ull;
+        F[e] = Finit;
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxChannels; ++c) {
+        if (c < nch) {
+            const uint4 k = kc[c];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const uint32_t d = __byte_perm(e < 4 ? R.w[c].x : R.w[c].y, 0u, 0x4440u | (uint32_t)(e & 3));
+                X[e] += (unsigned long long)d * k.x + ((unsigned long long)(d * k.z) << 32);
+                F[e] += d * k.y;
+            }
+        }
+    }
+    const unsigned long long Xoff = I.Xoff, M = I.Mfull;
+    long long out[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) out[e] = (long long)(X[e] - Xoff - (unsigned long long)(F[e] >> 14) * M);
+    long long* crow = reinterpret_cast<long long*>(crow32);
+    if (I.beta != 0) {  // a later slice of the inner dimension adds to the earlier ones
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (col + e < n) out[e] += crow[col + e];
+    }
+    if (full8) {
+#pragma unroll
+        for (int e = 0; e < 8; e += 2)
+            *reinterpret_cast<longlong2*>(crow + col + e) = make_longlong2(out[e], out[e + 1]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+            if (col + e < n) crow[col + e] = out[e];
+    }
+}
+
+template <bool kInt>
+__device__ __forceinline__ void comb_row(const InstInfo& I, const uint4* kc, int nch, const CombRow& R,
                                          uint32_t* crow, int col, int n, bool full8) {
+    if constexpr (kInt) {
+        comb_row_int(I, kc, nch, R, crow, col, n, full8);
+        return;
+    }
     unsigned long long S[8];
     uint32_t F[8];
     const uint32_t Kfix = I.Kfix, Finit = I.Finit;
@@ -177,7 +228,7 @@ __device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int
 #pragma unroll
     for (int c = 0; c < kMaxChannels; ++c) {
         if (c < nch) {
-            const uint2 k = kc[c];
+            const uint4 k = kc[c];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const uint32_t b = __byte_perm(e < 4 ? R.w[c].x : R.w[c].y, 0u, 0x4440u | (uint32_t)(e & 3));
@@ -210,7 +261,8 @@ __device__ __forceinline__ void comb_row(const InstInfo& I, const uint2* kc, int
     }
 }
 
-__device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc, int row0, int col0,
+template <bool kInt>
+__device__ __forceinline__ void combine_block(const InstInfo& I, const uint4* kc, int row0, int col0,
                                               const unsigned char* slot, size_t chan_stride, int vw, int nw,
                                               int lane) {
     const int rows = min(kTileM, I.m - row0);
@@ -219,7 +271,7 @@ __device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc
     if (vw >= rows || col >= n) return;  // nothing below is warp-collective
     const int nch = I.nch;
     const bool full8 = (col + 7 < n) && I.vec_ok;
-    const bool ldo = I.beta != 0;
+    const bool ldo = I.beta != 0 && !kInt;  // integer mode reads its int64 partial itself
     const long long ldc = I.ldc;
     uint32_t* const C = I.C + (long long)row0 * ldc;
     const unsigned char* const src = slot + 8 * lane;
@@ -230,28 +282,28 @@ __device__ __forceinline__ void combine_block(const InstInfo& I, const uint2* kc
     while (true) {
         if (r + nw < rows)
             comb_load(src + size_t(r + nw) * kTileN, chan_stride, nch, C + (r + nw) * ldc, col, n, full8, ldo, B);
-        comb_row(I, kc, nch, A, C + r * ldc, col, n, full8);
+        comb_row<kInt>(I, kc, nch, A, C + r * ldc, col, n, full8);
         r += nw;
         if (r >= rows) break;
         if (r + nw < rows)
             comb_load(src + size_t(r + nw) * kTileN, chan_stride, nch, C + (r + nw) * ldc, col, n, full8, ldo, A);
-        comb_row(I, kc, nch, B, C + r * ldc, col, n, full8);
+        comb_row<kInt>(I, kc, nch, B, C + r * ldc, col, n, full8);
         r += nw;
         if (r >= rows) break;
     }
 }
 
 // The constants for one warp's own use (an epilogue warp joining a reconstruction).
-__device__ __forceinline__ void stage_consts_warp(const InstInfo& I, uint2* kc, int lane) {
-    if (lane < I.nch) kc[lane] = make_uint2(I.Wa[lane], I.fr[lane]);
+__device__ __forceinline__ void stage_consts_warp(const InstInfo& I, uint4* kc, int lane) {
+    if (lane < I.nch) kc[lane] = make_uint4(I.Wa[lane], I.fr[lane], I.Mhi[lane], 0u);
     __syncwarp();
 }
 
 // Per-instance constants of the reconstruction, {Wa_c, fr_c}, staged in shared
 // memory by the combine warps (barriers among them on both sides).
-__device__ __forceinline__ void stage_consts(const InstInfo& I, uint2* kc, int tid) {
+__device__ __forceinline__ void stage_consts(const InstInfo& I, uint4* kc, int tid) {
     asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
-    if (tid < I.nch) kc[tid] = make_uint2(I.Wa[tid], I.fr[tid]);
+    if (tid < I.nch) kc[tid] = make_uint4(I.Wa[tid], I.fr[tid], I.Mhi[tid], 0u);
     asm volatile("bar.sync 1, %0;" ::"r"(kCombineWarps * 32) : "memory");
 }
 
@@ -419,7 +471,7 @@ struct GroupSched {
     __device__ int* err() const { return P.err; }
 };
 
-template <class Sched, class Params>
+template <class Sched, bool kInt, class Params>
 __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUtensorMap* mapB,
                                               const Params& P) {
     extern __shared__ unsigned char smem_raw[];
@@ -427,7 +479,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kStages * kABytes;
-    uint2* kc = reinterpret_cast<uint2*>(sB + kStages * kBBytes);
+    uint4* kc = reinterpret_cast<uint4*>(sB + kStages * kBBytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(kc) + kConstBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kStages;
@@ -641,11 +693,11 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
             Job d;
             S.last_job(d);
-            uint2* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
+            uint4* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(*d.inst, kcw, lane);
             if (mbar_wait(&slot_full[d.slot], (uint32_t)(tiles_on[d.slot] - 1) & 1u, abort_flag, err,
                           kDevTimeoutEpilogue))
-                combine_block(*d.inst, kcw, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+                combine_block<kInt>(*d.inst, kcw, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
                               size_t(kTileM) * kTileN, kCombineWarps + (warp - 2), kCombineWarps + kEpiWarps, lane);
         }
     } else {
@@ -667,7 +719,7 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
             if (!mbar_wait(&slot_full[d.slot], sfp[d.slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[d.slot] ^= 1u;
             const bool last = j == J - 1;  // the epilogue warps join the last tile's reconstruction
-            combine_block(*d.inst, kc, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
+            combine_block<kInt>(*d.inst, kc, d.tm * kTileM, d.tn * kTileN, slot_base + size_t(d.slot) * sstride,
                           size_t(kTileM) * kTileN, cw, last ? kCombineWarps + kEpiWarps : kCombineWarps, lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[d.slot]);
@@ -687,12 +739,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     rns_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                     const __grid_constant__ CUtensorMap mapB,
                     const __grid_constant__ RnsGemmParams P) {
-    rns_gemm_body<SingleSched>(&mapA, &mapB, P);
+    rns_gemm_body<SingleSched, false>(&mapA, &mapB, P);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_int_kernel(const __grid_constant__ CUtensorMap mapA,
+                        const __grid_constant__ CUtensorMap mapB,
+                        const __grid_constant__ RnsGemmParams P) {
+    rns_gemm_body<SingleSched, true>(&mapA, &mapB, P);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
     rns_gemm_grouped_kernel(const __grid_constant__ GroupGemmParams P) {
-    rns_gemm_body<GroupSched>(nullptr, nullptr, P);
+    rns_gemm_body<GroupSched, false>(nullptr, nullptr, P);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    rns_gemm_grouped_int_kernel(const __grid_constant__ GroupGemmParams P) {
+    rns_gemm_body<GroupSched, true>(nullptr, nullptr, P);
 }
 
 
@@ -722,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* sA = base;
     unsigned char* sB = base + kPStages * kPABytes;
-    uint2* kc = reinterpret_cast<uint2*>(sB + kPStages * kPBBytes);
+    uint4* kc = reinterpret_cast<uint4*>(sB + kPStages * kPBBytes);
     uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(kc) + kConstBytes);
     uint64_t* full = bars;
     uint64_t* empty = bars + kPStages;
@@ -949,10 +1013,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ti = my_tiles - 1;
             int tm, tn;
             tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
-            uint2* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
+            uint4* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(I, kcw, lane);
             if (mbar_wait(&slot_full[ti & 1], (uint32_t)(ti >> 1) & 1u, abort_flag, err, kDevTimeoutEpilogue))
-                combine_block(I, kcw, (2 * tm + (int)rank) * kTileM, tn * kTileN,
+                combine_block<false>(I, kcw, (2 * tm + (int)rank) * kTileM, tn * kTileN,
                               slot_base + size_t(ti & 1) * P.slot_stride, size_t(kTileM) * kTileN,
                               kCombineWarps + (warp - 2), kCombineWarps + kEpiWarps, lane);
         }
@@ -969,7 +1033,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int tm, tn;
             tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
-            combine_block(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
+            combine_block<false>(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
                           size_t(kTileM) * kTileN, cw, ti == my_tiles - 1 ? kCombineWarps + kEpiWarps : kCombineWarps,
                           lane);
             __syncwarp();
@@ -1057,16 +1121,31 @@ cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
     return cudaGetLastError();
 }
 
-cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s) {
+cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s, bool int_out) {
+    static bool attr_set = false, attr_set_int = false;
+    if (!(int_out ? attr_set_int : attr_set)) {
+        cudaError_t e = cudaFuncSetAttribute(int_out ? rns_gemm_grouped_int_kernel : rns_gemm_grouped_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        (int_out ? attr_set_int : attr_set) = true;
+    }
+    if (int_out)
+        rns_gemm_grouped_int_kernel<<<grid, kThreads, kSmemBytes, s>>>(prm);
+    else
+        rns_gemm_grouped_kernel<<<grid, kThreads, kSmemBytes, s>>>(prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rns_gemm_int(const CUtensorMap& mapA, const CUtensorMap& mapB, const RnsGemmParams& prm,
+                                int grid, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(rns_gemm_grouped_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(rns_gemm_int_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)kSmemBytes);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    rns_gemm_grouped_kernel<<<grid, kThreads, kSmemBytes, s>>>(prm);
+    rns_gemm_int_kernel<<<grid, kThreads, kSmemBytes, s>>>(mapA, mapB, prm);
     return cudaGetLastError();
 }
 

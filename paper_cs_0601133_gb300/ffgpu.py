@@ -88,6 +88,12 @@ class FgemmDesc(ctypes.Structure):
                 ("ldb", ctypes.c_int64), ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64)]
 
 
+class MultimodDesc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("B", ctypes.c_void_p),
+                ("ldb", ctypes.c_int64), ("C", ctypes.POINTER(ctypes.c_void_p)), ("ldc", ctypes.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -112,6 +118,9 @@ SIGNATURES = {
     "ffgpu_server_get_stats": [_VP, ctypes.POINTER(ServerStats)],
     "ffgpu_server_destroy": [_VP],
     "ffgpu_fgemm_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP],
+    "ffgpu_fgemm_multimod_batched": [_I64, ctypes.POINTER(MultimodDesc), _I32, _I32, ctypes.POINTER(_U32), _VP],
+    "ffgpu_fgemm_multimod": [_I64, _I64, _I64, _I32, _VP, _I64, _VP, _I64, _I32, ctypes.POINTER(_U32),
+                             ctypes.POINTER(_VP), _I64, _VP],
     "ffgpu_fgemm_batched_plan_create": [_I64, ctypes.POINTER(FgemmDesc), ctypes.POINTER(_VP)],
     "ffgpu_fgemm_batched_plan_run": [_VP, _VP],
     "ffgpu_fgemm_batched_plan_error": [_VP],
@@ -216,6 +225,84 @@ def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "r
     check(lib().ffgpu_fgemm_ex(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
                                ctypes.byref(opt), _stream_ptr(stream)), "ffgpu_fgemm_ex")
     return C
+
+
+def fgemm_multimod(A, B, primes, bits: int, C=None, stream=None):
+    """C_i = (A @ B) mod p_i for every p in primes, from ONE exact integer
+    product (ffgpu_fgemm_multimod).  A (m x k) and B (k x n) are int32 CUDA
+    tensors with |entries| <= 2^bits; returns the list of C_i (int32 tensors
+    holding the residues in [0, p_i))."""
+    import torch
+    if A.dtype != torch.int32 or B.dtype != torch.int32:
+        raise ValueError("A and B must be int32")
+    m, k = A.shape
+    if B.shape[0] != k:
+        raise ValueError("inner dimensions differ")
+    n = B.shape[1]
+    primes = [int(p) for p in primes]
+    if C is None:
+        C = [torch.empty((m, n), dtype=torch.int32, device=A.device) for _ in primes]
+    a, lda = _mat(A, "A")
+    b, ldb = _mat(B, "B")
+    ldc = None
+    ptrs = []
+    for Ci in C:
+        if tuple(Ci.shape) != (m, n):
+            raise ValueError("every C must be m x n")
+        c, ldc_i = _mat(Ci, "C")
+        if ldc is None:
+            ldc = ldc_i
+        elif ldc_i != ldc:
+            raise ValueError("every C must have the same leading dimension")
+        ptrs.append(c)
+    if ldc is None:
+        ldc = max(n, 1)
+    parr = (_U32 * max(1, len(primes)))(*primes)
+    carr = (_VP * max(1, len(ptrs)))(*ptrs)
+    check(lib().ffgpu_fgemm_multimod(m, n, k, bits, a, lda, b, ldb, len(primes), parr, carr, ldc,
+                                     _stream_ptr(stream)), "ffgpu_fgemm_multimod")
+    return C
+
+
+def multimod_descs(problems):
+    """Host descriptors (ffgpu_multimod_desc[]) for problems (A, B, [C_1..C_P])
+    of int32 A, B and int32 C_i CUDA tensors; returns (array, count, keep),
+    `keep` holding the per-problem pointer arrays alive."""
+    probs = list(problems)
+    arr = (MultimodDesc * max(1, len(probs)))()
+    keep = []
+    for i, (A, B, Cs) in enumerate(probs):
+        m, k = A.shape
+        n = B.shape[1]
+        a, lda = _mat(A, "A")
+        b, ldb = _mat(B, "B")
+        ptrs, ldc = [], None
+        for Ci in Cs:
+            c, l = _mat(Ci, "C")
+            if ldc is None:
+                ldc = l
+            elif l != ldc:
+                raise ValueError("problem %d: every C must have the same leading dimension" % i)
+            ptrs.append(c)
+        parr = (_VP * max(1, len(ptrs)))(*ptrs)
+        keep.append(parr)
+        arr[i] = MultimodDesc(m, n, k, a, lda, b, ldb, parr, ldc if ldc is not None else max(n, 1))
+    return arr, len(probs), keep
+
+
+def fgemm_multimod_batched_descs(descs, count: int, primes, bits: int, stream=None):
+    """ffgpu_fgemm_multimod_batched on a prebuilt descriptor array (see multimod_descs)."""
+    parr = (_U32 * max(1, len(primes)))(*[int(p) for p in primes])
+    check(lib().ffgpu_fgemm_multimod_batched(count, descs, bits, len(primes), parr, _stream_ptr(stream)),
+          "ffgpu_fgemm_multimod_batched")
+
+
+def fgemm_multimod_batched(problems, primes, bits: int, stream=None):
+    """For every (A, B, [C_1..C_P]): C_i = (A @ B) mod primes[i], one exact
+    integer product per problem, all problems in grouped launches."""
+    arr, n, keep = multimod_descs(problems)
+    fgemm_multimod_batched_descs(arr, n, primes, bits, stream)
+    del keep
 
 
 def batched_descs(problems):
