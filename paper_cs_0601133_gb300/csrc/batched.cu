@@ -355,10 +355,7 @@ ffgpu_status launch_wave(const std::vector<BInst>& w, const WaveLayout& L, unsig
         FanPrimes F;
         std::memset(&F, 0, sizeof(F));
         F.nprimes = mc->nprimes;
-        for (int q = 0; q < mc->nprimes; ++q) {
-            F.p[q] = mc->primes[q];
-            F.mu[q] = ~0ull / mc->primes[q];
-        }
+        for (int q = 0; q < mc->nprimes; ++q) F.pr[q] = fan_prime(mc->primes[q]);
         if (timed_launch("multimod_fanout_grouped", s, [&] {
                 return launch_multimod_fanout_grouped(reinterpret_cast<const FanInst*>(tabs + L.t_fan),
                                                       reinterpret_cast<const long long*>(tabs + L.t_fanbb), n_inst,

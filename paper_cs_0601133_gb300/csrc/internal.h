@@ -214,14 +214,27 @@ ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t 
 
 // multi-modular products from one exact integer product (multimod.cu)
 constexpr int kMaxFanoutPrimes = 64;
+// Per prime of a fan-out: p, R = 2^32 mod p and the Shoup quotients
+// floor(R 2^32 / p) and floor(2^32 / p), so that a 62-bit magnitude
+// u = u_hi 2^32 + u_lo reduces as u_hi R + u_lo with 32-bit products.
+struct FanPrime {
+    uint32_t p, R, Rs, one_s;
+};
 struct FanoutParams {              // X mod p_i for every prime (passed by value)
     int nprimes;
     long long ldc;
-    uint32_t p[kMaxFanoutPrimes];
-    unsigned long long mu[kMaxFanoutPrimes];  // floor((2^64-1)/p_i)
+    FanPrime pr[kMaxFanoutPrimes];
     uint32_t* C[kMaxFanoutPrimes];
     unsigned char vec_ok[kMaxFanoutPrimes];   // 16-byte stores legal
 };
+inline FanPrime fan_prime(uint32_t p) {
+    FanPrime f;
+    f.p = p;
+    f.R = (uint32_t)((1ull << 32) % p);
+    f.Rs = (uint32_t)(((unsigned long long)f.R << 32) / p);
+    f.one_s = (uint32_t)((1ull << 32) / p);
+    return f;
+}
 void fill_inst_int(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, long long* X, int64_t ldx);
 ffgpu_status multimod_check(int64_t m, int64_t n, int64_t k, int bits, const void* A, int64_t lda, const void* B,
                             int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc);
@@ -243,8 +256,7 @@ struct FanInst {
 };
 struct FanPrimes {
     int nprimes;
-    uint32_t p[kMaxFanoutPrimes];
-    unsigned long long mu[kMaxFanoutPrimes];
+    FanPrime pr[kMaxFanoutPrimes];
 };
 long long multimod_fanout_blocks(int m, int n);
 cudaError_t launch_multimod_fanout_grouped(const FanInst* insts, const long long* block_begin, int n_inst,

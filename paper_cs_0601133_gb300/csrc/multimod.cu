@@ -27,6 +27,18 @@ typedef unsigned __int128 u128;
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// u mod p for a magnitude u < 2^62: u_hi R + u_lo with Shoup products (each in
+// [0, 2p)), folded to [0, p) -- 32-bit arithmetic only.
+__device__ __forceinline__ uint32_t fan_mod(unsigned long long u, const FanPrime& f) {
+    const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+    uint32_t t1 = hi * f.R - __umulhi(hi, f.Rs) * f.p;
+    t1 = min(t1, t1 - f.p);
+    uint32_t t2 = lo - __umulhi(lo, f.one_s) * f.p;
+    t2 = min(t2, t2 - f.p);
+    const uint32_t t = t1 + t2;
+    return min(t, t - f.p);
+}
+
 // X (int64, m x n, ldx) -> C_i = X mod p_i in [0, p_i), 4 columns per thread.
 __global__ void __launch_bounds__(256) multimod_fanout_kernel(const long long* __restrict__ X, long long ldx, int m,
                                                               int n, const __grid_constant__ FanoutParams P) {
@@ -48,13 +60,12 @@ __global__ void __launch_bounds__(256) multimod_fanout_kernel(const long long* _
         const bool full4 = c0 + 3 < n;
 #pragma unroll 1
         for (int i = 0; i < P.nprimes; ++i) {
-            const uint32_t p = P.p[i];
-            const unsigned long long mu = P.mu[i];
+            const FanPrime f = P.pr[i];
             uint32_t out[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const uint32_t t = mod_u64(u[e], p, mu);
-                out[e] = (neg[e] && t != 0u) ? p - t : t;
+                const uint32_t t = fan_mod(u[e], f);
+                out[e] = (neg[e] && t != 0u) ? f.p - t : t;
             }
             uint32_t* dst = P.C[i] + (long long)r * P.ldc + c0;
             if (full4 && P.vec_ok[i]) {
@@ -103,13 +114,12 @@ __global__ void __launch_bounds__(kFanThreads) multimod_fanout_grouped_kernel(
     const bool full4 = c0 + 3 < F.n;
 #pragma unroll 1
     for (int q = 0; q < P.nprimes; ++q) {
-        const uint32_t p = P.p[q];
-        const unsigned long long mu = P.mu[q];
+        const FanPrime f = P.pr[q];
         uint32_t out[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const uint32_t t = mod_u64(u[e], p, mu);
-            out[e] = (neg[e] && t != 0u) ? p - t : t;
+            const uint32_t t = fan_mod(u[e], f);
+            out[e] = (neg[e] && t != 0u) ? f.p - t : t;
         }
         uint32_t* dst = cptrs[F.cbase + q] + (long long)r * F.ldc + c0;
         if (full4 && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
@@ -216,8 +226,7 @@ void fanout_params(int nprimes, const uint32_t* primes, uint32_t* const* C, int6
     F.nprimes = nprimes;
     F.ldc = ldc;
     for (int i = 0; i < nprimes; ++i) {
-        F.p[i] = primes[i];
-        F.mu[i] = ~0ull / primes[i];
+        F.pr[i] = fan_prime(primes[i]);
         F.C[i] = C[i];
         F.vec_ok[i] = ((reinterpret_cast<uintptr_t>(C[i]) & 15) == 0) && (ldc % 4 == 0);
     }
