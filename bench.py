@@ -453,19 +453,21 @@ def run_ftrsm(args):
             dB0 = torch.from_numpy(B.view(np.int32)).cuda()
             dB = dB0.clone()
             steps = 3 if n < 8192 else 2
-            ms = time_call(lambda: (dB.copy_(dB0), ff.ftrsm(dT, dB, p, 1, "L", uplo, diag)), torch, steps, 1)
-            ff.profile_enable(True)
-            ff.ftrsm(dT, dB, p, 1, "L", uplo, diag)
-            torch.cuda.synchronize()
-            ff.profile_enable(False)
-            kern = {k: (v[0], round(v[1], 3)) for k, v in ff.profile_read().items()}
             copy_ms = time_call(lambda: dB.copy_(dB0), torch, steps, 1)
             dC = torch.zeros((n, n), dtype=torch.int32, device="cuda")
             gemm_ms = time_call(lambda: ff.fgemm(dT, dB0, p, 1, 0, dC), torch, steps, 1)
-            t = ms - copy_ms
-            print(json.dumps({"workload": "ftrsm", "n": n, "p": p, "side": "L", "uplo": uplo, "diag": diag,
-                              "ms": t, "GOPS": n ** 3 / (t / 1e3) / 1e9, "fgemm_ms": gemm_ms,
-                              "ftrsm_over_fgemm": t / gemm_ms, "kernels_launches_ms": kern}), flush=True)
+            for algo in ("recursive", "delayed"):
+                ms = time_call(lambda: (dB.copy_(dB0), ff.ftrsm(dT, dB, p, 1, "L", uplo, diag, algorithm=algo)),
+                               torch, steps, 1)
+                ff.profile_enable(True)
+                ff.ftrsm(dT, dB, p, 1, "L", uplo, diag, algorithm=algo)
+                torch.cuda.synchronize()
+                ff.profile_enable(False)
+                kern = {k: (v[0], round(v[1], 3)) for k, v in ff.profile_read().items()}
+                t = ms - copy_ms
+                print(json.dumps({"workload": "ftrsm", "algorithm": algo, "n": n, "p": p, "side": "L", "uplo": uplo,
+                                  "diag": diag, "ms": t, "GOPS": n ** 3 / (t / 1e3) / 1e9, "fgemm_ms": gemm_ms,
+                                  "ftrsm_over_fgemm": t / gemm_ms, "kernels_launches_ms": kern}), flush=True)
             del dT, dB0, dB, dC
     return 0
 

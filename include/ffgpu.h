@@ -201,6 +201,29 @@ FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int6
                                    uint32_t alpha, const uint32_t* T, int64_t ldt, uint32_t* B,
                                    int64_t ldb, void* stream);
 
+/*
+ * ftrsm with the algorithm chosen (ffgpu_ftrsm uses FFGPU_TRSM_DEFAULT):
+ *   FFGPU_TRSM_RECURSIVE  Algorithm 1 (section 4.1): split the triangle in two,
+ *                         solve, update the other half with one fgemm, solve;
+ *                         every level's update is reduced mod p.
+ *   FFGPU_TRSM_DELAYED    the delayed-reduction idea of Algorithms 2-3
+ *                         (section 4.2) restated: left-looking, each block of
+ *                         X computed by ONE product over all earlier blocks at
+ *                         once, X_i = [Inv_i | -Inv_i T_i,prev] [B_i ; X_prev],
+ *                         so every output block is reduced exactly once (the
+ *                         residue system keeps the whole accumulation exact).
+ *   FFGPU_TRSM_DEFAULT    the recursive algorithm (measured the faster of the
+ *                         two from n = 4096 on).
+ * Same arguments, results and errors as ffgpu_ftrsm; FFGPU_ERR_INVALID for an
+ * unknown algorithm.
+ */
+#define FFGPU_TRSM_DEFAULT (-1)
+#define FFGPU_TRSM_RECURSIVE 0
+#define FFGPU_TRSM_DELAYED 1
+FFGPU_API ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                                      const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, int algorithm,
+                                      void* stream);
+
 /* One independent fgemm of a batch: C <- (alpha*A*B + beta*C) mod p. */
 typedef struct {
     int64_t m, n, k;

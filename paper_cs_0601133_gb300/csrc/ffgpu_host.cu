@@ -530,10 +530,12 @@ ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, v
     return batched_run(count, descs, static_cast<cudaStream_t>(stream));
 }
 
-ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
-                         const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* stream) {
+ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                            const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, int algorithm, void* stream) {
     if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
     if (side < 0 || side > 1 || uplo < 0 || uplo > 1 || diag < 0 || diag > 1) return FFGPU_ERR_INVALID;
+    if (algorithm != FFGPU_TRSM_DEFAULT && algorithm != FFGPU_TRSM_RECURSIVE && algorithm != FFGPU_TRSM_DELAYED)
+        return FFGPU_ERR_INVALID;
     if (m < 0 || n < 0 || m > INT32_MAX / 2 || n > INT32_MAX / 2) return FFGPU_ERR_INVALID;
     if (m == 0 || n == 0) return FFGPU_OK;
     const int64_t nt = side == 0 ? m : n;
@@ -542,9 +544,15 @@ ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uin
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
     Pool* pool = nullptr;
-    ffgpu_status st = pool_get(s, ftrsm_ws_bytes(side, m, n, p, sm_count(dev)), &pool);
+    ffgpu_status st = pool_get(s, ftrsm_ws_bytes(side, uplo, algorithm, m, n, p, sm_count(dev)), &pool);
     if (st != FFGPU_OK) return st;
-    return ftrsm_run(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, pool->ptr, pool->bytes, pool->err, s);
+    return ftrsm_run(side, uplo, diag, algorithm, m, n, p, alpha, T, ldt, B, ldb, pool->ptr, pool->bytes, pool->err,
+                     s);
+}
+
+ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                         const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* stream) {
+    return ffgpu_ftrsm_ex(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, FFGPU_TRSM_DEFAULT, stream);
 }
 
 ffgpu_status ffgpu_fgemm_batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs,

@@ -259,13 +259,86 @@ void doubling_descs(int64_t sz, int64_t L, int64_t s, int uplo, uint32_t p, cons
     }
 }
 
-struct TrsmLayout {
-    int64_t L, nl;
-    size_t inv, panel, tmp, rest;  // byte offsets; rest = start of the fgemm / batched workspace
-    size_t fg;                     // bytes the products need
+// Delayed (left-looking) solve: leaf i in the order its dependences allow is
+// X_i = Q_i * (the rows, or columns, of B that hold X_prev and B_i), one
+// product whose inner dimension covers every earlier leaf at once -- each
+// block of X is reduced mod p exactly once (the delayed reduction of
+// Algorithms 2-3, section 4.2, restated: the residue system keeps the whole
+// accumulation exact, so the bound never forces an intermediate reduction).
+// Q_i holds Inv_i next to -W_i, W_i = Inv_i T_i,prev (side L) or
+// T_prev,i Inv_i (side R), all W_i from one batched product.
+struct LeafGeo {
+    int64_t off, Li;   // leaf rows/columns [off, off + Li)
+    int64_t pb, plen;  // the earlier leaves: [pb, pb + plen)
+    int64_t ob, len;   // operand range [ob, ob + len) of B (rows for side L, columns for side R)
+    size_t q;          // word offset of Q_i in the Q region
 };
 
-TrsmLayout trsm_layout(int side, int64_t m, int64_t n, uint32_t p, int sms) {
+// Leaves in solve order with their geometry; returns the Q region's words.
+size_t delayed_geometry(int side, int uplo, int64_t sz, int64_t L, std::vector<LeafGeo>& g) {
+    const int64_t nl = (sz + L - 1) / L;
+    // side L lower / side R upper: ascending; the other two: descending
+    const bool asc = (side == 0) == (uplo == 0);
+    size_t q = 0;
+    for (int64_t t = 0; t < nl; ++t) {
+        const int64_t i = asc ? t : nl - 1 - t;
+        LeafGeo x;
+        x.off = i * L;
+        x.Li = std::min(L, sz - x.off);
+        if (asc) {
+            x.pb = 0;
+            x.plen = x.off;
+            x.ob = 0;
+            x.len = x.off + x.Li;
+        } else {
+            x.pb = x.off + x.Li;
+            x.plen = sz - x.pb;
+            x.ob = x.off;
+            x.len = sz - x.off;
+        }
+        x.q = q;
+        q += size_t(x.Li) * x.len;
+        g.push_back(x);
+    }
+    return q;
+}
+
+// The W_i products (Q's off-diagonal parts, negated); null pointers: shapes only.
+void delayed_w_descs(int side, const std::vector<LeafGeo>& g, int64_t L, uint32_t p, const uint32_t* T,
+                     int64_t ldt, const uint32_t* inv, uint32_t* Q, std::vector<ffgpu_fgemm_desc>& out) {
+    const uint32_t* dummy = reinterpret_cast<const uint32_t*>(uintptr_t(256));  // shapes only: never dereferenced
+    for (const LeafGeo& x : g) {
+        if (x.plen == 0) continue;
+        const uint32_t* Inv = inv ? inv + size_t(x.off / L) * L * L : dummy;
+        uint32_t* Qi = Q ? Q + x.q : const_cast<uint32_t*>(dummy);
+        const bool before = x.pb < x.off;  // the earlier leaves come first in the operand
+        ffgpu_fgemm_desc d;
+        std::memset(&d, 0, sizeof(d));
+        d.p = p;
+        d.alpha = p - 1;
+        d.beta = 0;
+        if (side == 0) {  // W = Inv_i (Li x Li) T[off.., pb..] (Li x plen), into Q_i (Li x len)
+            d.m = x.Li; d.n = x.plen; d.k = x.Li;
+            d.A = Inv; d.lda = L;
+            d.B = T ? T + x.off * ldt + x.pb : dummy; d.ldb = ldt;
+            d.C = Q ? Qi + (before ? 0 : x.Li) : Qi; d.ldc = x.len;
+        } else {          // W = T[pb.., off..] (plen x Li) Inv_i (Li x Li), into Q_i (len x Li)
+            d.m = x.plen; d.n = x.Li; d.k = x.Li;
+            d.A = T ? T + x.pb * ldt + x.off : dummy; d.lda = ldt;
+            d.B = Inv; d.ldb = L;
+            d.C = Q ? Qi + (before ? 0 : size_t(x.Li) * x.Li) : Qi; d.ldc = x.Li;
+        }
+        out.push_back(d);
+    }
+}
+
+struct TrsmLayout {
+    int64_t L, nl;
+    size_t inv, panel, tmp, qreg, rest;  // byte offsets; rest = start of the fgemm / batched workspace
+    size_t fg;                           // bytes the products need
+};
+
+TrsmLayout trsm_layout(int side, int uplo, int algo, int64_t m, int64_t n, uint32_t p, int sms) {
     TrsmLayout Y;
     const int64_t sz = side == 0 ? m : n, rhs = side == 0 ? n : m;
     Y.L = leaf_size(sz);
@@ -273,7 +346,11 @@ TrsmLayout trsm_layout(int side, int64_t m, int64_t n, uint32_t p, int sms) {
     Y.inv = 0;
     Y.panel = align256(size_t(Y.nl) * Y.L * Y.L * 4);
     Y.tmp = Y.panel + align256(size_t(Y.L) * rhs * 4);
-    Y.rest = Y.tmp + align256(size_t(sz) * Y.L / 2 * 4 + 4);
+    Y.qreg = Y.tmp + align256(size_t(sz) * Y.L / 2 * 4 + 4);
+    std::vector<LeafGeo> geo;
+    size_t qwords = 0;
+    if (algo == 1) qwords = delayed_geometry(side, uplo, sz, Y.L, geo);
+    Y.rest = Y.qreg + align256(qwords * 4);
     size_t fg = fgemm_ws_bytes(side == 0 ? Y.L : rhs, side == 0 ? rhs : Y.L, Y.L, p, sms);
     if (sz > Y.L) {
         const int64_t h = split(sz, Y.L), r = sz - h;
@@ -283,31 +360,93 @@ TrsmLayout trsm_layout(int side, int64_t m, int64_t n, uint32_t p, int sms) {
             fg = std::max(fg, std::max(fgemm_ws_bytes(m, r, h, p, sms), fgemm_ws_bytes(m, h, r, p, sms)));
     }
     for (int64_t s = kBlk; s < Y.L; s *= 2)
-        for (int uplo = 0; uplo < 2; ++uplo)
-            for (int step = 0; step < 2; ++step) {
-                std::vector<ffgpu_fgemm_desc> d;
-                doubling_descs(sz, Y.L, s, uplo, p, nullptr, sz, nullptr, nullptr, step, d);
-                if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
-            }
+        for (int step = 0; step < 2; ++step) {
+            std::vector<ffgpu_fgemm_desc> d;
+            doubling_descs(sz, Y.L, s, uplo, p, nullptr, sz, nullptr, nullptr, step, d);
+            if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
+        }
+    if (algo == 1) {
+        std::vector<ffgpu_fgemm_desc> d;
+        delayed_w_descs(side, geo, Y.L, p, nullptr, sz, nullptr, nullptr, d);
+        if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
+        for (const LeafGeo& x : geo)
+            fg = std::max(fg, side == 0 ? fgemm_ws_bytes(x.Li, rhs, x.len, p, sms)
+                                        : fgemm_ws_bytes(rhs, x.Li, x.len, p, sms));
+    }
     Y.fg = fg;
     return Y;
 }
 
+ffgpu_status delayed_solve(const TrsmCtx& c, const TrsmLayout& Y, int64_t sz, int64_t m, int64_t n,
+                           const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, uint32_t* Q) {
+    std::vector<LeafGeo> geo;
+    delayed_geometry(c.side, c.uplo, sz, Y.L, geo);
+    // Q_i: the inverse part, then every W_i in one batched product
+    for (const LeafGeo& x : geo) {
+        const uint32_t* Inv = c.inv + size_t(x.off / Y.L) * Y.L * Y.L;
+        const bool before = x.pb < x.off;
+        uint32_t* dst;
+        size_t dpitch;
+        if (c.side == 0) {
+            dst = Q + x.q + (before ? x.plen : 0);
+            dpitch = size_t(x.len) * 4;
+        } else {
+            dst = Q + x.q + (before ? size_t(x.plen) * x.Li : 0);
+            dpitch = size_t(x.Li) * 4;
+        }
+        if (cudaMemcpy2DAsync(dst, dpitch, Inv, size_t(Y.L) * 4, size_t(x.Li) * 4, x.Li, cudaMemcpyDeviceToDevice,
+                              c.s) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+    }
+    {
+        std::vector<ffgpu_fgemm_desc> d;
+        delayed_w_descs(c.side, geo, Y.L, c.p, T, ldt, c.inv, Q, d);
+        if (!d.empty()) {
+            const ffgpu_status st = batched_run_ws((int64_t)d.size(), d.data(), c.ws, c.ws_bytes, c.err, c.s);
+            if (st != FFGPU_OK) return st;
+        }
+    }
+    // one product per leaf, in dependence order
+    for (const LeafGeo& x : geo) {
+        ffgpu_status st;
+        if (c.side == 0) {  // X_i = Q_i (Li x len) B[ob.., :] (len x n)
+            if ((st = gemm(c, x.Li, n, x.len, 1, Q + x.q, x.len, B + x.ob * ldb, ldb, 0, c.panel, n)) != FFGPU_OK)
+                return st;
+            if (cudaMemcpy2DAsync(B + x.off * ldb, ldb * 4, c.panel, n * 4, n * 4, x.Li, cudaMemcpyDeviceToDevice,
+                                  c.s) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+        } else {            // X_i = B[:, ob..] (m x len) Q_i (len x Li)
+            if ((st = gemm(c, m, x.Li, x.len, 1, B + x.ob, ldb, Q + x.q, x.Li, 0, c.panel, x.Li)) != FFGPU_OK)
+                return st;
+            if (cudaMemcpy2DAsync(B + x.off, ldb * 4, c.panel, x.Li * 4, x.Li * 4, m, cudaMemcpyDeviceToDevice,
+                                  c.s) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+        }
+    }
+    return FFGPU_OK;
+}
+
 }  // namespace
 
-// Workspace: leaf inverses | leaf panel | doubling temporaries | the largest product's workspace.
-size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms) {
-    const TrsmLayout Y = trsm_layout(side, m, n, p, sms);
+// The algorithm a call uses: FFGPU_TRSM_DEFAULT resolves to the recursive one,
+// measured faster from n = 4096 on (the delayed variant's leaf products are
+// skinny, L rows by n, and leave a partial wave of tiles).
+int ftrsm_algo(int algo) { return algo == FFGPU_TRSM_DEFAULT ? FFGPU_TRSM_RECURSIVE : algo; }
+
+// Workspace: leaf inverses | leaf panel | doubling temporaries | [Q] | the largest product's workspace.
+size_t ftrsm_ws_bytes(int side, int uplo, int algo, int64_t m, int64_t n, uint32_t p, int sms) {
+    const TrsmLayout Y = trsm_layout(side, uplo, ftrsm_algo(algo), m, n, p, sms);
     return Y.rest + align256(Y.fg);
 }
 
-ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
                        const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s) {
     const int64_t sz = side == 0 ? m : n;
+    algo = ftrsm_algo(algo);
     int dev = 0;
     cudaGetDevice(&dev);
-    const TrsmLayout Y = trsm_layout(side, m, n, p, sm_count(dev));
+    const TrsmLayout Y = trsm_layout(side, uplo, algo, m, n, p, sm_count(dev));
     if (ws_bytes < Y.rest) return FFGPU_ERR_NOMEM;
     unsigned char* w = static_cast<unsigned char*>(ws);
     TrsmCtx c;
@@ -358,6 +497,8 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint3
             if (st != FFGPU_OK) return st;
         }
     }
+    if (algo == FFGPU_TRSM_DELAYED)
+        return delayed_solve(c, Y, sz, m, n, T, ldt, B, ldb, reinterpret_cast<uint32_t*>(w + Y.qreg));
     return rec(c, 0, sz, m, n, T, ldt, B, ldb);
 }
 

@@ -286,8 +286,9 @@ void batched_plan_destroy(BatchedPlan* plan);
 void batched_plan_info(const BatchedPlan* plan, int* waves, int* singles, size_t* nodes, size_t* device_bytes);
 
 // ftrsm (ftrsm.cu)
-size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);
-ffgpu_status ftrsm_run(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+int ftrsm_algo(int algo);
+size_t ftrsm_ws_bytes(int side, int uplo, int algo, int64_t m, int64_t n, uint32_t p, int sms);
+ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
                        const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s);
 

@@ -24,7 +24,6 @@
 
 namespace ffgpu {
 
-size_t ftrsm_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);
 
 namespace {
 
@@ -129,7 +128,7 @@ struct Server {
         }
         const int64_t nt = q.side == 0 ? q.m : q.n;
         return align256(size_t(nt) * nt * 4) + align256(size_t(q.m) * q.n * 4) +
-               align256(ftrsm_ws_bytes(q.side, q.m, q.n, q.p, sms));
+               align256(ftrsm_ws_bytes(q.side, q.uplo, FFGPU_TRSM_DEFAULT, q.m, q.n, q.p, sms));
     }
 
     // enqueue the whole request on stream `si` using arena block `off`
@@ -163,7 +162,8 @@ struct Server {
             const size_t ws_bytes = q->bytes - size_t(ws - blk);
             cudaMemcpy2DAsync(dT, nt * 4, r.A, r.lda * 4, nt * 4, nt, cudaMemcpyHostToDevice, s);
             cudaMemcpy2DAsync(dB, r.n * 4, r.B, r.ldb * 4, r.n * 4, r.m, cudaMemcpyHostToDevice, s);
-            st = ftrsm_run(r.side, r.uplo, r.diag, r.m, r.n, r.p, r.alpha, dT, nt, dB, r.n, ws, ws_bytes, errs[si], s);
+            st = ftrsm_run(r.side, r.uplo, r.diag, FFGPU_TRSM_DEFAULT, r.m, r.n, r.p, r.alpha, dT, nt, dB, r.n, ws, ws_bytes,
+                           errs[si], s);
             cudaMemcpy2DAsync(r.out, r.ldo * 4, dB, r.n * 4, r.n * 4, r.m, cudaMemcpyDeviceToHost, s);
         }
         cudaEventRecord(q->done, s);

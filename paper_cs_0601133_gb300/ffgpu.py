@@ -128,6 +128,7 @@ SIGNATURES = {
                                       ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)],
     "ffgpu_fgemm_batched_plan_destroy": [_VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
+    "ffgpu_ftrsm_ex": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _I32, _VP],
     "ffgpu_selftest_wait_timeout": [_I64, _VP],
     "ffgpu_autotune": [_I64, _I64, _I64, _U32, _I32, _VP, ctypes.POINTER(Tuned)],
     "ffgpu_autotune_lookup": [_I64, _I64, _I64, _U32, _I32, ctypes.POINTER(Tuned)],
@@ -337,16 +338,23 @@ def fgemm_batched(problems, stream=None):
     return [pr[2] for pr in probs]
 
 
-def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: str = "U", stream=None):
-    """In place: B <- alpha*T^{-1}*B (side "L") or alpha*B*T^{-1} (side "R") mod p. Returns B."""
+TRSM_ALGORITHMS = {"default": -1, "recursive": 0, "delayed": 1}
+
+
+def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: str = "U", stream=None,
+          algorithm: str = "default"):
+    """In place: B <- alpha*T^{-1}*B (side "L") or alpha*B*T^{-1} (side "R") mod p. Returns B.
+    algorithm: "recursive" (Algorithm 1), "delayed" (left-looking, one reduction
+    per block) or "default"."""
     m, n = B.shape
     nt = m if side == "L" else n
     if tuple(T.shape) != (nt, nt):
         raise ValueError("T must be %d x %d" % (nt, nt))
     t, ldt = _mat(T, "T")
     b, ldb = _mat(B, "B")
-    check(lib().ffgpu_ftrsm(0 if side == "L" else 1, 0 if uplo == "L" else 1, 1 if diag == "U" else 0,
-                            m, n, p, alpha % 2**32, t, ldt, b, ldb, _stream_ptr(stream)), "ffgpu_ftrsm")
+    check(lib().ffgpu_ftrsm_ex(0 if side == "L" else 1, 0 if uplo == "L" else 1, 1 if diag == "U" else 0,
+                               m, n, p, alpha % 2**32, t, ldt, b, ldb, TRSM_ALGORITHMS[algorithm],
+                               _stream_ptr(stream)), "ffgpu_ftrsm_ex")
     return B
 
 

@@ -18,19 +18,20 @@ from tests.gpu_util import from_dev, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def solve(T, B, p, alpha, side, uplo, diag):
+def solve(T, B, p, alpha, side, uplo, diag, algorithm="default"):
     dT, dB = to_dev(T), to_dev(B)
-    ff.ftrsm(dT, dB, p, alpha, side, uplo, diag)
+    ff.ftrsm(dT, dB, p, alpha, side, uplo, diag, algorithm=algorithm)
     torch.cuda.synchronize()
     rc = ff.last_device_error()
     return from_dev(dB), rc
 
 
+@pytest.mark.parametrize("algorithm", ["recursive", "delayed"])
 @pytest.mark.parametrize("p", [3, 251, 65521, 2147483647])
 @pytest.mark.parametrize("side", ["L", "R"])
 @pytest.mark.parametrize("uplo", ["L", "U"])
 @pytest.mark.parametrize("diag", ["U", "N"])
-def test_against_oracle(p, side, uplo, diag):
+def test_against_oracle(p, side, uplo, diag, algorithm):
     rng = W.rng_for("ftrsm", p, ord(side), ord(uplo), ord(diag))
     m, n = (300, 170) if side == "L" else (170, 300)
     nt = m if side == "L" else n
@@ -39,7 +40,7 @@ def test_against_oracle(p, side, uplo, diag):
     T = T + (W.uniform_words(rng, T.shape) % 7).astype(np.uint32) * (np.triu(np.ones_like(T), 1) if uplo == "L" else np.tril(np.ones_like(T), -1))
     B = W.uniform_words(rng, (m, n))
     alpha = int(rng.integers(1, p))
-    got, rc = solve(T, B, p, alpha, side, uplo, diag)
+    got, rc = solve(T, B, p, alpha, side, uplo, diag, algorithm)
     assert rc == 0
     expect = oracle.ftrsm(T, B, p, alpha, side, uplo, diag)
     assert np.array_equal(got, expect)
@@ -85,10 +86,11 @@ def test_singular_diagonal_is_reported():
     assert ff.last_device_error() == 0
 
 
+@pytest.mark.parametrize("algorithm", ["recursive", "delayed"])
 @pytest.mark.parametrize("p", [65521, 2147483647])
 @pytest.mark.parametrize("side,uplo,diag", [("L", "L", "U"), ("L", "U", "N"), ("R", "U", "U"), ("R", "L", "N"),
                                             ("L", "L", "N"), ("R", "U", "N")])
-def test_doubling_levels_and_ragged_leaves(p, side, uplo, diag):
+def test_doubling_levels_and_ragged_leaves(p, side, uplo, diag, algorithm):
     """2500-row triangle: 512-row leaves (two doubling levels 128 -> 256 ->
     512), the last leaf 452 rows, the last 128-block 68 rows."""
     rng = W.rng_for("ftrsm", 8, p, ord(side), ord(uplo), ord(diag))
@@ -97,12 +99,13 @@ def test_doubling_levels_and_ragged_leaves(p, side, uplo, diag):
     T = W.triangular(rng, nt, p, uplo, diag == "U")
     B = W.uniform_words(rng, (m, n))
     alpha = int(rng.integers(1, p))
-    got, rc = solve(T, B, p, alpha, side, uplo, diag)
+    got, rc = solve(T, B, p, alpha, side, uplo, diag, algorithm)
     assert rc == 0
     assert np.array_equal(got, oracle.ftrsm(T, B, p, alpha, side, uplo, diag))
 
 
-def test_three_doubling_levels_four_row_last_leaf():
+@pytest.mark.parametrize("algorithm", ["recursive", "delayed"])
+def test_three_doubling_levels_four_row_last_leaf(algorithm):
     """4100 rows: 1024-row leaves (doubling 128 -> ... -> 1024), a last leaf
     of 4 rows."""
     p = 2147483647
@@ -110,6 +113,6 @@ def test_three_doubling_levels_four_row_last_leaf():
     nt, nrhs = 4100, 40
     T = W.triangular(rng, nt, p, "L", False)
     B = W.uniform_residues(rng, (nt, nrhs), p)
-    got, rc = solve(T, B, p, 5, "L", "L", "N")
+    got, rc = solve(T, B, p, 5, "L", "L", "N", algorithm)
     assert rc == 0
     assert np.array_equal(got, oracle.ftrsm(T, B, p, 5, "L", "L", "N"))
