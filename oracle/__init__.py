@@ -1,4 +1,4 @@
-"""CPU oracle for fgemm / ftrsm over Z/pZ -- TEST INFRASTRUCTURE ONLY.
+"""CPU oracle for fgemm / ftrsm / LQUP over Z/pZ -- TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product path (the CUDA library and
@@ -8,6 +8,9 @@ product path.
 Contents
   * ``fgemm``/``fgemm_entries``/``matvec``/``ftrsm``: thin ctypes wrappers over
     ``ffgpu_oracle.c`` (the definitions, exact 128-bit integer arithmetic).
+  * ``lqup``/``rank``/``det``/``inverse``: LQUP by row-by-row elimination with
+    the first-non-zero pivot rule, rank by column echelon form, determinant by
+    Gaussian elimination, inverse by Gauss-Jordan (sections 5-6).
   * ``winograd``: the Strassen-Winograd schedule of Table 2 over Z with the
     intermediate-size tracking of Theorem 3.1 (section 3.2).
   * ``bounds``: the delayed-reduction bounds (eq. 1, eq. 2, Corollaries
@@ -55,9 +58,15 @@ def _load():
             lib.oracle_matvec.argtypes = [i64, i64, u32, vp, i64, vp, vp]
             lib.oracle_ftrsm.argtypes = [i, i, i, i64, i64, u32, u32, vp, i64, vp, i64]
             lib.oracle_num_threads.argtypes = []
+            lib.oracle_lqup.argtypes = [i64, i64, u32, vp, i64, vp, vp]
+            lib.oracle_rank.argtypes = [i64, i64, u32, vp, i64]
+            lib.oracle_det.argtypes = [i64, u32, vp, i64, vp]
+            lib.oracle_inverse.argtypes = [i64, u32, vp, i64, vp, i64]
             for f in (lib.oracle_fgemm, lib.oracle_fgemm_entries, lib.oracle_matvec,
-                      lib.oracle_ftrsm, lib.oracle_num_threads):
+                      lib.oracle_ftrsm, lib.oracle_num_threads, lib.oracle_det, lib.oracle_inverse):
                 f.restype = ctypes.c_int
+            lib.oracle_lqup.restype = ctypes.c_int64
+            lib.oracle_rank.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -154,3 +163,57 @@ def freivalds(A, B, C_old, C_new, p: int, alpha: int, beta: int, trials: int = 3
         if not np.array_equal(lhs.astype(np.uint64), rhs.astype(np.uint64)):
             return False
     return True
+
+
+def lqup(A, p: int):
+    """Packed LQUP of A mod p (p prime): returns (M, r, rowperm, colperm) with
+    A[rowperm][:, colperm] = L U mod p, M holding L strictly below the diagonal
+    of its first r columns and U on and above it (rows >= r zero beyond column
+    r).  A is not modified."""
+    A = _u32(A)
+    M = np.array(A, dtype=np.uint32, copy=True)
+    m, n = M.shape
+    rowperm = np.zeros(m, np.int32)
+    colperm = np.zeros(n, np.int32)
+    r = _load().oracle_lqup(m, n, p, _ptr(M), _ld(M) if m else max(n, 1), _ptr(rowperm), _ptr(colperm))
+    if r < 0:
+        raise ValueError("oracle_lqup failed (%d)" % r)
+    return M, int(r), rowperm, colperm
+
+
+def rank(A, p: int) -> int:
+    """Rank of A mod p (p prime), by column echelon form."""
+    A = np.ascontiguousarray(_u32(A))
+    m, n = A.shape
+    r = _load().oracle_rank(m, n, p, _ptr(A), max(n, 1))
+    if r < 0:
+        raise ValueError("oracle_rank failed (%d)" % r)
+    return int(r)
+
+
+def det(A, p: int) -> int:
+    """Determinant of the square matrix A mod p (p prime), by Gaussian elimination."""
+    A = np.ascontiguousarray(_u32(A))
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("det needs a square matrix")
+    out = np.zeros(1, np.uint32)
+    rc = _load().oracle_det(n, p, _ptr(A), max(n, 1), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_det failed (%d)" % rc)
+    return int(out[0])
+
+
+def inverse(A, p: int):
+    """A^{-1} mod p (p prime) by Gauss-Jordan elimination, or None if A is singular."""
+    A = np.ascontiguousarray(_u32(A))
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("inverse needs a square matrix")
+    X = np.zeros((n, n), np.uint32)
+    rc = _load().oracle_inverse(n, p, _ptr(A), max(n, 1), _ptr(X), max(n, 1))
+    if rc == 1:
+        return None
+    if rc != 0:
+        raise ValueError("oracle_inverse failed (%d)" % rc)
+    return X

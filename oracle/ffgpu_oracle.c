@@ -1,5 +1,6 @@
 /*
- * CPU oracle for fgemm / ftrsm over Z/pZ.  TEST INFRASTRUCTURE ONLY.
+ * CPU oracle for fgemm / ftrsm / LQUP (rank, determinant, inverse) over Z/pZ.
+ * TEST INFRASTRUCTURE ONLY.
  *
  * This file is the plain, slow, obviously correct definition of what the GPU
  * path computes.  It is called by tests/, by __graft_entry__.smoke() and by the
@@ -194,6 +195,220 @@ int oracle_ftrsm(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p,
         }
     }
     free(dinv);
+    return OR_OK;
+}
+
+/*
+ * LQUP (section 5: A = L Q U P with L lower triangular, P and Q permutations
+ * and U upper triangular of rank r whose first r rows are non-zero; section 6:
+ * rank, determinant and inverse derived from it), in packed form.
+ *
+ * Elimination row by row, top to bottom (the order in which the block
+ * recursion of section 5 meets the rows).  When row i is reached it holds its
+ * Schur complement s_i (every earlier pivot row has been subtracted from it).
+ * If s_i is zero, row i is not a pivot row.  Otherwise it becomes pivot number
+ * k with pivot column j = the smallest original column index with
+ * s_i[j] != 0; U_k = s_i; every later row t gets the multiplier
+ * l_tk = s_t[j] / s_i[j] and loses l_tk U_k.  The paper leaves the pivot
+ * choice to the implementation; this rule (first non-zero in original column
+ * order) makes the factorization unique, so a fast implementation that follows
+ * it must produce exactly this output.
+ *
+ * Output (p prime, every input first reduced mod p):
+ *   rowperm[0..m): the pivot rows in order, then the other rows ascending;
+ *   colperm[0..n): the pivot columns in pivot order, then the other columns
+ *                  ascending;
+ *   A overwritten by M with M[a][b] = L[a][b] for b < min(a, r) and
+ *   U[a][b] otherwise (zero for a >= r), where A[rowperm][:, colperm] = L U,
+ *   L m x r unit lower trapezoidal (its unit diagonal is not stored), U r x n
+ *   upper trapezoidal with non-zero diagonal.
+ * Returns the rank r, or a negative OR_* code.
+ */
+int64_t oracle_lqup(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda,
+                    int32_t* rowperm, int32_t* colperm)
+{
+    if (p < 2 || m < 0 || n < 0 || (m > 0 && lda < n)) return OR_INVALID;
+    const uint64_t P = p;
+    const int64_t mn = m < n ? m : n;
+    uint32_t* W = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m * n + 1));
+    uint32_t* Lm = (uint32_t*)calloc((size_t)(m * mn + 1), sizeof(uint32_t));
+    int64_t* prow = (int64_t*)malloc(sizeof(int64_t) * (size_t)(mn + 1));
+    int64_t* pcol = (int64_t*)malloc(sizeof(int64_t) * (size_t)(mn + 1));
+    char* used = (char*)calloc((size_t)(m + n + 1), 1);
+    if (!W || !Lm || !prow || !pcol || !used) {
+        free(W); free(Lm); free(prow); free(pcol); free(used);
+        return OR_NOMEM;
+    }
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) W[i * n + j] = (uint32_t)(A[i * lda + j] % P);
+    int64_t r = 0;
+    for (int64_t i = 0; i < m && r < mn; i++) {
+        const uint32_t* wi = W + i * n;
+        int64_t j = 0;
+        while (j < n && wi[j] == 0) j++;
+        if (j == n) continue;                    /* zero Schur complement: not a pivot row */
+        const uint64_t inv = inv_mod(wi[j], P);
+        if (inv == 0) { r = OR_INVALID; break; } /* p not prime */
+        prow[r] = i;
+        pcol[r] = j;
+#pragma omp parallel for schedule(static)
+        for (int64_t t = i + 1; t < m; t++) {
+            uint32_t* wt = W + t * n;
+            if (wt[j] == 0) continue;
+            const uint64_t l = ((uint64_t)wt[j] * inv) % P;
+            Lm[t * mn + r] = (uint32_t)l;
+            const uint64_t nl = P - l;
+            for (int64_t q = 0; q < n; q++) wt[q] = (uint32_t)(((uint64_t)wt[q] + nl * wi[q]) % P);
+        }
+        r++;
+    }
+    if (r >= 0) {
+        int64_t a = 0;
+        for (int64_t k = 0; k < r; k++) { rowperm[a++] = (int32_t)prow[k]; used[prow[k]] = 1; }
+        for (int64_t i = 0; i < m; i++) if (!used[i]) rowperm[a++] = (int32_t)i;
+        int64_t b = 0;
+        for (int64_t k = 0; k < r; k++) { colperm[b++] = (int32_t)pcol[k]; used[m + pcol[k]] = 1; }
+        for (int64_t j = 0; j < n; j++) if (!used[m + j]) colperm[b++] = (int32_t)j;
+        for (int64_t a2 = 0; a2 < m; a2++) {
+            const int64_t t = rowperm[a2];
+            for (int64_t b2 = 0; b2 < n; b2++) {
+                uint32_t v;
+                if (b2 < (a2 < r ? a2 : r)) v = Lm[t * mn + b2];
+                else v = a2 < r ? W[t * n + colperm[b2]] : 0u;
+                A[a2 * lda + b2] = v;
+            }
+        }
+    }
+    free(W); free(Lm); free(prow); free(pcol); free(used);
+    return r;
+}
+
+/*
+ * Rank by the textbook column-by-column reduction to row echelon form (an
+ * algorithm other than the one above): for each column, take the first
+ * remaining row with a non-zero entry as the pivot, swap it up, clear the
+ * column below it.  p prime.  Returns the rank, or a negative OR_* code.
+ */
+int64_t oracle_rank(int64_t m, int64_t n, uint32_t p, const uint32_t* A, int64_t lda)
+{
+    if (p < 2 || m < 0 || n < 0 || (m > 0 && lda < n)) return OR_INVALID;
+    const uint64_t P = p;
+    uint32_t* W = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(m * n + 1));
+    if (!W) return OR_NOMEM;
+    for (int64_t i = 0; i < m; i++)
+        for (int64_t j = 0; j < n; j++) W[i * n + j] = (uint32_t)(A[i * lda + j] % P);
+    int64_t row = 0;
+    for (int64_t col = 0; col < n && row < m; col++) {
+        int64_t piv = row;
+        while (piv < m && W[piv * n + col] == 0) piv++;
+        if (piv == m) continue;
+        if (piv != row)
+            for (int64_t q = 0; q < n; q++) {
+                const uint32_t x = W[row * n + q];
+                W[row * n + q] = W[piv * n + q];
+                W[piv * n + q] = x;
+            }
+        const uint64_t inv = inv_mod(W[row * n + col], P);
+        if (inv == 0) { free(W); return OR_INVALID; }
+#pragma omp parallel for schedule(static)
+        for (int64_t t = row + 1; t < m; t++) {
+            const uint64_t f = ((uint64_t)W[t * n + col] * inv) % P;
+            if (f == 0) continue;
+            for (int64_t q = col; q < n; q++)
+                W[t * n + q] = (uint32_t)(((uint64_t)W[t * n + q] + (P - f) * W[row * n + q]) % P);
+        }
+        row++;
+    }
+    free(W);
+    return row;
+}
+
+/*
+ * Determinant by textbook Gaussian elimination with row swaps (each swap
+ * negates it; section 6 defines the determinant through LQUP as the product of
+ * U's diagonal, this is the independent classical route).  p prime.
+ */
+int oracle_det(int64_t n, uint32_t p, const uint32_t* A, int64_t lda, uint32_t* det)
+{
+    if (p < 2 || n < 0 || (n > 0 && lda < n) || !det) return OR_INVALID;
+    const uint64_t P = p;
+    uint32_t* W = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n * n + 1));
+    if (!W) return OR_NOMEM;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) W[i * n + j] = (uint32_t)(A[i * lda + j] % P);
+    uint64_t d = 1 % P;
+    for (int64_t c = 0; c < n; c++) {
+        int64_t piv = c;
+        while (piv < n && W[piv * n + c] == 0) piv++;
+        if (piv == n) { d = 0; break; }
+        if (piv != c) {
+            for (int64_t q = 0; q < n; q++) {
+                const uint32_t x = W[c * n + q];
+                W[c * n + q] = W[piv * n + q];
+                W[piv * n + q] = x;
+            }
+            d = (P - d) % P;
+        }
+        const uint64_t pv = W[c * n + c], inv = inv_mod(pv, P);
+        if (inv == 0) { free(W); return OR_INVALID; }
+        d = (d * pv) % P;
+#pragma omp parallel for schedule(static)
+        for (int64_t t = c + 1; t < n; t++) {
+            const uint64_t f = ((uint64_t)W[t * n + c] * inv) % P;
+            if (f == 0) continue;
+            for (int64_t q = c; q < n; q++)
+                W[t * n + q] = (uint32_t)(((uint64_t)W[t * n + q] + (P - f) * W[c * n + q]) % P);
+        }
+    }
+    free(W);
+    *det = (uint32_t)d;
+    return OR_OK;
+}
+
+/*
+ * Inverse by Gauss-Jordan elimination on [A | I] (the classical definition;
+ * section 6 derives it from LQUP and two triangular solves).  X receives
+ * A^{-1} mod p.  Returns OR_OK, OR_SINGULAR if A is singular mod p (X is then
+ * unspecified), or another negative OR_* code.  p prime.
+ */
+#define OR_SINGULAR 1
+int oracle_inverse(int64_t n, uint32_t p, const uint32_t* A, int64_t lda, uint32_t* X, int64_t ldx)
+{
+    if (p < 2 || n < 0 || (n > 0 && (lda < n || ldx < n))) return OR_INVALID;
+    const uint64_t P = p;
+    const int64_t w = 2 * n;
+    uint32_t* W = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)(n * w + 1));
+    if (!W) return OR_NOMEM;
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) {
+            W[i * w + j] = (uint32_t)(A[i * lda + j] % P);
+            W[i * w + n + j] = (i == j) ? (uint32_t)(1 % P) : 0u;
+        }
+    for (int64_t c = 0; c < n; c++) {
+        int64_t piv = c;
+        while (piv < n && W[piv * w + c] == 0) piv++;
+        if (piv == n) { free(W); return OR_SINGULAR; }
+        if (piv != c)
+            for (int64_t q = 0; q < w; q++) {
+                const uint32_t x = W[c * w + q];
+                W[c * w + q] = W[piv * w + q];
+                W[piv * w + q] = x;
+            }
+        const uint64_t inv = inv_mod(W[c * w + c], P);
+        if (inv == 0) { free(W); return OR_INVALID; }
+        for (int64_t q = 0; q < w; q++) W[c * w + q] = (uint32_t)(((uint64_t)W[c * w + q] * inv) % P);
+#pragma omp parallel for schedule(static)
+        for (int64_t t = 0; t < n; t++) {
+            if (t == c) continue;
+            const uint64_t f = W[t * w + c];
+            if (f == 0) continue;
+            for (int64_t q = 0; q < w; q++)
+                W[t * w + q] = (uint32_t)(((uint64_t)W[t * w + q] + (P - f) * W[c * w + q]) % P);
+        }
+    }
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t j = 0; j < n; j++) X[i * ldx + j] = W[i * w + n + j];
+    free(W);
     return OR_OK;
 }
 

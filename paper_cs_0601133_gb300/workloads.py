@@ -13,6 +13,9 @@ with uniform residues modulo a word-size prime, sections 3.3 and 4.4):
     one integer matrix pair with entries in [-2^20, 2^20], reduced modulo each of
     32 primes just below 2^31 (the use of fgemm inside Chinese remaindering).
   * ``serving``: Poisson arrivals of mixed fgemm / ftrsm requests.
+  * ``lqup``: matrices to factor (section 5): uniform residues (full rank with
+    high probability), rank-deficient ones built by copying rows and columns,
+    ones whose leading columns are zero, and sparse ones.
 """
 from __future__ import annotations
 
@@ -21,7 +24,7 @@ import math
 import numpy as np
 
 SEED = 601133
-FAMILIES = ("square", "adversarial", "precision", "multimodular", "serving", "ftrsm", "smoke")
+FAMILIES = ("square", "adversarial", "precision", "multimodular", "serving", "ftrsm", "smoke", "lqup")
 
 
 def rng_for(family: str, *extra: int) -> np.random.Generator:
@@ -178,3 +181,37 @@ def serving_requests(n_requests: int = 2000, rate_per_s: float = 100.0, lo: int 
         p = int(primes[int(rng.integers(0, len(primes)))])
         out.append(dict(kind=kind, n=n, nrhs=nrhs, p=p, t_arrival=float(t[i]), seed=i))
     return out
+
+
+def lqup_matrix(rng: np.random.Generator, m: int, n: int, p: int, kind: str = "uniform",
+                r: int | None = None, z: int = 0, density: float = 0.1) -> np.ndarray:
+    """An m x n matrix of residues mod p for the factorization tests and bench.
+
+    kind "uniform": i.i.d. uniform residues.
+    kind "copies": r uniform base rows, every row a copy of a random base row,
+      then every column beyond the first r replaced, with probability 1/2, by a
+      copy of a random earlier column (rank at most r; built by copying only).
+    kind "zerolead": uniform, with the first z columns zero and every other
+      column zero with probability 1/8 (pivots far from the diagonal).
+    kind "sparse": each entry non-zero with probability `density`.
+    """
+    if kind == "uniform":
+        return uniform_residues(rng, (m, n), p)
+    if kind == "copies":
+        r = max(1, min(r if r is not None else min(m, n) // 2, m, n))
+        base = uniform_residues(rng, (r, n), p)
+        A = base[rng.integers(0, r, size=m)].copy()
+        for j in range(r, n):
+            if rng.integers(0, 2):
+                A[:, j] = A[:, int(rng.integers(0, j))]
+        return A
+    if kind == "zerolead":
+        A = uniform_residues(rng, (m, n), p)
+        A[:, : min(z, n)] = 0
+        A[:, rng.random(n) < 0.125] = 0
+        return A
+    if kind == "sparse":
+        A = uniform_residues(rng, (m, n), p)
+        A[rng.random((m, n)) >= density] = 0
+        return A
+    raise ValueError("unknown kind %r" % kind)
