@@ -51,7 +51,8 @@ typedef enum {
     FFGPU_ERR_NOMEM = -3,         /* workspace allocation failed or caller workspace too small */
     FFGPU_ERR_CUDA = -4,          /* a CUDA runtime call failed (launch, copy, no device) */
     FFGPU_ERR_TIMEOUT = -5,       /* a kernel's bounded wait ran out; its results are invalid */
-    FFGPU_ERR_BUDGET = -6         /* request exceeds a configured memory budget */
+    FFGPU_ERR_BUDGET = -6,        /* request exceeds a configured memory budget */
+    FFGPU_ERR_SINGULAR = -7       /* the matrix is singular mod p (ffgpu_inverse) */
 } ffgpu_status;
 
 /* Human-readable name of a status code (static storage). */
@@ -77,13 +78,19 @@ FFGPU_API ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, 
 
 /*
  * fgemm with a choice of arithmetic path and Winograd levels (section 3.2):
- *   path FFGPU_PATH_RNS  (0): the residue-number-system tensor-core path (default);
+ *   path FFGPU_PATH_RNS  (0): the default route of ffgpu_fgemm: the residue-number-
+ *                             system tensor-core path, small products on the
+ *                             CUDA cores (ffgpu_set_small_threshold);
  *   path FFGPU_PATH_FP64 (1): residues carried in doubles on the FP64 DMMA unit,
  *                             reduced after every 16 products (eq. 2, gamma = 53),
  *                             p < 2^25;
  *   path FFGPU_PATH_FP32 (2): residues carried in floats (SIMT FFMA), reduced
  *                             before the sum can reach 2^24 (eq. 1-2, gamma = 24),
- *                             p <= 256.
+ *                             p <= 256;
+ *   path FFGPU_PATH_SIMT (3): exact 96-bit integer dot products on the CUDA
+ *                             cores, one reduction per output (what ffgpu_fgemm
+ *                             uses for small products, see
+ *                             ffgpu_set_small_threshold); m below 4194240.
  * winograd_levels (0..8): recursive levels of Winograd's variant with the
  * schedule of Table 2 (additions mod p, products by the chosen path) and
  * dynamic peeling of odd dimensions.  Every combination gives the same exact
@@ -97,6 +104,18 @@ typedef struct {
 #define FFGPU_PATH_RNS 0
 #define FFGPU_PATH_FP64 1
 #define FFGPU_PATH_FP32 2
+#define FFGPU_PATH_SIMT 3
+
+/*
+ * Products with m*n*k at most max_macs multiply-adds (default 2^27) are
+ * computed by ffgpu_fgemm, ffgpu_ftrsm and the LQUP routines on the CUDA
+ * cores (path FFGPU_PATH_SIMT): for them the tensor-core path's fixed costs
+ * (conversions, one product per channel, the CRT epilogue) exceed the
+ * arithmetic.  0 sends every product to the tensor cores.  Process-wide; not
+ * in the paper.  FFGPU_ERR_INVALID for a negative value.
+ */
+FFGPU_API ffgpu_status ffgpu_set_small_threshold(int64_t max_macs);
+FFGPU_API int64_t ffgpu_get_small_threshold(void);
 
 FFGPU_API ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
                                       const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
@@ -223,6 +242,60 @@ FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int6
 FFGPU_API ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
                                       const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, int algorithm,
                                       void* stream);
+
+/*
+ * LQUP factorization over Z/pZ (section 5: A = L Q U P, L lower triangular,
+ * Q and P permutations, U upper triangular of rank r with its first r rows
+ * non-zero; block recursion on the rows, reduced to ftrsm and fgemm).
+ * In place and packed: afterwards A[rowperm][:, colperm] = L U mod p with
+ *   L  m x r, unit lower trapezoidal, stored strictly below the diagonal of
+ *      A's first r columns (its unit diagonal is not stored);
+ *   U  r x n, upper trapezoidal with a non-zero diagonal, stored on and above
+ *      the diagonal of A's first r rows;
+ *   A's rows r..m-1 are zero from column r on.
+ * Pivot rule (the paper leaves it open): rows are met top to bottom; a row
+ * whose Schur complement is non-zero is the next pivot row and its pivot
+ * column is the first non-zero one in original column order.  rowperm
+ * (device, m entries) lists the pivot rows in order, then the other rows
+ * ascending; colperm (device, n entries) the pivot columns in pivot order,
+ * then the other columns ascending.  With this rule the result is unique.
+ * *rank (host) receives r.
+ * A: device, row-major, lda >= n, entries any uint32 (taken mod p).  p must
+ * be a prime in [2, 2^31 - 1], else FFGPU_ERR_UNSUPPORTED_P.  The call is
+ * host-synchronous: pivot decisions are read back as the recursion proceeds
+ * (workspace from the stream's pool).  Errors: FFGPU_ERR_INVALID (shapes,
+ * null pointers, m or n above 2^30), FFGPU_ERR_NOMEM, FFGPU_ERR_CUDA,
+ * FFGPU_ERR_TIMEOUT (a product's bounded wait ran out).
+ */
+FFGPU_API ffgpu_status ffgpu_lqup(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda, int64_t* rank,
+                                  int32_t* rowperm, int32_t* colperm, void* stream);
+
+/*
+ * Rank of A mod p (section 6: the number of non-zero rows of U), from the
+ * LQUP of a copy of A; A (device, lda >= n) is not modified; *rank on the
+ * host.  Same p rule, synchronization and errors as ffgpu_lqup.
+ */
+FFGPU_API ffgpu_status ffgpu_rank(int64_t m, int64_t n, uint32_t p, const uint32_t* A, int64_t lda, int64_t* rank,
+                                  void* stream);
+
+/*
+ * Determinant of the n x n matrix A mod p (section 6: the product of U's
+ * diagonal, zero as soon as the rank is below n), signed by the column
+ * permutation; *det on the host, in [0, p); n = 0 gives 1.  A (device) is not
+ * modified.  Same p rule, synchronization and errors as ffgpu_lqup.
+ */
+FFGPU_API ffgpu_status ffgpu_det(int64_t n, uint32_t p, const uint32_t* A, int64_t lda, uint32_t* det,
+                                 void* stream);
+
+/*
+ * Inverse of the n x n matrix A mod p (section 6, "Matrix inverse": LQUP,
+ * then X = P^{-1} U^{-1} L^{-1} Q^{-1} by two triangular solves and a row
+ * permutation).  X (device, ldx >= n, must not overlap A) receives A^{-1};
+ * A is not modified.  FFGPU_ERR_SINGULAR if A is singular mod p (X is then
+ * unchanged).  Same p rule, synchronization and other errors as ffgpu_lqup.
+ */
+FFGPU_API ffgpu_status ffgpu_inverse(int64_t n, uint32_t p, const uint32_t* A, int64_t lda, uint32_t* X,
+                                     int64_t ldx, void* stream);
 
 /* One independent fgemm of a batch: C <- (alpha*A*B + beta*C) mod p. */
 typedef struct {

@@ -20,6 +20,45 @@ __device__ __forceinline__ uint32_t mod_u64(unsigned long long x, uint32_t p,
     return (uint32_t)r;
 }
 
+// a^{-1} mod p by the extended Euclidean algorithm (the classical
+// representation's division, section 2.1.1); 0 if a is not invertible.
+__device__ __forceinline__ uint32_t inv_mod_dev(uint32_t a, uint32_t p) {
+    long long r0 = p, r1 = a % p, s0 = 0, s1 = 1;
+    while (r1 != 0) {
+        const long long q = r0 / r1;
+        long long t = r0 - q * r1;
+        r0 = r1;
+        r1 = t;
+        t = s0 - q * s1;
+        s0 = s1;
+        s1 = t;
+    }
+    if (r0 != 1) return 0;
+    if (s0 < 0) s0 += p;
+    return (uint32_t)s0;
+}
+
+// floor(l 2^32 / p) for l < p < 2^31 (Shoup's precomputed quotient), from the
+// Barrett estimate of mod_u64 and at most two corrections.
+__device__ __forceinline__ uint32_t shoup_quot(uint32_t l, uint32_t p, unsigned long long mu) {
+    const unsigned long long x = (unsigned long long)l << 32;
+    unsigned long long q = __umul64hi(x, mu);
+    unsigned long long r = x - q * p;
+    while (r >= p) {
+        r -= p;
+        ++q;
+    }
+    return (uint32_t)q;
+}
+
+// l x mod p for any 32-bit x, l < p < 2^31 and ls = shoup_quot(l): the
+// estimate x l - floor(x ls / 2^32) p lies in [0, 2p), one subtraction left.
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t l, uint32_t ls, uint32_t p) {
+    const uint32_t q = __umulhi(x, ls);
+    const uint32_t t = x * l - q * p;
+    return t >= p ? t - p : t;
+}
+
 __device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
 }

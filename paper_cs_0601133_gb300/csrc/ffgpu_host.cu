@@ -59,6 +59,14 @@ std::mutex g_plan_mu;
 std::map<uint32_t, PlanCacheEntry> g_plan_cache;
 }  // namespace
 
+// True when fgemm_run(..., k, ...) converts all of A and B before its product
+// kernel writes C (a single k-slice): C may then overlap A or B.
+bool fgemm_single_pass(uint32_t p, int64_t k) {
+    RnsPlan pl;
+    make_plan(p, std::max<int64_t>(k, 1), pl);
+    return k <= pl.k_slice;
+}
+
 void make_plan(uint32_t p, int64_t k, RnsPlan& pl) {
     if (p <= kDirectMaxP) {
         build_plan(p, k, pl);
@@ -338,6 +346,17 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
                        const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                        uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s, int max_grid, bool untimed) {
+    if (m > 0 && n > 0 && fgemm_small(m, n, k)) {
+        auto f = [&] { return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, p, alpha, beta, s); };
+        return (untimed ? f() : timed_launch("small_gemm", s, f)) == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA;
+    }
+    return fgemm_run_rns(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_bytes, err, s, max_grid, untimed);
+}
+
+ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                           const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                           uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                           int* err, cudaStream_t s, int max_grid, bool untimed) {
     const unsigned long long mu = barrett_mu(p);
     auto launch = [&](const char* name, auto&& f) { return untimed ? f() : timed_launch(name, s, f); };
     const uint32_t al = alpha % p;
@@ -429,11 +448,20 @@ const char* ffgpu_status_string(ffgpu_status s) {
         case FFGPU_ERR_CUDA: return "FFGPU_ERR_CUDA";
         case FFGPU_ERR_TIMEOUT: return "FFGPU_ERR_TIMEOUT";
         case FFGPU_ERR_BUDGET: return "FFGPU_ERR_BUDGET";
+        case FFGPU_ERR_SINGULAR: return "FFGPU_ERR_SINGULAR";
     }
     return "FFGPU_UNKNOWN_STATUS";
 }
 
 int ffgpu_version(void) { return 100; }
+
+ffgpu_status ffgpu_set_small_threshold(int64_t max_macs) {
+    if (max_macs < 0) return FFGPU_ERR_INVALID;
+    set_small_threshold(max_macs);
+    return FFGPU_OK;
+}
+
+int64_t ffgpu_get_small_threshold(void) { return small_threshold(); }
 
 ffgpu_status ffgpu_fgemm_workspace_size(int64_t m, int64_t n, int64_t k, uint32_t p, size_t* bytes) {
     if (!bytes) return FFGPU_ERR_INVALID;

@@ -6,7 +6,7 @@
 // solve the second half.  The recursion stops at diagonal blocks of L rows,
 // L between 128 and 1024 (about eight leaves), whose inverses are computed up
 // front: one kernel inverts every 128 x 128 diagonal block (one CTA per block,
-// one thread per column of the inverse, substitution mod p; non-unit
+// eight lanes per column of the inverse, substitution mod p; non-unit
 // diagonals inverted by the extended Euclidean algorithm of section 2.1.1; a
 // non-invertible diagonal entry is recorded in the device error word), then
 // each doubling level s -> 2s forms the off-diagonal block of every pair
@@ -38,22 +38,6 @@ int64_t leaf_size(int64_t sz) {
     return L;
 }
 
-__device__ uint32_t inv_mod_dev(uint32_t a, uint32_t p) {
-    long long r0 = p, r1 = a % p, s0 = 0, s1 = 1;
-    while (r1 != 0) {
-        const long long q = r0 / r1;
-        long long t = r0 - q * r1;
-        r0 = r1;
-        r1 = t;
-        t = s0 - q * s1;
-        s0 = s1;
-        s1 = t;
-    }
-    if (r0 != 1) return 0;
-    if (s0 < 0) s0 += p;
-    return (uint32_t)s0;
-}
-
 // Exact sum of products as a 128-bit value (hi, lo); reduced once.
 struct Acc128 {
     unsigned long long lo = 0, hi = 0;
@@ -69,16 +53,19 @@ struct Acc128 {
 
 // Inverse of diagonal block b of T (rows/cols [b kBlk, b kBlk + tb)), written
 // densely into the leaf-sized inverse that contains it (kBlk x kBlk, zeros
-// outside the triangle).
-// Thread j computes column j of the inverse: T x = e_j by forward (lower) or
-// back (upper) substitution mod p; x lives in shared memory.
-__global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt, int size,
-                                                           int upper, int unit, uint32_t p, unsigned long long mu,
-                                                           uint32_t two64p, uint32_t* __restrict__ Inv, int leaf,
-                                                           int* err) {
+// outside the triangle).  One CTA of 8 kBlk threads: eight lanes per column
+// j of the inverse, which solves T x = e_j by forward (lower) or back (upper)
+// substitution mod p; each step's dot product is split over the eight lanes
+// (exact 128-bit partial sums, reduced once, combined by shuffles), so the
+// sequential chain is one short step per row.
+constexpr int kInvThreads = 8 * kBlk;
+__global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt,
+                                                                  int size, int upper, int unit, uint32_t p,
+                                                                  unsigned long long mu, uint32_t two64p,
+                                                                  uint32_t* __restrict__ Inv, int leaf, int* err) {
     extern __shared__ uint32_t sm[];
-    uint32_t* sX = sm;                     // [kBlk][kBlk]: x of thread j at sX[i*kBlk + j]
-    uint32_t* sT = sm + kBlk * kBlk;       // [kBlk][kBlk]: the block of T (read by every column's substitution)
+    uint32_t* sX = sm;                     // [kBlk][kBlk]: column j of the inverse at sX[i*kBlk + j]
+    uint32_t* sT = sm + kBlk * kBlk;       // [kBlk][kBlk]: the block of T
     uint32_t* sD = sm + 2 * kBlk * kBlk;   // [kBlk] inverse diagonal
     const int b = blockIdx.x;
     const int base = b * kBlk;
@@ -97,34 +84,37 @@ __global__ void __launch_bounds__(kBlk) trsm_invert_blocks(const uint32_t* __res
             sD[i] = d;
         }
     }
+    for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) sX[idx] = 0u;
     __syncthreads();
-    const int j = threadIdx.x;
-    // the block's place on the diagonal of its leaf-sized inverse (row-major, leading dimension `leaf`)
-    const int per = leaf / kBlk;
-    uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
-    if (j < tb) {
-        for (int s = 0; s < tb; ++s) {
-            const int i = upper ? tb - 1 - s : s;
-            uint32_t v;
-            if (upper ? i > j : i < j) {
-                v = 0u;  // outside the triangle of column j
-            } else {
-                Acc128 acc;
-                const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
-                // any 32-bit word times a residue < 2^31 stays below 2^63; the
-                // 128-bit sum of at most kBlk of them is reduced once
-                const uint32_t* Ti = sT + i * kBlk;
-                for (int l = lo; l < hi; ++l) acc.add((unsigned long long)Ti[l] * sX[l * kBlk + j]);
-                const uint32_t sum = acc.mod(p, mu, two64p);
-                const uint32_t rhs = (i == j) ? 1u : 0u;
-                const uint32_t t = rhs >= sum ? rhs - sum : rhs + (p - sum);
-                v = mod_u64((unsigned long long)t * sD[i], p, mu);
-            }
-            sX[i * kBlk + j] = v;
+    const int j = threadIdx.x >> 3, gl = threadIdx.x & 7;
+    const bool col = j < tb;
+    for (int s = 0; s < tb; ++s) {  // same trip count in every lane (shuffles below)
+        const int i = upper ? tb - 1 - s : s;
+        const bool act = col && (upper ? i <= j : i >= j);
+        Acc128 acc;
+        if (act) {
+            // any 32-bit word times a residue < 2^31 stays below 2^63
+            const uint32_t* Ti = sT + i * kBlk;
+            const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
+            for (int l = lo + gl; l < hi; l += 8) acc.add((unsigned long long)Ti[l] * sX[l * kBlk + j]);
         }
+        uint32_t v = act ? acc.mod(p, mu, two64p) : 0u;
+        for (int o = 4; o > 0; o >>= 1) {
+            const uint32_t y = __shfl_xor_sync(0xffffffffu, v, o);
+            v += y;
+            v = v >= p ? v - p : v;
+        }
+        if (act && gl == 0) {
+            const uint32_t rhs = (i == j) ? 1u : 0u;
+            const uint32_t t = rhs >= v ? rhs - v : rhs + (p - v);
+            sX[i * kBlk + j] = mod_u64((unsigned long long)t * sD[i], p, mu);
+        }
+        __syncwarp();
     }
     __syncthreads();
     // dense kBlk x kBlk block (zero padding beyond tb)
+    const int per = leaf / kBlk;
+    uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
     for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) {
         const int r = idx / kBlk, c = idx % kBlk;
         out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[r * kBlk + c] : 0u;
@@ -483,7 +473,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
     }
     const int nb = (int)((sz + kBlk - 1) / kBlk);
     if (timed_launch("trsm_invert_blocks", s, [&] {
-            trsm_invert_blocks<<<nb, kBlk, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p, inv, (int)Y.L,
+            trsm_invert_blocks<<<nb, kInvThreads, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p, inv, (int)Y.L,
                                                       err);
             return cudaGetLastError();
         }) != cudaSuccess)

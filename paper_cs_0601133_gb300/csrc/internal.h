@@ -196,11 +196,25 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
                        uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s, int max_grid, bool untimed);
 size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);
+// The tensor-core route alone (fgemm_run dispatches small products to the
+// CUDA-core kernel of small_gemm.cu, everything else here).
+ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
+                           const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
+                           uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                           int* err, cudaStream_t s, int max_grid, bool untimed);
+// small contractions on the CUDA cores (small_gemm.cu)
+bool fgemm_small(int64_t m, int64_t n, int64_t k);
+void set_small_threshold(int64_t macs);
+int64_t small_threshold();
+cudaError_t launch_small_gemm(int64_t m, int64_t n, int64_t k, const uint32_t* A, int64_t lda, const uint32_t* B,
+                              int64_t ldb, uint32_t* C, int64_t ldc, uint32_t p, uint32_t alpha, uint32_t beta,
+                              cudaStream_t s);
 ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
                         const void* B, int64_t ldb, const void* C, int64_t ldc);
 int sm_count(int dev);
 
 void make_plan(uint32_t p, int64_t k, RnsPlan& pl);
+bool fgemm_single_pass(uint32_t p, int64_t k);
 int chunk_steps_for(const RnsPlan& pl);
 unsigned long long barrett_mu(uint32_t p);
 void fill_inst(InstInfo& I, int64_t m, int64_t n, int64_t kp, const RnsPlan& pl, uint32_t al, uint32_t be,

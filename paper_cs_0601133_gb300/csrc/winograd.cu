@@ -83,6 +83,20 @@ ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, cons
         return fgemm_run(m, n, k, c.p, al, A, lda, B, ldb, be, C, ldc, c.fg_ws, c.fg_ws_bytes, c.err, c.s, 0,
                          false);
     }
+    if (c.path == 3) {
+        if (c.dry || k == 0) {
+            if (!c.dry)
+                return launch_scale(C, ldc, (int)m, (int)n, c.p, be, c.mu, c.s) == cudaSuccess ? FFGPU_OK
+                                                                                              : FFGPU_ERR_CUDA;
+            return FFGPU_OK;
+        }
+        if (m > int64_t(65535) * 64) return FFGPU_ERR_INVALID;
+        return timed_launch("small_gemm", c.s, [&] {
+                   return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, c.p, al, be, c.s);
+               }) == cudaSuccess
+                   ? FFGPU_OK
+                   : FFGPU_ERR_CUDA;
+    }
     if (c.dry) return FFGPU_OK;
     if (k == 0)
         return timed_launch("scale_mod_p", c.s, [&] { return launch_scale(C, ldc, (int)m, (int)n, c.p, be, c.mu, c.s); }) ==
@@ -162,7 +176,7 @@ ffgpu_status wino(WinoCtx& c, int level, int64_t m, int64_t n, int64_t k, uint32
 ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
                           int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
                           int path, int levels, cudaStream_t s) {
-    if (path < 0 || path > 2 || levels < 0 || levels > 8) return FFGPU_ERR_INVALID;
+    if (path < 0 || path > 3 || levels < 0 || levels > 8) return FFGPU_ERR_INVALID;
     if (path == 1 && p > dmma_max_p()) return FFGPU_ERR_UNSUPPORTED_P;
     if (path == 2 && p > sgemm_max_p()) return FFGPU_ERR_UNSUPPORTED_P;
     int dev = 0;

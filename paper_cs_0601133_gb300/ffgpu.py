@@ -26,6 +26,7 @@ STATUS = {
     -4: "FFGPU_ERR_CUDA",
     -5: "FFGPU_ERR_TIMEOUT",
     -6: "FFGPU_ERR_BUDGET",
+    -7: "FFGPU_ERR_SINGULAR",
 }
 
 
@@ -52,7 +53,7 @@ class Options(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 6)]
 
 
-PATHS = {"rns": 0, "fp64": 1, "fp32": 2}
+PATHS = {"rns": 0, "fp64": 1, "fp32": 2, "simt": 3}
 
 
 class Request(ctypes.Structure):
@@ -138,8 +139,14 @@ SIGNATURES = {
     "ffgpu_fgemm_auto": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _I32, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
+    "ffgpu_set_small_threshold": [_I64],
+    "ffgpu_get_small_threshold": [],
+    "ffgpu_lqup": [_I64, _I64, _U32, _VP, _I64, ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP],
+    "ffgpu_rank": [_I64, _I64, _U32, _VP, _I64, ctypes.POINTER(ctypes.c_int64), _VP],
+    "ffgpu_det": [_I64, _U32, _VP, _I64, ctypes.POINTER(_U32), _VP],
+    "ffgpu_inverse": [_I64, _U32, _VP, _I64, _VP, _I64, _VP],
 }
-_RESTYPES = {"ffgpu_status_string": ctypes.c_char_p}
+_RESTYPES = {"ffgpu_status_string": ctypes.c_char_p, "ffgpu_get_small_threshold": ctypes.c_int64}
 
 
 def lib():
@@ -211,7 +218,7 @@ def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, strea
 
 def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "rns",
              winograd_levels: int = 0, stream=None):
-    """fgemm through a chosen arithmetic path ("rns", "fp64", "fp32") with
+    """fgemm through a chosen arithmetic path ("rns", "fp64", "fp32", "simt") with
     `winograd_levels` levels of Winograd's variant. Returns C."""
     import torch
     m, k = A.shape
@@ -356,6 +363,67 @@ def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: 
                                m, n, p, alpha % 2**32, t, ldt, b, ldb, TRSM_ALGORITHMS[algorithm],
                                _stream_ptr(stream)), "ffgpu_ftrsm_ex")
     return B
+
+
+def set_small_threshold(max_macs: int) -> None:
+    """Products with m*n*k <= max_macs run on the CUDA cores (0: none)."""
+    check(lib().ffgpu_set_small_threshold(max_macs), "ffgpu_set_small_threshold")
+
+
+def get_small_threshold() -> int:
+    return int(lib().ffgpu_get_small_threshold())
+
+
+def lqup(A, p: int, stream=None):
+    """In-place packed LQUP of A mod p (p prime): afterwards
+    A[rowperm][:, colperm] = L U, L strictly below the diagonal of A's first r
+    columns (unit diagonal implied), U on and above the diagonal of its first
+    r rows.  Returns (r, rowperm, colperm), the permutations as int32 CUDA
+    tensors.  Host-synchronous."""
+    import torch
+    m, n = A.shape
+    a, lda = _mat(A, "A")
+    rowperm = torch.empty(m, dtype=torch.int32, device=A.device)
+    colperm = torch.empty(n, dtype=torch.int32, device=A.device)
+    r = ctypes.c_int64(0)
+    check(lib().ffgpu_lqup(m, n, p, a, lda, ctypes.byref(r), rowperm.data_ptr(), colperm.data_ptr(),
+                           _stream_ptr(stream)), "ffgpu_lqup")
+    return int(r.value), rowperm, colperm
+
+
+def rank(A, p: int, stream=None) -> int:
+    """Rank of A mod p (p prime); A is not modified."""
+    m, n = A.shape
+    a, lda = _mat(A, "A")
+    r = ctypes.c_int64(0)
+    check(lib().ffgpu_rank(m, n, p, a, lda, ctypes.byref(r), _stream_ptr(stream)), "ffgpu_rank")
+    return int(r.value)
+
+
+def det(A, p: int, stream=None) -> int:
+    """Determinant of the square matrix A mod p (p prime), in [0, p)."""
+    n, n2 = A.shape
+    if n != n2:
+        raise ValueError("det needs a square matrix")
+    a, lda = _mat(A, "A")
+    d = ctypes.c_uint32(0)
+    check(lib().ffgpu_det(n, p, a, lda, ctypes.byref(d), _stream_ptr(stream)), "ffgpu_det")
+    return int(d.value)
+
+
+def inverse(A, p: int, X=None, stream=None):
+    """A^{-1} mod p (p prime) into X (allocated if None); raises FFGPUError
+    with FFGPU_ERR_SINGULAR (-7) if A is singular mod p.  Returns X."""
+    import torch
+    n, n2 = A.shape
+    if n != n2:
+        raise ValueError("inverse needs a square matrix")
+    if X is None:
+        X = torch.zeros((n, n), dtype=torch.uint32, device=A.device)
+    a, lda = _mat(A, "A")
+    x, ldx = _mat(X, "X")
+    check(lib().ffgpu_inverse(n, p, a, lda, x, ldx, _stream_ptr(stream)), "ffgpu_inverse")
+    return X
 
 
 def fgemm_noalloc_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream_ptr=0) -> int:

@@ -18,6 +18,16 @@ from tests.gpu_util import from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
+@pytest.fixture(autouse=True, scope="module")
+def tensor_cores_only():
+    """Every product of this module on the tensor-core route, small ones
+    included (ffgpu_fgemm would send those to the CUDA-core kernel)."""
+    old = ff.get_small_threshold()
+    ff.set_small_threshold(0)
+    yield
+    ff.set_small_threshold(old)
+
+
 SWEEP = [251, 65521, 8388593, 2147483647]
 
 

@@ -15,6 +15,16 @@ from tests.gpu_util import from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
+@pytest.fixture(autouse=True, scope="module")
+def tensor_cores_only():
+    """Every product of this module on the tensor-core route, small ones
+    included (ffgpu_fgemm would send those to the CUDA-core kernel)."""
+    old = ff.get_small_threshold()
+    ff.set_small_threshold(0)
+    yield
+    ff.set_small_threshold(old)
+
+
 CASES = [("rns", 65521), ("rns", 2147483647), ("rns", 251), ("fp64", 251), ("fp64", 65521),
          ("fp64", 1048573), ("fp64", 8388593), ("fp32", 251), ("fp32", 2)]
 
@@ -65,3 +75,14 @@ def test_unsupported_modulus_for_a_path():
         ff.fgemm_ex(A, A, 257, path="fp32")
     with pytest.raises(ff.FFGPUError):
         ff.fgemm_ex(A, A, 2**25 + 1, path="fp64")
+
+
+@pytest.mark.parametrize("p", [2, 251, 65521, 2147483647])
+@pytest.mark.parametrize("levels", [0, 1, 2])
+def test_simt_path_with_levels(p, levels):
+    rng = W.rng_for("precision", p, levels, 7)
+    m, n, k = 131, 97, 259
+    A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta, "simt", levels)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
