@@ -336,7 +336,9 @@ size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
     RnsPlan pl;
     make_plan(p, k, pl);
     const int64_t ks = std::min<int64_t>(k, pl.k_slice);
-    return layout_for(m, n, round64(ks), pl.nch, grid_for_tiles(m, n, sms)).total;
+    const size_t rns = layout_for(m, n, round64(ks), pl.nch, grid_for_tiles(m, n, sms)).total;
+    // a small product runs on the CUDA cores, its k-split partial sums in the workspace
+    return fgemm_small(m, n, k) ? std::max(rns, small_ws_bytes(m, n, k, sms)) : rns;
 }
 
 // The launch sequence: per slice of the inner dimension, convert A and B to
@@ -347,7 +349,10 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
                        uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s, int max_grid, bool untimed) {
     if (m > 0 && n > 0 && fgemm_small(m, n, k)) {
-        auto f = [&] { return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, p, alpha, beta, s); };
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int sms = sm_count(dev);
+        auto f = [&] { return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, p, alpha, beta, ws, ws_bytes, sms, s); };
         return (untimed ? f() : timed_launch("small_gemm", s, f)) == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA;
     }
     return fgemm_run_rns(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_bytes, err, s, max_grid, untimed);

@@ -206,9 +206,13 @@ ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t
 bool fgemm_small(int64_t m, int64_t n, int64_t k);
 void set_small_threshold(int64_t macs);
 int64_t small_threshold();
+size_t small_ws_bytes(int64_t m, int64_t n, int64_t k, int sms);
+// ws may be null (then no k-split); C may overlap A or B when the launch
+// splits k (partial sums first) or when n <= 64 (each CTA reads only the rows
+// it writes).
 cudaError_t launch_small_gemm(int64_t m, int64_t n, int64_t k, const uint32_t* A, int64_t lda, const uint32_t* B,
                               int64_t ldb, uint32_t* C, int64_t ldc, uint32_t p, uint32_t alpha, uint32_t beta,
-                              cudaStream_t s);
+                              void* ws, size_t ws_bytes, int sms, cudaStream_t s);
 ffgpu_status check_args(int64_t m, int64_t n, int64_t k, uint32_t p, const void* A, int64_t lda,
                         const void* B, int64_t ldb, const void* C, int64_t ldc);
 int sm_count(int dev);

@@ -9,7 +9,10 @@
 // mod p once, then alpha and beta applied (the delayed reduction of section
 // 3.1 taken to its limit: one reduction per output).  64 x 64 output tiles,
 // 256 threads with 4 x 4 outputs each, k staged through shared memory 32 at a
-// time.
+// time.  When the tiles alone would not fill two waves of CTAs, k is split:
+// each split writes its exact 96-bit partial sums to the workspace and a
+// second kernel adds them, reduces mod p and applies alpha and beta (C is then
+// written only after every read of A and B).
 #include <algorithm>
 #include <atomic>
 
@@ -32,10 +35,24 @@ __device__ __forceinline__ void mac96(uint32_t& lo, uint32_t& mid, uint32_t& hi,
         : "r"(a), "r"(b));
 }
 
-__global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, int k, const uint32_t* __restrict__ A,
-                                                                long long lda, const uint32_t* __restrict__ B,
-                                                                long long ldb, uint32_t* C, long long ldc, uint32_t p,
-                                                                unsigned long long mu, uint32_t two64p,
+// (hi 2^64 + mid 2^32 + lo) mod p, then alpha v + beta c mod p
+__device__ __forceinline__ uint32_t finish96(uint32_t lo, uint32_t mid, uint32_t hi, uint32_t c, uint32_t p,
+                                             unsigned long long mu, uint32_t two64p, uint32_t alpha, uint32_t beta) {
+    const uint32_t th = mod_u64((unsigned long long)mod_u64(hi, p, mu) * two64p, p, mu);
+    const uint32_t tl = mod_u64(((unsigned long long)mid << 32) | lo, p, mu);
+    const uint32_t v = th + tl >= p ? th + tl - p : th + tl;
+    const unsigned long long acc = (unsigned long long)alpha * v + (unsigned long long)beta * c;
+    return mod_u64(acc, p, mu);
+}
+
+// Split s = blockIdx.z sums k-range [s kps, (s + 1) kps); with part null it
+// finishes the outputs itself, else it stores its partial sums there
+// (uint4 per output: lo, mid, hi, 0; split-major, m x n each).
+__global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, int k, int kps,
+                                                                const uint32_t* __restrict__ A, long long lda,
+                                                                const uint32_t* __restrict__ B, long long ldb,
+                                                                uint32_t* C, long long ldc, uint4* __restrict__ part,
+                                                                uint32_t p, unsigned long long mu, uint32_t two64p,
                                                                 uint32_t alpha, uint32_t beta) {
     __shared__ __align__(16) uint32_t As[kSmK][kSmT];  // As[kk][row]
     __shared__ __align__(16) uint32_t Bs[kSmK][kSmT];  // Bs[kk][col]
@@ -46,13 +63,14 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) lo[i][j] = mid[i][j] = hi[i][j] = 0u;
-    for (int k0 = 0; k0 < k; k0 += kSmK) {
+    const int kbeg = blockIdx.z * kps, kend = min(k, kbeg + kps);
+    for (int k0 = kbeg; k0 < kend; k0 += kSmK) {
         {
             const int r = tid >> 2, kk0 = (tid & 3) * 8, gi = row0 + r;
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int gk = k0 + kk0 + e;
-                As[kk0 + e][r] = (gi < m && gk < k) ? __ldg(A + (long long)gi * lda + gk) : 0u;
+                As[kk0 + e][r] = (gi < m && gk < kend) ? __ldg(A + (long long)gi * lda + gk) : 0u;
             }
         }
         {
@@ -60,7 +78,7 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int gj = col0 + c0 + e;
-                Bs[kk][c0 + e] = (gk < k && gj < n) ? __ldg(B + (long long)gk * ldb + gj) : 0u;
+                Bs[kk][c0 + e] = (gk < kend && gj < n) ? __ldg(B + (long long)gk * ldb + gj) : 0u;
             }
         }
         __syncthreads();
@@ -84,16 +102,48 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
         for (int j = 0; j < 4; ++j) {
             const int gj = col0 + tx * 4 + j;
             if (gj >= n) continue;
-            // (hi 2^64 + mid 2^32 + lo) mod p
-            const uint32_t th = mod_u64((unsigned long long)mod_u64(hi[i][j], p, mu) * two64p, p, mu);
-            const uint32_t tl = mod_u64(((unsigned long long)mid[i][j] << 32) | lo[i][j], p, mu);
-            const uint32_t v = th + tl >= p ? th + tl - p : th + tl;
-            uint32_t* cp = C + (long long)gi * ldc + gj;
-            const unsigned long long acc =
-                (unsigned long long)alpha * v + (beta ? (unsigned long long)beta * (*cp) : 0ull);
-            *cp = mod_u64(acc, p, mu);
+            if (part) {
+                part[((long long)blockIdx.z * m + gi) * n + gj] = make_uint4(lo[i][j], mid[i][j], hi[i][j], 0u);
+            } else {
+                uint32_t* cp = C + (long long)gi * ldc + gj;
+                *cp = finish96(lo[i][j], mid[i][j], hi[i][j], beta ? *cp : 0u, p, mu, two64p, alpha, beta);
+            }
         }
     }
+}
+
+// Sum of the splits' partial sums (below k 2^64 < 2^96, so three words and
+// their carries suffice), then the reduction and alpha, beta.
+__global__ void __launch_bounds__(kSmThreads) small_reduce_kernel(int m, int n, int splits,
+                                                                  const uint4* __restrict__ part, uint32_t* C,
+                                                                  long long ldc, uint32_t p, unsigned long long mu,
+                                                                  uint32_t two64p, uint32_t alpha, uint32_t beta) {
+    const long long total = (long long)m * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        uint32_t lo = 0u, mid = 0u, hi = 0u;
+        for (int z = 0; z < splits; ++z) {
+            const uint4 q = __ldg(part + z * total + e);
+            asm("add.cc.u32 %0, %0, %3;\n\t"
+                "addc.cc.u32 %1, %1, %4;\n\t"
+                "addc.u32 %2, %2, %5;"
+                : "+r"(lo), "+r"(mid), "+r"(hi)
+                : "r"(q.x), "r"(q.y), "r"(q.z));
+        }
+        const int gi = (int)(e / n), gj = (int)(e - (long long)gi * n);
+        uint32_t* cp = C + (long long)gi * ldc + gj;
+        *cp = finish96(lo, mid, hi, beta ? *cp : 0u, p, mu, two64p, alpha, beta);
+    }
+}
+
+// Number of k-splits for a product: enough CTAs for two waves, each split at
+// least one 32-long chunk, at most 16.
+int small_splits(int64_t m, int64_t n, int64_t k, int sms) {
+    const int64_t tiles = ((m + kSmT - 1) / kSmT) * ((n + kSmT - 1) / kSmT);
+    const int64_t chunks = (k + kSmK - 1) / kSmK;
+    int s = 1;
+    while (s < 16 && tiles * s < 2 * (int64_t)sms && 2 * s <= chunks) s *= 2;
+    return s;
 }
 
 }  // namespace
@@ -113,16 +163,32 @@ bool fgemm_small(int64_t m, int64_t n, int64_t k) {
            m <= int64_t(65535) * kSmT;
 }
 
+size_t small_ws_bytes(int64_t m, int64_t n, int64_t k, int sms) {
+    const int sp = small_splits(m, n, k, sms);
+    return sp > 1 ? size_t(sp) * m * n * sizeof(uint4) : 0;
+}
+
 cudaError_t launch_small_gemm(int64_t m, int64_t n, int64_t k, const uint32_t* A, int64_t lda, const uint32_t* B,
                               int64_t ldb, uint32_t* C, int64_t ldc, uint32_t p, uint32_t alpha, uint32_t beta,
-                              cudaStream_t s) {
+                              void* ws, size_t ws_bytes, int sms, cudaStream_t s) {
     if (m == 0 || n == 0) return cudaSuccess;
     const unsigned long long mu = ~0ull / p;
     const uint32_t two64p = (uint32_t)(((unsigned __int128)1 << 64) % p);
-    const dim3 grid((unsigned)((n + kSmT - 1) / kSmT), (unsigned)((m + kSmT - 1) / kSmT));
+    int sp = small_splits(m, n, k, sms);
+    if (sp > 1 && (!ws || size_t(sp) * m * n * sizeof(uint4) > ws_bytes || (reinterpret_cast<uintptr_t>(ws) & 15)))
+        sp = 1;
+    const int64_t chunks = (k + kSmK - 1) / kSmK;
+    const int kps = (int)(((chunks + sp - 1) / sp) * kSmK);
+    const dim3 grid((unsigned)((n + kSmT - 1) / kSmT), (unsigned)((m + kSmT - 1) / kSmT), (unsigned)sp);
     if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
-    small_gemm_kernel<<<grid, kSmThreads, 0, s>>>((int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, p, mu, two64p,
-                                                  alpha % p, beta % p);
+    uint4* part = sp > 1 ? static_cast<uint4*>(ws) : nullptr;
+    small_gemm_kernel<<<grid, kSmThreads, 0, s>>>((int)m, (int)n, (int)k, kps, A, lda, B, ldb, C, ldc, part, p, mu,
+                                                  two64p, alpha % p, beta % p);
+    if (sp > 1) {
+        const long long blocks = std::min<long long>((m * n + kSmThreads - 1) / kSmThreads, (long long)sms * 8);
+        small_reduce_kernel<<<(unsigned)blocks, kSmThreads, 0, s>>>((int)m, (int)n, sp, part, C, ldc, p, mu, two64p,
+                                                                    alpha % p, beta % p);
+    }
     return cudaGetLastError();
 }
 

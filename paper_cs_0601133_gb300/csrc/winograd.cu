@@ -92,7 +92,7 @@ ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, cons
         }
         if (m > int64_t(65535) * 64) return FFGPU_ERR_INVALID;
         return timed_launch("small_gemm", c.s, [&] {
-                   return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, c.p, al, be, c.s);
+                   return launch_small_gemm(m, n, k, A, lda, B, ldb, C, ldc, c.p, al, be, nullptr, 0, c.sms, c.s);
                }) == cudaSuccess
                    ? FFGPU_OK
                    : FFGPU_ERR_CUDA;
