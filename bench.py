@@ -48,7 +48,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve", "ftrsm", "batched", "multimod"],
+    ap.add_argument("--lqup-n", type=int, default=0,
+                    help="--workload lqup: only this n (with --p), uniform matrix")
+    ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve", "ftrsm", "batched", "multimod",
+                                           "lqup"],
                     default="headline",
                     help="headline: the driver's line; the others print one line per configuration point")
     return ap.parse_args()
@@ -488,6 +491,54 @@ def run_ftrsm(args):
     return 0
 
 
+def run_lqup(args):
+    """LQUP and what section 6 derives from it: effective GOPS with the classic
+    counts (LQUP of an n x n matrix 2n^3/3, inverse 2n^3), the time ratio
+    LQUP / fgemm at the same n (the paper's comparison of triangularization
+    with multiplication), rank and determinant.  Uniform residues (full rank),
+    and one rank-deficient matrix of copied rows and columns."""
+    import torch
+    import paper_cs_0601133_gb300 as ff
+    from paper_cs_0601133_gb300 import workloads as W
+    cases = [(n, p, "uniform") for n in (2048, 4096, 8192) for p in (65521, 2147483647)]
+    cases.append((4096, 2147483647, "copies"))
+    if args.lqup_n:
+        cases = [(args.lqup_n, args.p, "uniform")]
+    for n, p, kind in cases:
+        rng = W.rng_for("lqup", 2000, n, p % 1000003)
+        A = W.lqup_matrix(rng, n, n, p, kind, r=n // 2)
+        dA0 = torch.from_numpy(A.view(np.int32)).cuda()
+        dA = dA0.clone()
+        steps = 3 if n < 8192 else 2
+        copy_ms = time_call(lambda: dA.copy_(dA0), torch, steps, 1)
+        holder = {}
+
+        def factor():
+            dA.copy_(dA0)
+            holder["r"] = ff.lqup(dA, p)[0]
+        lqup_ms = time_call(factor, torch, steps, 1) - copy_ms
+        dC = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+        gemm_ms = time_call(lambda: ff.fgemm(dA0, dA0, p, 1, 0, dC), torch, steps, 1)
+        det_ms = time_call(lambda: holder.__setitem__("det", ff.det(dA0, p)), torch, steps, 1)
+        X = torch.zeros((n, n), dtype=torch.int32, device="cuda")
+        inv_ms = None
+        if holder["r"] == n:
+            inv_ms = time_call(lambda: ff.inverse(dA0, p, X), torch, steps, 1)
+        ff.profile_enable(True)
+        factor()
+        torch.cuda.synchronize()
+        ff.profile_enable(False)
+        kern = {k: (v[0], round(v[1], 3)) for k, v in ff.profile_read().items()}
+        out = {"workload": "lqup", "n": n, "p": p, "matrix": kind, "rank": holder["r"], "lqup_ms": lqup_ms,
+               "lqup_GOPS": 2 * n ** 3 / 3 / (lqup_ms / 1e3) / 1e9, "fgemm_ms": gemm_ms,
+               "lqup_over_fgemm": lqup_ms / gemm_ms, "det_ms": det_ms, "inverse_ms": inv_ms,
+               "inverse_GOPS": (2 * n ** 3 / (inv_ms / 1e3) / 1e9) if inv_ms else None,
+               "kernels_launches_ms": kern}
+        print(json.dumps(out), flush=True)
+        del dA0, dA, dC, X
+    return 0
+
+
 def run_batched(args):
     """Batched multi-modular fgemm: instances with m, n, k log-uniform in
     [16, 1024], one integer matrix pair per instance (entries in [-2^20, 2^20])
@@ -606,6 +657,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "lqup":
+        return run_lqup(args)
     if args.workload == "sweep":
         return run_sweep(args)
     if args.workload == "precision":
