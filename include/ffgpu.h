@@ -95,16 +95,30 @@ FFGPU_API ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, 
  * schedule of Table 2 (additions mod p, products by the chosen path) and
  * dynamic peeling of odd dimensions.  Every combination gives the same exact
  * result as ffgpu_fgemm.  p outside a path's range: FFGPU_ERR_UNSUPPORTED_P.
+ * unreduced = 1 (with winograd_levels >= 1; path ignored): the variant that
+ * section 3.2 analyses -- the levels run over Z on balanced residues (int32
+ * operands, exact int64 products and sums) and the result is reduced once
+ * at the end; admitted only when Theorem 3.1's bound on every intermediate
+ * value, (3^l (p-1)/2)^2 floor(k/2^l), is below 2^62 and the operands
+ * (at most 4^l (p-1)/2) fit int32, else FFGPU_ERR_UNSUPPORTED_P
+ * (ffgpu_winograd_unreduced_kmax gives the largest admitted k).
  */
 typedef struct {
     int32_t path;
     int32_t winograd_levels;
-    int32_t reserved[6];   /* must be zero */
+    int32_t unreduced;     /* 1: the levels' additions over Z, no reduction until the end (below) */
+    int32_t reserved[5];   /* must be zero */
 } ffgpu_options;
 #define FFGPU_PATH_RNS 0
 #define FFGPU_PATH_FP64 1
 #define FFGPU_PATH_FP32 2
 #define FFGPU_PATH_SIMT 3
+
+/* Largest inner dimension k that l unreduced Winograd levels admit for p
+ * (Theorem 3.1 / Corollary 3.4 with a 62-bit exact range, int32 operands);
+ * 0 if none.  Host-only.  FFGPU_ERR_INVALID for p outside [2, 2^31 - 1] or
+ * l outside [1, 8]. */
+FFGPU_API ffgpu_status ffgpu_winograd_unreduced_kmax(uint32_t p, int levels, int64_t* kmax);
 
 /*
  * Products with m*n*k at most max_macs multiply-adds (default 2^27) are

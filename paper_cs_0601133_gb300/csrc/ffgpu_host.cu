@@ -543,9 +543,14 @@ ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
     ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
     if (st != FFGPU_OK || m == 0 || n == 0) return st;
     const int path = opt ? opt->path : 0, levels = opt ? opt->winograd_levels : 0;
-    if (opt)
-        for (int i = 0; i < 6; ++i)
+    if (opt) {
+        for (int i = 0; i < 5; ++i)
             if (opt->reserved[i] != 0) return FFGPU_ERR_INVALID;
+        if (opt->unreduced != 0 && opt->unreduced != 1) return FFGPU_ERR_INVALID;
+        if (opt->unreduced)
+            return winograd_z_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, levels,
+                                  static_cast<cudaStream_t>(stream));
+    }
     if (path == 0 && levels == 0)
         return ffgpu_fgemm(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, stream);
     return fgemm_ex_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, path, levels,

@@ -230,6 +230,12 @@ ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t 
                           int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
                           int path, int levels, cudaStream_t s);
 
+// Winograd levels over Z, one reduction at the end (winograd_z.cu)
+int64_t winograd_z_kmax(uint32_t p, int levels);
+ffgpu_status winograd_z_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
+                            int64_t lda, const uint32_t* B, int64_t ldb, uint32_t beta, uint32_t* C, int64_t ldc,
+                            int levels, cudaStream_t s);
+
 // multi-modular products from one exact integer product (multimod.cu)
 constexpr int kMaxFanoutPrimes = 64;
 // Per prime of a fan-out: p, R = 2^32 mod p and the Shoup quotients

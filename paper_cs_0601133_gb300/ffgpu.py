@@ -49,8 +49,8 @@ class KernelTime(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    _fields_ = [("path", ctypes.c_int32), ("winograd_levels", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("path", ctypes.c_int32), ("winograd_levels", ctypes.c_int32), ("unreduced", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 PATHS = {"rns": 0, "fp64": 1, "fp32": 2, "simt": 3}
@@ -140,6 +140,7 @@ SIGNATURES = {
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
     "ffgpu_set_small_threshold": [_I64],
+    "ffgpu_winograd_unreduced_kmax": [_U32, _I32, ctypes.POINTER(ctypes.c_int64)],
     "ffgpu_get_small_threshold": [],
     "ffgpu_lqup": [_I64, _I64, _U32, _VP, _I64, ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP],
     "ffgpu_rank": [_I64, _I64, _U32, _VP, _I64, ctypes.POINTER(ctypes.c_int64), _VP],
@@ -217,9 +218,11 @@ def fgemm_ptr(m, n, k, p, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, strea
 
 
 def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "rns",
-             winograd_levels: int = 0, stream=None):
+             winograd_levels: int = 0, stream=None, unreduced: bool = False):
     """fgemm through a chosen arithmetic path ("rns", "fp64", "fp32", "simt") with
-    `winograd_levels` levels of Winograd's variant. Returns C."""
+    `winograd_levels` levels of Winograd's variant; unreduced=True runs the
+    levels over Z with one reduction at the end (Theorem 3.1's admission).
+    Returns C."""
     import torch
     m, k = A.shape
     n = B.shape[1]
@@ -229,7 +232,7 @@ def fgemm_ex(A, B, p: int, alpha: int = 1, beta: int = 0, C=None, path: str = "r
     a, lda = _mat(A, "A")
     b, ldb = _mat(B, "B")
     c, ldc = _mat(C, "C")
-    opt = Options(PATHS[path], winograd_levels)
+    opt = Options(PATHS[path], winograd_levels, 1 if unreduced else 0)
     check(lib().ffgpu_fgemm_ex(m, n, k, p, alpha % 2**32, a, lda, b, ldb, beta % 2**32, c, ldc,
                                ctypes.byref(opt), _stream_ptr(stream)), "ffgpu_fgemm_ex")
     return C
@@ -368,6 +371,13 @@ def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: 
 def set_small_threshold(max_macs: int) -> None:
     """Products with m*n*k <= max_macs run on the CUDA cores (0: none)."""
     check(lib().ffgpu_set_small_threshold(max_macs), "ffgpu_set_small_threshold")
+
+
+def winograd_unreduced_kmax(p: int, levels: int) -> int:
+    """Largest k that `levels` unreduced Winograd levels admit for p (0: none)."""
+    out = ctypes.c_int64(0)
+    check(lib().ffgpu_winograd_unreduced_kmax(p, levels, ctypes.byref(out)), "ffgpu_winograd_unreduced_kmax")
+    return int(out.value)
 
 
 def get_small_threshold() -> int:
