@@ -292,6 +292,15 @@ def run_own(args):
                     "algorithmic": "2*m*n*k_padded*channels = %.4g tensor FLOP per launch (%d channels)"
                                    % (plan["mma_flops"], plan["channels"]),
                     "avg_launch_ms": gms / gl}
+        # the int8 reference point: tcgen05 has no int8 kind on sm_103a, so the
+        # GPU's int8 tensor rate is the warp-level mma.sync rate, measured now
+        try:
+            i8 = ff.peak_probe("int8", 100000) / 1e12
+            roofline["int8_mma_sync_peak_tops"] = i8
+            roofline["tensor_ops_over_int8_peak"] = achieved / i8 if i8 > 0 else None
+        except Exception as e:  # the probe is informational
+            roofline["int8_mma_sync_peak_tops"] = None
+            roofline["int8_probe_error"] = str(e)
 
     e2e = None
     if not args.no_e2e:

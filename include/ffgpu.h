@@ -519,6 +519,17 @@ FFGPU_API ffgpu_status ffgpu_profile_read(ffgpu_kernel_time* out, int cap, int* 
  */
 FFGPU_API ffgpu_status ffgpu_selftest_wait_timeout(int64_t limit_cycles, void* stream);
 
+/*
+ * Peak rate of a warp-level MMA unit, measured now on the current device:
+ * register-only mma.sync chains on every SM for `iters` iterations (1 .. 2^24),
+ * timed with CUDA events.  kind 0: int8 (m16n8k32, s8 x s8 -> s32), 1: bf16
+ * (m16n8k16 -> f32), 2: FP64 DMMA (m8n8k4).  *ops_per_second counts 2 M N K
+ * per MMA.  tcgen05 has no int8 kind on sm_103a, so kind 0 is this GPU's int8
+ * tensor rate, the reference point beside the bf16 tensor-core roofline.
+ * Synchronizes `stream`.  Not in the paper.
+ */
+FFGPU_API ffgpu_status ffgpu_peak_probe(int kind, int64_t iters, double* ops_per_second, void* stream);
+
 /* Frees every workspace pool of the calling process (synchronizes the device). */
 FFGPU_API ffgpu_status ffgpu_release_workspaces(void);
 

@@ -140,6 +140,7 @@ SIGNATURES = {
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
     "ffgpu_set_small_threshold": [_I64],
+    "ffgpu_peak_probe": [_I32, _I64, ctypes.POINTER(ctypes.c_double), _VP],
     "ffgpu_winograd_unreduced_kmax": [_U32, _I32, ctypes.POINTER(ctypes.c_int64)],
     "ffgpu_get_small_threshold": [],
     "ffgpu_lqup": [_I64, _I64, _U32, _VP, _I64, ctypes.POINTER(ctypes.c_int64), _VP, _VP, _VP],
@@ -371,6 +372,17 @@ def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: 
 def set_small_threshold(max_macs: int) -> None:
     """Products with m*n*k <= max_macs run on the CUDA cores (0: none)."""
     check(lib().ffgpu_set_small_threshold(max_macs), "ffgpu_set_small_threshold")
+
+
+PEAK_KINDS = {"int8": 0, "bf16": 1, "fp64": 2}
+
+
+def peak_probe(kind: str = "int8", iters: int = 100000, stream=None) -> float:
+    """Measured peak of a warp-level MMA unit (mma.sync), in operations/s."""
+    out = ctypes.c_double(0.0)
+    check(lib().ffgpu_peak_probe(PEAK_KINDS[kind], iters, ctypes.byref(out), _stream_ptr(stream)),
+          "ffgpu_peak_probe")
+    return float(out.value)
 
 
 def winograd_unreduced_kmax(p: int, levels: int) -> int:
