@@ -256,7 +256,7 @@ __device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, 
     return k;
 }
 
-__global__ void __launch_bounds__(kWinThreads) lqup_window_kernel(const uint32_t* __restrict__ A, long long lda,
+__global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint32_t* __restrict__ A, long long lda,
                                                                   int h, int W, int WS, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
@@ -283,9 +283,20 @@ __global__ void __launch_bounds__(kWinThreads) lqup_window_kernel(const uint32_t
     constexpr int nwarps = kWinThreads / 32;
     const uint32_t one = 1u % p;
 
-    for (int idx = tid; idx < h * WS; idx += blockDim.x) {
-        const int r = idx / WS, q = idx - r * WS;
-        T[idx] = q < W ? __ldg(A + (long long)r * lda + q) : 0u;
+    // eight independent loads in flight per thread before their stores
+    for (int base = 0; base < h * WS; base += 8 * blockDim.x) {
+        uint32_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x + tid;
+            const int r = idx / WS, q = idx - r * WS;
+            v[e] = (idx < h * WS && q < W) ? __ldg(A + (long long)r * lda + q) : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = base + e * blockDim.x + tid;
+            if (idx < h * WS) T[idx] = v[e];
+        }
     }
     for (int idx = tid; idx < h * h; idx += blockDim.x) {
         Lsm[idx] = 0u;
@@ -518,18 +529,40 @@ __global__ void __launch_bounds__(kThreads) lqup_rest_kernel(const uint32_t* __r
     if ((int)blockIdx.x < nleft) {
         const int col = blockIdx.x * blockDim.x + tid;
         if (col < c)
-            for (int i = 0; i < h; ++i) rows[(long long)i * ldr + col] = __ldg(A + (long long)s_newrow[i] * lda + col);
+            for (int i0 = 0; i0 < h; i0 += 16) {  // sixteen loads in flight before their stores
+                uint32_t v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    v[e] = i0 + e < h ? __ldg(A + (long long)s_newrow[i0 + e] * lda + col) : 0u;
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                    if (i0 + e < h) rows[(long long)(i0 + e) * ldr + col] = v[e];
+            }
         return;
     }
     const int q0 = c + W + (blockIdx.x - nleft) * kRestCols;
     const int nq = min(kRestCols, n - q0);
     uint32_t* R = sm;                   // [h][kRestCols]
     uint32_t* Es = R + h * kRestCols;   // [h][h]
-    for (int idx = tid; idx < h * kRestCols; idx += blockDim.x) {
-        const int i = idx / kRestCols, q = idx % kRestCols;
-        R[idx] = q < nq ? __ldg(A + (long long)i * lda + q0 + q) : 0u;
+    {
+        // every load of the thread in flight before the stores (h <= 64: at
+        // most 16 of R and 16 of E per thread)
+        constexpr int kPer = kLeafRows * kRestCols / kThreads;
+        uint32_t vr[kPer], ve[kPer];
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const int idx = e * kThreads + tid;
+            const int i = idx / kRestCols, q = idx % kRestCols;
+            vr[e] = (i < h && q < nq) ? __ldg(A + (long long)i * lda + q0 + q) : 0u;
+            ve[e] = idx < h * h ? __ldg(Eg + idx) : 0u;
+        }
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const int idx = e * kThreads + tid;
+            if (idx < h * kRestCols) R[idx] = vr[e];
+            if (idx < h * h) Es[idx] = ve[e];
+        }
     }
-    for (int idx = tid; idx < h * h; idx += blockDim.x) Es[idx] = __ldg(Eg + idx);
     __syncthreads();
     const int q = tid % kRestCols;
     for (int i = tid / kRestCols; i < h; i += kThreads / kRestCols) {

@@ -137,13 +137,13 @@ __global__ void __launch_bounds__(kSmThreads) small_reduce_kernel(int m, int n, 
 }
 
 // Number of k-splits for a product: enough CTAs for two waves, each split at
-// least four 32-long chunks (a shorter split does not pay for the reduction
-// launch), at most 16.
+// least one 32-long chunk, at most 16 (measured in LQUP: a rule of four
+// chunks per split, fewer reduction launches, was slower overall).
 int small_splits(int64_t m, int64_t n, int64_t k, int sms) {
     const int64_t tiles = ((m + kSmT - 1) / kSmT) * ((n + kSmT - 1) / kSmT);
     const int64_t chunks = (k + kSmK - 1) / kSmK;
     int s = 1;
-    while (s < 16 && tiles * s < 2 * (int64_t)sms && 8 * s <= chunks) s *= 2;
+    while (s < 16 && tiles * s < 2 * (int64_t)sms && 2 * s <= chunks) s *= 2;
     return s;
 }
 
