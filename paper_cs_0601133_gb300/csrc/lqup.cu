@@ -96,7 +96,9 @@ __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uns
 // t' below pivot k (row t, column j, scaled value P) becomes
 // P row_t' - a row_t with a its scaled entry in column j, and its scale d_t'
 // (the factor by which the stored row exceeds the true Schur complement) is
-// multiplied by P.  The rows live in registers (warp w holds rows w, w + 16,
+// multiplied by P (recovered afterwards from which steps touched the row).
+// The pivot row is published with the Shoup quotients of its values, so a
+// row's update needs no quotient of its own multiplier.  The rows live in registers (warp w holds rows w, w + 16,
 // w + 32, w + 48; lane l columns l, l + 32, ...); per row one barrier: the
 // pivot row and its pivot are published in shared memory, every warp updates
 // its rows below it, and the warp that owns the next row updates that row
@@ -132,9 +134,9 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&v)[NC], int c) {
 // pivot, in slot `slot`; the pivot becomes number kk.
 template <int NC>
 __device__ __forceinline__ void win_publish(const uint32_t (&vrow)[NC], int trow, int kk, int slot, uint32_t p,
-                                            unsigned long long mu, uint32_t* s_row, int* s_j, uint32_t* s_Pv,
-                                            uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P, int* s_colpiv,
-                                            int* s_rowpiv) {
+                                            unsigned long long mu, uint32_t* s_row, uint32_t* s_rowq, int* s_j,
+                                            uint32_t* s_Pv, uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P,
+                                            int* s_colpiv, int* s_rowpiv) {
     const int lane = threadIdx.x & 31;
     int j = -1;
 #pragma unroll
@@ -142,8 +144,13 @@ __device__ __forceinline__ void win_publish(const uint32_t (&vrow)[NC], int trow
         const unsigned bal = __ballot_sync(0xffffffffu, vrow[c] != 0u);
         if (j < 0 && bal) j = 32 * c + __ffs(bal) - 1;
     }
+    // the row's values and their Shoup quotients: every later row's update
+    // multiplies them by its own entry a, so no quotient of a is needed
 #pragma unroll
-    for (int c = 0; c < NC; ++c) s_row[slot * kMaxWin + lane + 32 * c] = vrow[c];
+    for (int c = 0; c < NC; ++c) {
+        s_row[slot * kMaxWin + lane + 32 * c] = vrow[c];
+        s_rowq[slot * kMaxWin + lane + 32 * c] = vrow[c] ? shoup_quot(vrow[c], p, mu) : 0u;
+    }
     const uint32_t P = __shfl_sync(0xffffffffu, pick<NC>(vrow, j >> 5), j & 31);
     if (lane == 0) {
         s_j[slot] = j;
@@ -161,15 +168,14 @@ __device__ __forceinline__ void win_publish(const uint32_t (&vrow)[NC], int trow
 
 // Row update: v <- P v - a u (mod p) with a = v[j].  Returns false if a = 0.
 template <int NC>
-__device__ __forceinline__ bool win_update(uint32_t (&v)[NC], const uint32_t (&u)[NC], int jc, int jl, uint32_t P,
-                                           uint32_t Ps, uint32_t p, unsigned long long mu, uint32_t& a_out) {
+__device__ __forceinline__ bool win_update(uint32_t (&v)[NC], const uint32_t (&u)[NC], const uint32_t (&uq)[NC],
+                                           int jc, int jl, uint32_t P, uint32_t Ps, uint32_t p, uint32_t& a_out) {
     const uint32_t a = __shfl_sync(0xffffffffu, pick<NC>(v, jc), jl);
     a_out = a;
     if (a == 0u) return false;
-    const uint32_t as = shoup_quot(a, p, mu);
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const uint32_t x = shoup_mul(v[c], P, Ps, p), y = shoup_mul(u[c], a, as, p);
+        const uint32_t x = shoup_mul(v[c], P, Ps, p), y = shoup_mul(a, u[c], uq[c], p);
         v[c] = x >= y ? x - y : x + (p - y);
     }
     return true;
@@ -177,18 +183,15 @@ __device__ __forceinline__ bool win_update(uint32_t (&v)[NC], const uint32_t (&u
 
 template <int NC>
 __device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, uint32_t p, unsigned long long mu,
-                                             uint32_t* Lsm, uint32_t* s_row, uint32_t* s_d, int* s_j, uint32_t* s_Pv,
-                                             uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P, int* s_colpiv,
-                                             int* s_rowpiv) {
+                                             uint32_t* Lsm, uint32_t* s_row, uint32_t* s_rowq, int* s_j,
+                                             uint32_t* s_Pv, uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P,
+                                             int* s_colpiv, int* s_rowpiv) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nw = kWinThreads / 32;
-    const uint32_t one = 1u % p;
     uint32_t v[kRowsPerWarp][NC];
-    uint32_t d[kRowsPerWarp];
 #pragma unroll
     for (int rr = 0; rr < kRowsPerWarp; ++rr) {
         const int tt = warp + nw * rr;
-        d[rr] = one;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const int q = lane + 32 * c;
@@ -196,7 +199,9 @@ __device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, 
         }
     }
     int k = 0;
-    if (warp == 0) win_publish<NC>(v[0], 0, 0, 0, p, mu, s_row, s_j, s_Pv, s_Ps, s_prow, s_pcol, s_P, s_colpiv, s_rowpiv);
+    if (warp == 0)
+        win_publish<NC>(v[0], 0, 0, 0, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol, s_P, s_colpiv,
+                        s_rowpiv);
     __syncthreads();
     for (int t = 0; t < h; ++t) {
         const int b = t & 1;
@@ -209,36 +214,33 @@ __device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, 
             uint32_t u[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) u[c] = s_row[b * kMaxWin + lane + 32 * c];
+            uint32_t uq[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) uq[c] = s_rowq[b * kMaxWin + lane + 32 * c];
             const int jc = j >> 5, jl = j & 31;
             // the next row first (its owner publishes it right after), then the others
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr) {
                 if (!(owner && rr == rn)) continue;
                 uint32_t a;
-                if (win_update<NC>(v[rr], u, jc, jl, P, Ps, p, mu, a)) {
-                    if (lane == 0) Lsm[tn * h + k] = a;
-                    d[rr] = mulm(d[rr], P, p, mu);
-                }
-                win_publish<NC>(v[rr], tn, k + 1, tn & 1, p, mu, s_row, s_j, s_Pv, s_Ps, s_prow, s_pcol, s_P,
-                                s_colpiv, s_rowpiv);
+                if (win_update<NC>(v[rr], u, uq, jc, jl, P, Ps, p, a) && lane == 0) Lsm[tn * h + k] = a;
+                win_publish<NC>(v[rr], tn, k + 1, tn & 1, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol,
+                                s_P, s_colpiv, s_rowpiv);
             }
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr) {
                 const int tt = warp + nw * rr;
                 if (tt <= tn || tt >= h) continue;  // warp-uniform
                 uint32_t a;
-                if (win_update<NC>(v[rr], u, jc, jl, P, Ps, p, mu, a)) {
-                    if (lane == 0) Lsm[tt * h + k] = a;
-                    d[rr] = mulm(d[rr], P, p, mu);
-                }
+                if (win_update<NC>(v[rr], u, uq, jc, jl, P, Ps, p, a) && lane == 0) Lsm[tt * h + k] = a;
             }
             ++k;
         } else if (owner) {
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr)
                 if (rr == rn)
-                    win_publish<NC>(v[rr], tn, k, tn & 1, p, mu, s_row, s_j, s_Pv, s_Ps, s_prow, s_pcol, s_P,
-                                    s_colpiv, s_rowpiv);
+                    win_publish<NC>(v[rr], tn, k, tn & 1, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol,
+                                    s_P, s_colpiv, s_rowpiv);
         }
         __syncthreads();
     }
@@ -251,7 +253,6 @@ __device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, 
             const int q = lane + 32 * c;
             if (q < WS) T[tt * WS + q] = v[rr][c];
         }
-        if (lane == 0) s_d[tt] = d[rr];
     }
     return k;
 }
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
     uint32_t* Ui = Nd + h * h;     // [h][h]: U11^{-1}
     uint32_t* TmE = Ui + h * h;          // [kTmWords]: doubling products (lower)
     uint32_t* TmU = TmE + kTmWords;      // [kTmWords]: doubling products (upper)
-    __shared__ uint32_t s_row[2 * kMaxWin];
+    __shared__ uint32_t s_row[2 * kMaxWin], s_rowq[2 * kMaxWin];
     __shared__ uint32_t s_d[kLeafRows], s_invd[kLeafRows];
     __shared__ uint32_t s_P[kLeafRows], s_invP[kLeafRows], s_c[kLeafRows];
     __shared__ int s_prow[kLeafRows], s_pcol[kLeafRows], s_pre[kLeafRows + 1];
@@ -309,10 +310,10 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
     for (int x = tid; x < kMaxWin; x += blockDim.x) s_colpiv[x] = -1;
     __syncthreads();
 
-    const int r = WS <= 96 ? win_eliminate<3>(T, WS, W, h, p, mu, Lsm, s_row, s_d, s_j, s_Pv, s_Ps, s_prow, s_pcol,
-                                              s_P, s_colpiv, s_rowpiv)
-                           : win_eliminate<8>(T, WS, W, h, p, mu, Lsm, s_row, s_d, s_j, s_Pv, s_Ps, s_prow, s_pcol,
-                                              s_P, s_colpiv, s_rowpiv);
+    const int r = WS <= 96 ? win_eliminate<3>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
+                                              s_pcol, s_P, s_colpiv, s_rowpiv)
+                           : win_eliminate<8>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
+                                              s_pcol, s_P, s_colpiv, s_rowpiv);
     __syncthreads();
 
     // 1 / P_k for every pivot: prefix and suffix products over warp 0 (two per lane), one inverse
@@ -343,6 +344,17 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
         int cnt = 0;
         for (int q = 0; q < r; ++q) cnt += s_prow[q] < x;
         s_pre[x] = cnt;
+    }
+    __syncthreads();
+    // scale of each row: the product of the pivots of the steps that touched it
+    // (those whose numerator is non-zero), one warp per row
+    for (int t = warp; t < h; t += nwarps) {
+        const int pre = s_pre[t];
+        const uint32_t g0 = lane < pre && Lsm[t * h + lane] ? s_P[lane] : one;
+        const uint32_t g1 = lane + 32 < pre && Lsm[t * h + lane + 32] ? s_P[lane + 32] : one;
+        uint32_t g = mulm(g0, g1, p, mu);
+        for (int o = 16; o > 0; o >>= 1) g = mulm(g, __shfl_xor_sync(0xffffffffu, g, o), p, mu);
+        if (lane == 0) s_d[t] = g;
     }
     __syncthreads();
     // c_k = d_{prow k} / P_k = 1 / (true pivot k)
