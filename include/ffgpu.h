@@ -279,7 +279,8 @@ FFGPU_API ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, i
  * host-synchronous: pivot decisions are read back as the recursion proceeds
  * (workspace from the stream's pool).  Errors: FFGPU_ERR_INVALID (shapes,
  * null pointers, m or n above 2^30), FFGPU_ERR_NOMEM, FFGPU_ERR_CUDA,
- * FFGPU_ERR_TIMEOUT (a product's bounded wait ran out).
+ * FFGPU_ERR_TIMEOUT (a product's bounded wait ran out); after an error other
+ * than an argument check, A, rowperm and colperm are unspecified.
  */
 FFGPU_API ffgpu_status ffgpu_lqup(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda, int64_t* rank,
                                   int32_t* rowperm, int32_t* colperm, void* stream);
