@@ -21,17 +21,20 @@ __device__ __forceinline__ uint32_t mod_u64(unsigned long long x, uint32_t p,
 }
 
 // a^{-1} mod p by the extended Euclidean algorithm (the classical
-// representation's division, section 2.1.1); 0 if a is not invertible.
+// representation's division, section 2.1.1); 0 if a is not invertible.  The
+// remainders stay below p < 2^32, so the quotients are 32-bit divisions; the
+// Bezout coefficients stay below p in magnitude (64-bit products only).
 __device__ __forceinline__ uint32_t inv_mod_dev(uint32_t a, uint32_t p) {
-    long long r0 = p, r1 = a % p, s0 = 0, s1 = 1;
+    uint32_t r0 = p, r1 = a % p;
+    long long s0 = 0, s1 = 1;
     while (r1 != 0) {
-        const long long q = r0 / r1;
-        long long t = r0 - q * r1;
+        const uint32_t q = r0 / r1;
+        const uint32_t t = r0 - q * r1;
         r0 = r1;
         r1 = t;
-        t = s0 - q * s1;
+        const long long u = s0 - (long long)q * s1;
         s0 = s1;
-        s1 = t;
+        s1 = u;
     }
     if (r0 != 1) return 0;
     if (s0 < 0) s0 += p;
