@@ -310,10 +310,12 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
     for (int x = tid; x < kMaxWin; x += blockDim.x) s_colpiv[x] = -1;
     __syncthreads();
 
-    const int r = WS <= 96 ? win_eliminate<3>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
-                                              s_pcol, s_P, s_colpiv, s_rowpiv)
-                           : win_eliminate<8>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
-                                              s_pcol, s_P, s_colpiv, s_rowpiv);
+    const int r = WS <= 64   ? win_eliminate<2>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
+                                                s_pcol, s_P, s_colpiv, s_rowpiv)
+                  : WS <= 96 ? win_eliminate<3>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
+                                                s_pcol, s_P, s_colpiv, s_rowpiv)
+                             : win_eliminate<8>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
+                                                s_pcol, s_P, s_colpiv, s_rowpiv);
     __syncthreads();
 
     // 1 / P_k for every pivot: prefix and suffix products over warp 0 (two per lane), one inverse
@@ -754,8 +756,9 @@ int64_t split_rows(int64_t h) {
 }
 
 // Window width: wide enough for a leaf's pivots plus the columns that small
-// fields skip (a zero Schur entry has probability 1/p).
-int window_for(uint32_t p) { return p > 64 ? kLeafRows + 32 : kMaxWin; }
+// fields skip (a zero Schur entry has probability 1/p: above 2^16 a 64-row
+// leaf meets one with probability below 10^-3, and then only splits).
+int window_for(uint32_t p) { return p > 65536 ? kLeafRows : p > 64 ? kLeafRows + 32 : kMaxWin; }
 
 struct Layout {
     size_t rows, e, usp, t1, g, info, words, rest;  // byte offsets; rest = products' workspace
