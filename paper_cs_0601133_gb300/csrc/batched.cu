@@ -405,16 +405,92 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_i
     return launch_wave(w, L, ws, ws + t0, errw, s, mc);
 }
 
-// Splits a batch into waves (bounded plane bytes, at most 0xFFFF inner lengths)
-// and single products (k = 0, k beyond one launch's capacity, huge m or n).
+// Small products of a batch: one grouped CUDA-core launch, one CTA per 64 x 64
+// output tile (the tensor-core route would spend a whole 128 x 256 tile and
+// its reconstruction on each).  Tables: the job records, then the tile -> job
+// map.
+constexpr int64_t kBatchSmallMacs = int64_t(1) << 23;  // measured best for the multi-modular batch (2^19 .. 2^24)
+
+struct SmallGroup {
+    std::vector<const ffgpu_fgemm_desc*> d;
+    int64_t tiles = 0;
+    size_t t_map = 0, bytes = 0;
+};
+
+void layout_small(SmallGroup& G) {
+    G.tiles = 0;
+    for (const ffgpu_fgemm_desc* d : G.d) G.tiles += small_tiles(d->m, d->n);
+    G.t_map = align_up(G.d.size() * sizeof(SmallJob), 256);
+    G.bytes = G.t_map + align_up(size_t(G.tiles) * sizeof(int), 256);
+}
+
+void fill_small(const SmallGroup& G, unsigned char* host) {
+    SmallJob* jobs = reinterpret_cast<SmallJob*>(host);
+    int* map = reinterpret_cast<int*>(host + G.t_map);
+    int64_t t = 0;
+    for (size_t j = 0; j < G.d.size(); ++j) {
+        small_job(jobs[j], *G.d[j], (int)t);
+        const int64_t nt = small_tiles(G.d[j]->m, G.d[j]->n);
+        for (int64_t q = 0; q < nt; ++q) map[t++] = (int)j;
+    }
+}
+
+ffgpu_status launch_small(const SmallGroup& G, const unsigned char* tabs, cudaStream_t s) {
+    if (G.tiles == 0) return FFGPU_OK;
+    return timed_launch("small_gemm_grouped", s, [&] {
+               return launch_small_grouped(reinterpret_cast<const SmallJob*>(tabs),
+                                           reinterpret_cast<const int*>(tabs + G.t_map), G.tiles, s);
+           }) == cudaSuccess
+               ? FFGPU_OK
+               : FFGPU_ERR_CUDA;
+}
+
+// Immediate execution: tables staged in pinned memory, copied into the
+// workspace (the caller's or the stream's pool) in stream order.
+ffgpu_status run_small(SmallGroup& G, cudaStream_t s, void* ws_in, size_t ws_bytes) {
+    if (G.d.empty()) return FFGPU_OK;
+    layout_small(G);
+    unsigned char* ws = nullptr;
+    if (ws_in) {
+        if (ws_bytes < G.bytes) return FFGPU_ERR_NOMEM;
+        ws = static_cast<unsigned char*>(ws_in);
+    } else {
+        Pool* pool = nullptr;
+        ffgpu_status st = pool_get(s, G.bytes, &pool);
+        if (st != FFGPU_OK) return st;
+        ws = static_cast<unsigned char*>(pool->ptr);
+    }
+    std::unique_lock<std::mutex> stage_lk(g_stage_mu);
+    int stage_idx = -1;
+    std::vector<unsigned char> fallback;
+    unsigned char* host = stage_get(G.bytes, &stage_idx);
+    if (!host) {
+        fallback.resize(G.bytes);
+        host = fallback.data();
+    }
+    fill_small(G, host);
+    if (cudaMemcpyAsync(ws, host, G.bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return FFGPU_ERR_CUDA;
+    if (stage_idx >= 0) stage_done(stage_idx, s);
+    stage_lk.unlock();
+    return launch_small(G, ws, s);
+}
+
+// Splits a batch into small products (CUDA cores, when `small` is given),
+// waves (bounded plane bytes, at most 0xFFFF inner lengths) and single
+// products (k = 0, k beyond one launch's capacity, huge m or n).
 void split_batch(int64_t count, const ffgpu_fgemm_desc* descs, std::vector<std::vector<BInst>>& waves,
-                 std::vector<const ffgpu_fgemm_desc*>& singles) {
+                 std::vector<const ffgpu_fgemm_desc*>& singles, SmallGroup* small = nullptr) {
     std::vector<BInst> wave;
     std::unordered_set<int64_t> wave_k;
     size_t wave_bytes = 0;
+    const int64_t small_limit = std::min<int64_t>(kBatchSmallMacs, small_threshold());
     for (int64_t i = 0; i < count; ++i) {
         const ffgpu_fgemm_desc& d = descs[i];
         if (d.m == 0 || d.n == 0) continue;
+        if (small && d.k > 0 && double(d.m) * double(d.n) * double(d.k) <= double(small_limit)) {
+            small->d.push_back(&d);
+            continue;
+        }
         RnsPlan pl;
         make_plan(d.p, d.k, pl);
         if (d.k == 0 || d.k > pl.k_slice) {
@@ -456,7 +532,10 @@ ffgpu_status batched_run(int64_t count, const ffgpu_fgemm_desc* descs, cudaStrea
     const int sms = sm_count(dev);
     std::vector<std::vector<BInst>> waves;
     std::vector<const ffgpu_fgemm_desc*> singles;
-    split_batch(count, descs, waves, singles);
+    SmallGroup small;
+    split_batch(count, descs, waves, singles, &small);
+    ffgpu_status st0 = run_small(small, s, nullptr, 0);
+    if (st0 != FFGPU_OK) return st0;
     for (auto& w : waves) {
         ffgpu_status st = run_wave(w, s, sms, nullptr, 0, nullptr);
         if (st != FFGPU_OK) return st;
@@ -481,7 +560,10 @@ ffgpu_status batched_run_ws(int64_t count, const ffgpu_fgemm_desc* descs, void* 
     const int sms = sm_count(dev);
     std::vector<std::vector<BInst>> waves;
     std::vector<const ffgpu_fgemm_desc*> singles;
-    split_batch(count, descs, waves, singles);
+    SmallGroup small;
+    split_batch(count, descs, waves, singles, &small);
+    ffgpu_status st0 = run_small(small, s, ws, ws_bytes);
+    if (st0 != FFGPU_OK) return st0;
     for (auto& w : waves) {
         ffgpu_status st = run_wave(w, s, sms, ws, ws_bytes, err);
         if (st != FFGPU_OK) return st;
@@ -546,8 +628,10 @@ ffgpu_status batched_multimod_run(int64_t count, const ffgpu_multimod_desc* md, 
 size_t batched_ws_bytes(int64_t count, const ffgpu_fgemm_desc* descs, int sms) {
     std::vector<std::vector<BInst>> waves;
     std::vector<const ffgpu_fgemm_desc*> singles;
-    split_batch(count, descs, waves, singles);
-    size_t need = 0;
+    SmallGroup small;
+    split_batch(count, descs, waves, singles, &small);
+    layout_small(small);
+    size_t need = small.d.empty() ? 0 : small.bytes;
     for (auto& w : waves) {
         WaveLayout L;
         layout_wave(w, sms, L, nullptr);
@@ -599,9 +683,13 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     const int sms = sm_count(P->dev);
     std::vector<std::vector<BInst>> waves;
     std::vector<const ffgpu_fgemm_desc*> singles;
-    split_batch(count, descs, waves, singles);
+    SmallGroup small;
+    split_batch(count, descs, waves, singles, &small);
+    layout_small(small);
     std::vector<WaveLayout> layouts(waves.size());
     std::vector<size_t> tab_off(waves.size());
+    const size_t small_off = 0;
+    if (!small.d.empty()) P->tab_bytes = align_up(small.bytes, 256);
     for (size_t i = 0; i < waves.size(); ++i) {
         layout_wave(waves[i], sms, layouts[i], nullptr);
         P->plane_bytes = std::max(P->plane_bytes, layouts[i].plane_bytes);
@@ -630,6 +718,7 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     std::vector<unsigned char> host(P->tab_bytes, 0);
     unsigned char* planes = static_cast<unsigned char*>(P->planes);
     unsigned char* tabs = static_cast<unsigned char*>(P->tabs);
+    if (!small.d.empty()) fill_small(small, host.data() + small_off);
     for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
         st = fill_wave_tables(waves[i], layouts[i], planes, host.data() + tab_off[i], nullptr);
     if (st == FFGPU_OK && P->tab_bytes > 0 &&
@@ -647,6 +736,7 @@ ffgpu_status batched_plan_create(int64_t count, const ffgpu_fgemm_desc* descs, B
     }
     g_capturing = true;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = FFGPU_ERR_CUDA;
+    if (st == FFGPU_OK && !small.d.empty()) st = launch_small(small, tabs + small_off, cs);
     for (size_t i = 0; i < waves.size() && st == FFGPU_OK; ++i)
         st = launch_wave(waves[i], layouts[i], planes, tabs + tab_off[i], P->err, cs, nullptr);
     for (size_t i = 0; i < singles.size() && st == FFGPU_OK; ++i) {

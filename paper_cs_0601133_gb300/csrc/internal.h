@@ -207,6 +207,19 @@ bool fgemm_small(int64_t m, int64_t n, int64_t k);
 void set_small_threshold(int64_t macs);
 int64_t small_threshold();
 size_t small_ws_bytes(int64_t m, int64_t n, int64_t k, int sms);
+// one small product of a grouped CUDA-core launch (batched fgemm)
+struct SmallJob {
+    const uint32_t* A;
+    const uint32_t* B;
+    uint32_t* C;
+    long long lda, ldb, ldc;
+    unsigned long long mu;
+    int m, n, k, tiles_n, tile0;
+    uint32_t p, alpha, beta, two64p;
+};
+void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0);
+int64_t small_tiles(int64_t m, int64_t n);
+cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, cudaStream_t s);
 // ws may be null (then no k-split); C may overlap A or B when the launch
 // splits k (partial sums first) or when n <= 64 (each CTA reads only the rows
 // it writes).

@@ -45,25 +45,22 @@ __device__ __forceinline__ uint32_t finish96(uint32_t lo, uint32_t mid, uint32_t
     return mod_u64(acc, p, mu);
 }
 
-// Split s = blockIdx.z sums k-range [s kps, (s + 1) kps); with part null it
-// finishes the outputs itself, else it stores its partial sums there
-// (uint4 per output: lo, mid, hi, 0; split-major, m x n each).
-__global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, int k, int kps,
-                                                                const uint32_t* __restrict__ A, long long lda,
-                                                                const uint32_t* __restrict__ B, long long ldb,
-                                                                uint32_t* C, long long ldc, uint4* __restrict__ part,
-                                                                uint32_t p, unsigned long long mu, uint32_t two64p,
-                                                                uint32_t alpha, uint32_t beta) {
+// One 64 x 64 output tile (rows row0.., columns col0..) over the k-range
+// [kbeg, kend): with part null it finishes the outputs itself, else it stores
+// its partial sums at part (uint4 per output: lo, mid, hi, 0; m x n).
+__device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int row0, int col0,
+                                           const uint32_t* __restrict__ A, long long lda,
+                                           const uint32_t* __restrict__ B, long long ldb, uint32_t* C, long long ldc,
+                                           uint4* __restrict__ part, uint32_t p, unsigned long long mu,
+                                           uint32_t two64p, uint32_t alpha, uint32_t beta) {
     __shared__ __align__(16) uint32_t As[kSmK][kSmT];  // As[kk][row]
     __shared__ __align__(16) uint32_t Bs[kSmK][kSmT];  // Bs[kk][col]
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int row0 = blockIdx.y * kSmT, col0 = blockIdx.x * kSmT;
     uint32_t lo[4][4], mid[4][4], hi[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) lo[i][j] = mid[i][j] = hi[i][j] = 0u;
-    const int kbeg = blockIdx.z * kps, kend = min(k, kbeg + kps);
     for (int k0 = kbeg; k0 < kend; k0 += kSmK) {
         {
             const int r = tid >> 2, kk0 = (tid & 3) * 8, gi = row0 + r;
@@ -103,13 +100,39 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
             const int gj = col0 + tx * 4 + j;
             if (gj >= n) continue;
             if (part) {
-                part[((long long)blockIdx.z * m + gi) * n + gj] = make_uint4(lo[i][j], mid[i][j], hi[i][j], 0u);
+                part[(long long)gi * n + gj] = make_uint4(lo[i][j], mid[i][j], hi[i][j], 0u);
             } else {
                 uint32_t* cp = C + (long long)gi * ldc + gj;
                 *cp = finish96(lo[i][j], mid[i][j], hi[i][j], beta ? *cp : 0u, p, mu, two64p, alpha, beta);
             }
         }
     }
+}
+
+// Split s = blockIdx.z sums k-range [s kps, (s + 1) kps); with part null it
+// finishes the outputs itself, else it stores its partial sums there
+// (split-major, m x n each).
+__global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, int k, int kps,
+                                                                const uint32_t* __restrict__ A, long long lda,
+                                                                const uint32_t* __restrict__ B, long long ldb,
+                                                                uint32_t* C, long long ldc, uint4* __restrict__ part,
+                                                                uint32_t p, unsigned long long mu, uint32_t two64p,
+                                                                uint32_t alpha, uint32_t beta) {
+    const int kbeg = blockIdx.z * kps, kend = min(k, kbeg + kps);
+    small_tile(m, n, kbeg, kend, blockIdx.y * kSmT, blockIdx.x * kSmT, A, lda, B, ldb, C, ldc,
+               part ? part + (long long)blockIdx.z * m * n : nullptr, p, mu, two64p, alpha, beta);
+}
+
+// Many independent small products in one launch: CTA t computes tile
+// t - jobs[j].tile0 of job j = tile_job[t] (row-major over the job's tiles).
+__global__ void __launch_bounds__(kSmThreads) small_grouped_kernel(const SmallJob* __restrict__ jobs,
+                                                                   const int* __restrict__ tile_job) {
+    const int t = blockIdx.x;
+    const SmallJob& J = jobs[tile_job[t]];
+    const int local = t - J.tile0;
+    const int tr = local / J.tiles_n, tc = local - tr * J.tiles_n;
+    small_tile(J.m, J.n, 0, J.k, tr * kSmT, tc * kSmT, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, nullptr, J.p, J.mu,
+               J.two64p, J.alpha, J.beta);
 }
 
 // Sum of the splits' partial sums (below k 2^64 < 2^96, so three words and
@@ -162,6 +185,34 @@ bool fgemm_small(int64_t m, int64_t n, int64_t k) {
     const double macs = double(m) * double(n) * double(k);
     return k > 0 && macs <= double(g_small_macs.load()) && k < (int64_t(1) << 31) &&
            m <= int64_t(65535) * kSmT;
+}
+
+void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0) {
+    J.A = d.A;
+    J.B = d.B;
+    J.C = d.C;
+    J.lda = d.lda;
+    J.ldb = d.ldb;
+    J.ldc = d.ldc;
+    J.mu = ~0ull / d.p;
+    J.m = (int)d.m;
+    J.n = (int)d.n;
+    J.k = (int)d.k;
+    J.tiles_n = (int)((d.n + kSmT - 1) / kSmT);
+    J.tile0 = tile0;
+    J.p = d.p;
+    J.alpha = d.alpha % d.p;
+    J.beta = d.beta % d.p;
+    J.two64p = (uint32_t)(((unsigned __int128)1 << 64) % d.p);
+}
+
+int64_t small_tiles(int64_t m, int64_t n) { return ((m + kSmT - 1) / kSmT) * ((n + kSmT - 1) / kSmT); }
+
+cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, cudaStream_t s) {
+    if (tiles == 0) return cudaSuccess;
+    if (tiles > INT32_MAX) return cudaErrorInvalidConfiguration;
+    small_grouped_kernel<<<(unsigned)tiles, kSmThreads, 0, s>>>(jobs, tile_job);
+    return cudaGetLastError();
 }
 
 size_t small_ws_bytes(int64_t m, int64_t n, int64_t k, int sms) {
