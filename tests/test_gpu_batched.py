@@ -1,6 +1,7 @@
-"""GPU parity of ffgpu_fgemm_batched (one grouped conversion per operand and one
-persistent grouped tensor-core launch per wave) against the CPU oracle, and
-against ffgpu_fgemm on the same descriptors.
+"""GPU parity of ffgpu_fgemm_batched (small products in one grouped CUDA-core
+launch; the others in one grouped conversion per operand and one persistent
+grouped tensor-core launch per wave) against the CPU oracle, and against
+ffgpu_fgemm on the same descriptors.
 
 Workloads follow the multi-modular configuration: uneven shapes drawn
 log-uniform in [16, 1024], integer matrices with entries in [-2^20, 2^20]
@@ -16,6 +17,18 @@ from paper_cs_0601133_gb300 import workloads as W
 from tests.gpu_util import from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True, params=["mixed", "tensor_only"])
+def routing(request):
+    """Each test twice: with the default routing (products of at most 2^23
+    multiply-adds in the grouped CUDA-core launch, the rest on the tensor
+    cores) and with every product on the tensor-core waves."""
+    old = ff.get_small_threshold()
+    if request.param == "tensor_only":
+        ff.set_small_threshold(0)
+    yield request.param
+    ff.set_small_threshold(old)
 
 
 def run_batch(problems):
