@@ -411,38 +411,58 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_i
 // map.
 constexpr int64_t kBatchSmallMacs = int64_t(1) << 23;  // measured best for the multi-modular batch (2^19 .. 2^24)
 
+// Two launches by tile size: products with a dimension of at most 32 on
+// 32 x 32 tiles (less padding), the others on 64 x 64 tiles.  Tables: per size
+// the job records, then the tile -> job map.
 struct SmallGroup {
     std::vector<const ffgpu_fgemm_desc*> d;
-    int64_t tiles = 0;
-    size_t t_map = 0, bytes = 0;
+    std::vector<const ffgpu_fgemm_desc*> by[2];  // [0]: 64 x 64 tiles, [1]: 32 x 32 tiles
+    int64_t tiles[2] = {0, 0};
+    size_t t_jobs[2] = {0, 0}, t_map[2] = {0, 0}, bytes = 0;
 };
 
+constexpr int kSmallTile[2] = {64, 32};
+
 void layout_small(SmallGroup& G) {
-    G.tiles = 0;
-    for (const ffgpu_fgemm_desc* d : G.d) G.tiles += small_tiles(d->m, d->n);
-    G.t_map = align_up(G.d.size() * sizeof(SmallJob), 256);
-    G.bytes = G.t_map + align_up(size_t(G.tiles) * sizeof(int), 256);
+    G.by[0].clear();
+    G.by[1].clear();
+    for (const ffgpu_fgemm_desc* d : G.d) G.by[std::min(d->m, d->n) <= 32 ? 1 : 0].push_back(d);
+    size_t off = 0;
+    for (int g = 0; g < 2; ++g) {
+        G.tiles[g] = 0;
+        for (const ffgpu_fgemm_desc* d : G.by[g]) G.tiles[g] += small_tiles(d->m, d->n, kSmallTile[g]);
+        G.t_jobs[g] = off;
+        off += align_up(G.by[g].size() * sizeof(SmallJob), 256);
+        G.t_map[g] = off;
+        off += align_up(size_t(G.tiles[g]) * sizeof(int), 256);
+    }
+    G.bytes = off;
 }
 
 void fill_small(const SmallGroup& G, unsigned char* host) {
-    SmallJob* jobs = reinterpret_cast<SmallJob*>(host);
-    int* map = reinterpret_cast<int*>(host + G.t_map);
-    int64_t t = 0;
-    for (size_t j = 0; j < G.d.size(); ++j) {
-        small_job(jobs[j], *G.d[j], (int)t);
-        const int64_t nt = small_tiles(G.d[j]->m, G.d[j]->n);
-        for (int64_t q = 0; q < nt; ++q) map[t++] = (int)j;
+    for (int g = 0; g < 2; ++g) {
+        SmallJob* jobs = reinterpret_cast<SmallJob*>(host + G.t_jobs[g]);
+        int* map = reinterpret_cast<int*>(host + G.t_map[g]);
+        int64_t t = 0;
+        for (size_t j = 0; j < G.by[g].size(); ++j) {
+            small_job(jobs[j], *G.by[g][j], (int)t, kSmallTile[g]);
+            const int64_t nt = small_tiles(G.by[g][j]->m, G.by[g][j]->n, kSmallTile[g]);
+            for (int64_t q = 0; q < nt; ++q) map[t++] = (int)j;
+        }
     }
 }
 
 ffgpu_status launch_small(const SmallGroup& G, const unsigned char* tabs, cudaStream_t s) {
-    if (G.tiles == 0) return FFGPU_OK;
-    return timed_launch("small_gemm_grouped", s, [&] {
-               return launch_small_grouped(reinterpret_cast<const SmallJob*>(tabs),
-                                           reinterpret_cast<const int*>(tabs + G.t_map), G.tiles, s);
-           }) == cudaSuccess
-               ? FFGPU_OK
-               : FFGPU_ERR_CUDA;
+    for (int g = 0; g < 2; ++g) {
+        if (G.tiles[g] == 0) continue;
+        if (timed_launch("small_gemm_grouped", s, [&] {
+                return launch_small_grouped(reinterpret_cast<const SmallJob*>(tabs + G.t_jobs[g]),
+                                            reinterpret_cast<const int*>(tabs + G.t_map[g]), G.tiles[g],
+                                            kSmallTile[g], s);
+            }) != cudaSuccess)
+            return FFGPU_ERR_CUDA;
+    }
+    return FFGPU_OK;
 }
 
 // Immediate execution: tables staged in pinned memory, copied into the

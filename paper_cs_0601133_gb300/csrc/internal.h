@@ -217,9 +217,9 @@ struct SmallJob {
     int m, n, k, tiles_n, tile0;
     uint32_t p, alpha, beta, two64p;
 };
-void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0);
-int64_t small_tiles(int64_t m, int64_t n);
-cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, cudaStream_t s);
+void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0, int tile);
+int64_t small_tiles(int64_t m, int64_t n, int tile);
+cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, int tile, cudaStream_t s);
 // ws may be null (then no k-split); C may overlap A or B when the launch
 // splits k (partial sums first) or when n <= 64 (each CTA reads only the rows
 // it writes).

@@ -9,7 +9,9 @@
 // mod p once, then alpha and beta applied (the delayed reduction of section
 // 3.1 taken to its limit: one reduction per output).  64 x 64 output tiles,
 // 256 threads with 4 x 4 outputs each, k staged through shared memory 32 at a
-// time.  When the tiles alone would not fill two waves of CTAs, k is split:
+// time (32 x 32 tiles with 64 threads for the batched launch's products with a
+// dimension of at most 32).  When the tiles alone would not fill two waves of
+// CTAs, k is split:
 // each split writes its exact 96-bit partial sums to the workspace and a
 // second kernel adds them, reduces mod p and applies alpha and beta (C is then
 // written only after every read of A and B).
@@ -45,17 +47,21 @@ __device__ __forceinline__ uint32_t finish96(uint32_t lo, uint32_t mid, uint32_t
     return mod_u64(acc, p, mu);
 }
 
-// One 64 x 64 output tile (rows row0.., columns col0..) over the k-range
-// [kbeg, kend): with part null it finishes the outputs itself, else it stores
-// its partial sums at part (uint4 per output: lo, mid, hi, 0; m x n).
+// One T x T output tile (rows row0.., columns col0..) over the k-range
+// [kbeg, kend), T * T / 16 threads with 4 x 4 outputs each: with part null
+// it finishes the outputs itself, else it stores its partial sums at part
+// (uint4 per output: lo, mid, hi, 0; m x n).
+template <int T>
 __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int row0, int col0,
                                            const uint32_t* __restrict__ A, long long lda,
                                            const uint32_t* __restrict__ B, long long ldb, uint32_t* C, long long ldc,
                                            uint4* __restrict__ part, uint32_t p, unsigned long long mu,
                                            uint32_t two64p, uint32_t alpha, uint32_t beta) {
-    __shared__ __align__(16) uint32_t As[kSmK][kSmT];  // As[kk][row]
-    __shared__ __align__(16) uint32_t Bs[kSmK][kSmT];  // Bs[kk][col]
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    constexpr int NT = T * T / 16;       // threads
+    constexpr int PER = T * kSmK / NT;   // staged words per thread and operand (8 for T = 64, 16 for T = 32)
+    __shared__ __align__(16) uint32_t As[kSmK][T];  // As[kk][row]
+    __shared__ __align__(16) uint32_t Bs[kSmK][T];  // Bs[kk][col]
+    const int tid = threadIdx.x, tx = tid % (T / 4), ty = tid / (T / 4);
     uint32_t lo[4][4], mid[4][4], hi[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -63,17 +69,18 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
         for (int j = 0; j < 4; ++j) lo[i][j] = mid[i][j] = hi[i][j] = 0u;
     for (int k0 = kbeg; k0 < kend; k0 += kSmK) {
         {
-            const int r = tid >> 2, kk0 = (tid & 3) * 8, gi = row0 + r;
+            // A: row r, k-run of PER words; B: k row kk, column run of PER words
+            const int r = tid / (kSmK / PER), kk0 = (tid % (kSmK / PER)) * PER, gi = row0 + r;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < PER; ++e) {
                 const int gk = k0 + kk0 + e;
                 As[kk0 + e][r] = (gi < m && gk < kend) ? __ldg(A + (long long)gi * lda + gk) : 0u;
             }
         }
         {
-            const int kk = tid >> 3, c0 = (tid & 7) * 8, gk = k0 + kk;
+            const int kk = tid / (T / PER), c0 = (tid % (T / PER)) * PER, gk = k0 + kk;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
+            for (int e = 0; e < PER; ++e) {
                 const int gj = col0 + c0 + e;
                 Bs[kk][c0 + e] = (gk < kend && gj < n) ? __ldg(B + (long long)gk * ldb + gj) : 0u;
             }
@@ -119,20 +126,22 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
                                                                 uint32_t p, unsigned long long mu, uint32_t two64p,
                                                                 uint32_t alpha, uint32_t beta) {
     const int kbeg = blockIdx.z * kps, kend = min(k, kbeg + kps);
-    small_tile(m, n, kbeg, kend, blockIdx.y * kSmT, blockIdx.x * kSmT, A, lda, B, ldb, C, ldc,
-               part ? part + (long long)blockIdx.z * m * n : nullptr, p, mu, two64p, alpha, beta);
+    small_tile<kSmT>(m, n, kbeg, kend, blockIdx.y * kSmT, blockIdx.x * kSmT, A, lda, B, ldb, C, ldc,
+                     part ? part + (long long)blockIdx.z * m * n : nullptr, p, mu, two64p, alpha, beta);
 }
 
 // Many independent small products in one launch: CTA t computes tile
-// t - jobs[j].tile0 of job j = tile_job[t] (row-major over the job's tiles).
-__global__ void __launch_bounds__(kSmThreads) small_grouped_kernel(const SmallJob* __restrict__ jobs,
+// t - jobs[j].tile0 of job j = tile_job[t] (row-major over the job's T x T
+// tiles).
+template <int T>
+__global__ void __launch_bounds__(T * T / 16) small_grouped_kernel(const SmallJob* __restrict__ jobs,
                                                                    const int* __restrict__ tile_job) {
     const int t = blockIdx.x;
     const SmallJob& J = jobs[tile_job[t]];
     const int local = t - J.tile0;
     const int tr = local / J.tiles_n, tc = local - tr * J.tiles_n;
-    small_tile(J.m, J.n, 0, J.k, tr * kSmT, tc * kSmT, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, nullptr, J.p, J.mu,
-               J.two64p, J.alpha, J.beta);
+    small_tile<T>(J.m, J.n, 0, J.k, tr * T, tc * T, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, nullptr, J.p, J.mu,
+                  J.two64p, J.alpha, J.beta);
 }
 
 // Sum of the splits' partial sums (below k 2^64 < 2^96, so three words and
@@ -187,7 +196,7 @@ bool fgemm_small(int64_t m, int64_t n, int64_t k) {
            m <= int64_t(65535) * kSmT;
 }
 
-void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0) {
+void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0, int tile) {
     J.A = d.A;
     J.B = d.B;
     J.C = d.C;
@@ -198,7 +207,7 @@ void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0) {
     J.m = (int)d.m;
     J.n = (int)d.n;
     J.k = (int)d.k;
-    J.tiles_n = (int)((d.n + kSmT - 1) / kSmT);
+    J.tiles_n = (int)((d.n + tile - 1) / tile);
     J.tile0 = tile0;
     J.p = d.p;
     J.alpha = d.alpha % d.p;
@@ -206,12 +215,16 @@ void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0) {
     J.two64p = (uint32_t)(((unsigned __int128)1 << 64) % d.p);
 }
 
-int64_t small_tiles(int64_t m, int64_t n) { return ((m + kSmT - 1) / kSmT) * ((n + kSmT - 1) / kSmT); }
+int64_t small_tiles(int64_t m, int64_t n, int tile) { return ((m + tile - 1) / tile) * ((n + tile - 1) / tile); }
 
-cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, cudaStream_t s) {
+// tile 64 (256 threads) or 32 (64 threads)
+cudaError_t launch_small_grouped(const SmallJob* jobs, const int* tile_job, int64_t tiles, int tile, cudaStream_t s) {
     if (tiles == 0) return cudaSuccess;
-    if (tiles > INT32_MAX) return cudaErrorInvalidConfiguration;
-    small_grouped_kernel<<<(unsigned)tiles, kSmThreads, 0, s>>>(jobs, tile_job);
+    if (tiles > INT32_MAX || (tile != 32 && tile != 64)) return cudaErrorInvalidConfiguration;
+    if (tile == 64)
+        small_grouped_kernel<64><<<(unsigned)tiles, 256, 0, s>>>(jobs, tile_job);
+    else
+        small_grouped_kernel<32><<<(unsigned)tiles, 64, 0, s>>>(jobs, tile_job);
     return cudaGetLastError();
 }
 
