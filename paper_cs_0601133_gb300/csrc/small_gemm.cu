@@ -168,14 +168,21 @@ __global__ void __launch_bounds__(kSmThreads) small_reduce_kernel(int m, int n, 
     }
 }
 
-// Number of k-splits for a product: enough CTAs for two waves, each split at
-// least one 32-long chunk, at most 16 (measured in LQUP: a rule of four
-// chunks per split, fewer reduction launches, was slower overall).
+// Number of k-splits for a product (at most 16, each at least one 32-long
+// chunk).  A split costs the partial sums' round trip and a second launch, so
+// k is split only while the CTAs still fit one per SM, and past half the SMs
+// only when every split keeps at least two chunks.  Measured per product on
+// one GPU (us, 256 threads; s = splits): 64x4096x64 s1 14.4 / s2 16.4,
+// 64x2048x64 16.4 / 14.3, 128x2048x128 s1 22.6 / s2 20.5, 128x4096x128
+// 22.6 / 29.7, 128x8192x128 36.9 / 52.1, 256^3 s1 38.9 / s4 16.5 / s8 15.4,
+// 512^3 s1 69.7 / s2 43.0 / s4 41.0, 64x64x2048 s1 253 / s16 26.7; the rule
+// this replaced (split until two waves of CTAs) took the slower choice for
+// every product of 64 to 256 tiles.
 int small_splits(int64_t m, int64_t n, int64_t k, int sms) {
     const int64_t tiles = ((m + kSmT - 1) / kSmT) * ((n + kSmT - 1) / kSmT);
     const int64_t chunks = (k + kSmK - 1) / kSmK;
     int s = 1;
-    while (s < 16 && tiles * s < 2 * (int64_t)sms && 2 * s <= chunks) s *= 2;
+    while (s < 16 && 2 * s <= chunks && tiles * 2 * s <= sms && (tiles * 4 * s <= sms || 4 * s <= chunks)) s *= 2;
     return s;
 }
 

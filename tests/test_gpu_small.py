@@ -2,7 +2,8 @@
 products (exact 96-bit integer dot products, one reduction per output).
 
 Against the oracle: ragged shapes across the 64 x 64 output tiles and the
-32-long k chunks, raw 32-bit words (products up to 2^64, sums up to 2^64 k),
+32-long k chunks (k split into 2 to 16 parts, and unsplit over several
+chunks), raw 32-bit words (products up to 2^64, sums up to 2^64 k),
 padded leading dimensions, alpha and beta, the all-(p-1) closed form with a
 long inner dimension.  The dispatch itself: below the threshold the kernel
 runs and no tensor-core product does, at threshold 0 the reverse."""
@@ -30,7 +31,7 @@ def run(A, B, C, p, alpha, beta, pad=0):
 
 @pytest.mark.parametrize("p", PRIMES)
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (64, 64, 64), (65, 63, 33), (130, 200, 97), (7, 300, 1000),
-                                   (300, 5, 31), (33, 65, 2049)])
+                                   (300, 5, 31), (33, 65, 2049), (600, 1100, 77)])
 def test_against_oracle(p, m, n, k):
     rng = W.rng_for("square", p % 99991, m, n, k)
     A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
