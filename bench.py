@@ -388,15 +388,25 @@ def run_e2e(args, ff, torch, dev, stream, A, B, C, alpha, beta, world):
 def run_serve_small():
     """Serving mix (Poisson arrivals of fgemm / unit-lower ftrsm, n log-uniform in
     [64, 4096], p from the four sweep primes, 40 GB budget): 400 requests at 0.8 of
-    the unbatched capacity, continuous batching (4 streams) vs the unbatched FIFO."""
+    the unbatched capacity, continuous batching (4 streams) vs the unbatched FIFO;
+    medians over three replays."""
+    import statistics
     from paper_cs_0601133_gb300 import serving
-    r = serving.serve_benchmark(n_requests=400, fracs=(0.8,), streams=4)
-    run = r["runs"][0]
+    # the mix is heavy-tailed (a few n = 4096 requests carry most of the work),
+    # so one replay's p99 swings with the timing of their bursts: three
+    # replays of the same seeded mix, the median of each figure reported
+    reps = [serving.serve_benchmark(n_requests=400, fracs=(0.8,), streams=4) for _ in range(3)]
+    runs = [r["runs"][0] for r in reps]
     keep = ("throughput_rps", "p50_ms", "p99_ms", "mean_ms", "failed", "peak_inflight")
-    return {"requests": 400, "load": run["load"], "rate_rps": run["rate_rps"],
-            "capacity_rps_unbatched": r["capacity_rps_unbatched"],
-            "batched": {k: run["batched"][k] for k in keep},
-            "unbatched": {k: run["unbatched"][k] for k in keep}}
+
+    def med(mode):
+        out = {k: statistics.median(run[mode][k] for run in runs) for k in keep}
+        out["p99_ms_each"] = [run[mode]["p99_ms"] for run in runs]
+        return out
+    return {"requests": 400, "replays": 3, "load": runs[0]["load"],
+            "rate_rps": statistics.median(run["rate_rps"] for run in runs),
+            "capacity_rps_unbatched": statistics.median(r["capacity_rps_unbatched"] for r in reps),
+            "batched": med("batched"), "unbatched": med("unbatched")}
 
 
 def time_call(fn, torch, steps, warmup):
