@@ -10,11 +10,11 @@
 // 3.1 taken to its limit: one reduction per output).  64 x 64 output tiles,
 // 256 threads with 4 x 4 outputs each, k staged through shared memory 32 at a
 // time (32 x 32 tiles with 64 threads for the batched launch's products with a
-// dimension of at most 32).  When the tiles alone would not fill two waves of
-// CTAs, k is split:
-// each split writes its exact 96-bit partial sums to the workspace and a
-// second kernel adds them, reduces mod p and applies alpha and beta (C is then
-// written only after every read of A and B).
+// dimension of at most 32).  When the tiles leave SMs idle, k is split (the
+// rule and its measurements are at small_splits): each split writes its exact
+// 96-bit partial sums to the workspace and a second kernel adds them, reduces
+// mod p and applies alpha and beta (C is then written only after every read
+// of A and B).
 #include <algorithm>
 #include <atomic>
 
