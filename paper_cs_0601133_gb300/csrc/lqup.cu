@@ -41,6 +41,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <vector>
 
@@ -763,6 +764,7 @@ int window_for(uint32_t p) { return p > 65536 ? kLeafRows : p > 64 ? kLeafRows +
 struct Layout {
     size_t rows, e, usp, t1, g, info, words, rest;  // byte offsets; rest = products' workspace
     size_t prod;                             // bytes the products need
+    size_t side;                             // the look-ahead products' workspace (prod bytes)
 };
 
 // Products of the recursion with the top half at full rank and the whole
@@ -795,6 +797,7 @@ Layout layout(int64_t m, int64_t n, uint32_t p, int sms) {
     Y.rest = Y.words + 256;
     Y.prod = 0;
     products_bound(m, n, p, sms, Y.prod);
+    Y.side = Y.rest + align256(Y.prod);
     return Y;
 }
 
@@ -819,7 +822,52 @@ struct Ctx {
     cudaStream_t s;
     int win;
     int* host;
+    int sms;
+    // look-ahead (null s2: off): the update of a bottom half's rows below its
+    // first leaf runs on s2, with its own workspace, while that leaf is
+    // factored; pending until the main stream has waited for ev_done
+    cudaStream_t s2;
+    cudaEvent_t ev_go, ev_done;
+    void* ws2;
+    size_t ws2_bytes;
+    mutable bool pending;
 };
+
+// The main stream waits for the pending side-stream update (a no-op when
+// none is pending).  Called before any launch that may touch rows other than
+// the current leaf's.
+ffgpu_status join(const Ctx& x) {
+    if (!x.pending) return FFGPU_OK;
+    x.pending = false;
+    return cudaStreamWaitEvent(x.s, x.ev_done, 0) == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA;
+}
+
+// One side stream and two events per host thread and device, created on
+// first use and kept for the thread's lifetime.
+struct SideRes {
+    cudaStream_t s = nullptr;
+    cudaEvent_t go = nullptr, done = nullptr;
+};
+
+const SideRes* side_resources() {
+    thread_local std::map<int, SideRes> all;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    SideRes& r = all[dev];
+    if (!r.s) {
+        SideRes t;
+        if (cudaStreamCreateWithFlags(&t.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t.go, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess) {
+            if (t.done) cudaEventDestroy(t.done);
+            if (t.go) cudaEventDestroy(t.go);
+            if (t.s) cudaStreamDestroy(t.s);
+            return nullptr;
+        }
+        r = t;
+    }
+    return &r;
+}
 
 ffgpu_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA; }
 
@@ -853,6 +901,15 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
         return cudaGetLastError();
     }));
     if (st != FFGPU_OK) return st;
+    // The window's outcome first: with every row a pivot no residual can be
+    // non-zero, so the rest of the leaf needs no second round trip.  (A
+    // pending side-stream update runs meanwhile: the window kernel reads and
+    // writes only this leaf's rows and the leaf's scratch.)
+    if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) != FFGPU_OK)
+        return st;
+    if ((st = cuda_ok(cudaStreamSynchronize(x.s))) != FFGPU_OK) return st;
+    const int r = x.host[0];
+    if ((st = join(x)) != FFGPU_OK) return st;
     const int nleft = (int)((c + kThreads - 1) / kThreads);
     const int nright = w > W ? (int)((w - W + kRestCols - 1) / kRestCols) : 0;
     if (nleft + nright > 0) {
@@ -863,10 +920,17 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
         }));
         if (st != FFGPU_OK) return st;
     }
-    if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) != FFGPU_OK)
-        return st;
-    if ((st = cuda_ok(cudaStreamSynchronize(x.s))) != FFGPU_OK) return st;
-    const int r = x.host[0], fail = x.host[1], ident = x.host[2], firstnz = x.host[3];
+    int fail = 0, ident = x.host[2], firstnz = INT_MAX;
+    if (r < h && nright > 0) {
+        // non-pivot rows: their residuals beyond the window decide
+        if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) !=
+            FFGPU_OK)
+            return st;
+        if ((st = cuda_ok(cudaStreamSynchronize(x.s))) != FFGPU_OK) return st;
+        fail = x.host[1];
+        ident = x.host[2];
+        firstnz = x.host[3];
+    }
     if (fail) {
         if (h > 1) {
             *ok = false;
@@ -946,9 +1010,8 @@ ffgpu_status rec(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank, 
     uint32_t* Ua = Uo ? Uo : x.Usp;
     const int64_t lda_u = Uo ? ldu : std::min(h1, x.n - c);  // r1 <= min(h1, n - c)
     if ((st = rec(x, rb, h1, c, &r1, Ua, lda_u)) != FFGPU_OK) return st;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const int sms = sm_count(dev);
+    if ((st = join(x)) != FFGPU_OK) return st;
+    const int sms = x.sms;
     auto product = [&](int64_t m, int64_t n, int64_t k, uint32_t alpha, const uint32_t* Ap, int64_t la,
                        const uint32_t* Bp, int64_t lb, uint32_t beta, uint32_t* Cp, int64_t lc) -> ffgpu_status {
         if (m == 0 || n == 0 || k == 0) return FFGPU_OK;
@@ -972,12 +1035,33 @@ ffgpu_status rec(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank, 
                 return FFGPU_ERR_CUDA;
         }
         // Z <- Z - G Y
-        if (c + r1 < x.n &&
-            (st = product(h2, x.n - c - r1, r1, x.p - 1, bot, x.lda, top + r1, x.lda, 1, bot + r1, x.lda)) != FFGPU_OK)
+        const int64_t w = x.n - c - r1;
+        const int64_t wz = std::min<int64_t>(w, x.win);  // the bottom half's first window
+        if (w > wz && x.s2 && h2 > kLeafRows && !fgemm_small(h2, w - wz, r1) &&
+            fgemm_ws_bytes(h2, w - wz, r1, x.p, sms) <= x.ws2_bytes) {
+            // look-ahead: the columns of the bottom half's first window here,
+            // the others on the side stream, on all but two SMs, while that
+            // window is factored on one of the two (its kernel touches only
+            // the first leaf's rows on those columns; every later launch
+            // joins the side stream first).  A product on the CUDA-core
+            // route would take every SM, so it stays on this stream.
+            if ((st = product(h2, wz, r1, x.p - 1, bot, x.lda, top + r1, x.lda, 1, bot + r1, x.lda)) != FFGPU_OK)
+                return st;
+            if (cudaEventRecord(x.ev_go, x.s) != cudaSuccess || cudaStreamWaitEvent(x.s2, x.ev_go, 0) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+            if ((st = fgemm_run(h2, w - wz, r1, x.p, x.p - 1, bot, x.lda, top + r1 + wz, x.lda, 1, bot + r1 + wz,
+                                x.lda, x.ws2, x.ws2_bytes, x.err, x.s2, std::max(2, sms - 2), false)) != FFGPU_OK)
+                return st;
+            if (cudaEventRecord(x.ev_done, x.s2) != cudaSuccess) return FFGPU_ERR_CUDA;
+            x.pending = true;
+        } else if (w > 0 &&
+                   (st = product(h2, w, r1, x.p - 1, bot, x.lda, top + r1, x.lda, 1, bot + r1, x.lda)) != FFGPU_OK) {
             return st;
+        }
     }
     uint32_t* Ub = Uo ? Uo + r1 * ldu + r1 : nullptr;
     if ((st = rec(x, rb + h1, h2, c + r1, &r2, Ub, ldu)) != FFGPU_OK) return st;
+    if ((st = join(x)) != FFGPU_OK) return st;
     if (r2 > 0 && h1 > r1) {
         // [top non-pivot rows | bottom pivot rows] -> [bottom pivot rows | top non-pivot rows]
         if ((st = reverse_rows(x, rb + r1, rb + h1)) != FFGPU_OK) return st;
@@ -1035,7 +1119,7 @@ bool is_prime_u32(uint32_t n) {
 
 size_t lqup_ws_bytes(int64_t m, int64_t n, uint32_t p, int sms) {
     const Layout Y = layout(m, n, p, sms);
-    return Y.rest + align256(Y.prod);
+    return Y.side + align256(Y.prod);
 }
 
 // In-place LQUP of the m x n matrix A (entries reduced mod p first).
@@ -1044,7 +1128,8 @@ ffgpu_status lqup_run(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda
                       int32_t* colperm, void* ws, size_t ws_bytes, int* err, cudaStream_t s) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const Layout Y = layout(m, n, p, sm_count(dev));
+    const int sms = sm_count(dev);
+    const Layout Y = layout(m, n, p, sms);
     if (ws_bytes < Y.rest) return FFGPU_ERR_NOMEM;
     ffgpu_status st = set_attrs();
     if (st != FFGPU_OK) return st;
@@ -1065,13 +1150,30 @@ ffgpu_status lqup_run(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda
     x.T1 = reinterpret_cast<uint32_t*>(w + Y.t1);
     x.G = reinterpret_cast<uint32_t*>(w + Y.g);
     x.info = reinterpret_cast<LeafInfo*>(w + Y.info);
-    x.ws = w + Y.rest;
-    x.ws_bytes = ws_bytes - Y.rest;
     x.err = err;
     x.s = s;
     x.win = window_for(p);
     x.host = pinned_words();
     if (!x.host) return FFGPU_ERR_NOMEM;
+    x.sms = sms;
+    x.pending = false;
+    x.s2 = nullptr;
+    x.ev_go = x.ev_done = nullptr;
+    x.ws2 = nullptr;
+    x.ws2_bytes = 0;
+    const SideRes* sr = ws_bytes >= Y.side + align256(Y.prod) ? side_resources() : nullptr;
+    if (sr) {
+        x.ws = w + Y.rest;
+        x.ws_bytes = Y.side - Y.rest;
+        x.s2 = sr->s;
+        x.ev_go = sr->go;
+        x.ev_done = sr->done;
+        x.ws2 = w + Y.side;
+        x.ws2_bytes = ws_bytes - Y.side;
+    } else {
+        x.ws = w + Y.rest;
+        x.ws_bytes = ws_bytes - Y.rest;
+    }
     if (m > 0)
         iota_kernel<<<grid_rows((m + 255) / 256), 256, 0, s>>>(rowperm, (int)m);
     if (n > 0)
@@ -1083,7 +1185,14 @@ ffgpu_status lqup_run(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda
             return FFGPU_ERR_CUDA;
     }
     int64_t r = 0;
-    if ((st = rec(x, 0, m, 0, &r, nullptr, 0)) != FFGPU_OK) return st;
+    st = rec(x, 0, m, 0, &r, nullptr, 0);
+    if (x.pending) {
+        // an error left the side stream's update in flight: let it finish
+        // before the workspace is handed back
+        cudaStreamSynchronize(x.s2);
+        x.pending = false;
+    }
+    if (st != FFGPU_OK) return st;
     if ((st = cuda_ok(cudaMemcpyAsync(x.host, err, sizeof(int), cudaMemcpyDeviceToHost, s))) != FFGPU_OK) return st;
     if ((st = cuda_ok(cudaStreamSynchronize(s))) != FFGPU_OK) return st;
     if (x.host[0] != 0) return FFGPU_ERR_TIMEOUT;
