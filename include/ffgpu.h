@@ -277,7 +277,9 @@ FFGPU_API ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, i
  * A: device, row-major, lda >= n, entries any uint32 (taken mod p).  p must
  * be a prime in [2, 2^31 - 1], else FFGPU_ERR_UNSUPPORTED_P.  The call is
  * host-synchronous: pivot decisions are read back as the recursion proceeds
- * (workspace from the stream's pool).  Errors: FFGPU_ERR_INVALID (shapes,
+ * (workspace from the stream's pool).  Part of some updates runs on a
+ * library-owned side stream of the calling thread; the call returns only
+ * after that stream's work is done.  Errors: FFGPU_ERR_INVALID (shapes,
  * null pointers, m or n above 2^30), FFGPU_ERR_NOMEM, FFGPU_ERR_CUDA,
  * FFGPU_ERR_TIMEOUT (a product's bounded wait ran out); after an error other
  * than an argument check, A, rowperm and colperm are unspecified.
