@@ -158,8 +158,13 @@ def cpu_baseline(A, B, C, p, alpha, beta, target_s=12.0):
     ncols = B.shape[1]
     rows = 4
     t = oracle_sample(A, B, C, p, alpha, beta, rows)
-    rows = int(max(4, min(n, rows * target_s / max(t, 1e-3))))
-    t = oracle_sample(A, B, C, p, alpha, beta, rows)
+    # a small sample's time is mostly fixed costs: scale the rows until the
+    # sample itself takes about target_s
+    for _ in range(3):
+        if t >= 0.7 * target_s or rows >= n:
+            break
+        rows = int(max(4, min(n, rows * target_s / max(t, 1e-3))))
+        t = oracle_sample(A, B, C, p, alpha, beta, rows)
     gops = 2.0 * rows * ncols * k / t / 1e9
     return {"value": gops, "unit": "GOPS", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d of %d rows of C (full k=%d, n=%d), %.1f s" % (rows, n, k, ncols, t)}
