@@ -38,6 +38,13 @@
 // single row whose window is zero takes its pivot from the first non-zero
 // column the check found.  The host reads every leaf's outcome (rank, commit
 // or split) before it issues the next step: the calls are host-synchronous.
+//
+// Look-ahead.  Where a node's update Z <- Z - G Y takes the tensor-core route
+// and its bottom half has more than one leaf, the columns of the bottom
+// half's first window are updated first on the caller's stream and the
+// others on a side stream (its own workspace, all but two SMs), so that the
+// first leaf's window kernel runs while the rest of the update does; every
+// later launch makes the caller's stream wait for the side stream first.
 #include <algorithm>
 #include <climits>
 #include <cstring>
