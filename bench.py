@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--lqup-n", type=int, default=0,
                     help="--workload lqup: only this n (with --p), uniform matrix")
     ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve", "ftrsm", "batched", "multimod",
-                                           "lqup"],
+                                           "lqup", "cpu"],
                     default="headline",
                     help="headline: the driver's line; the others print one line per configuration point")
     return ap.parse_args()
@@ -670,6 +670,99 @@ def run_multimod(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# CPU baselines on the host cores (--workload cpu): the oracle, and the paper's
+# own design restated on the CPU for comparison
+# ---------------------------------------------------------------------------
+CPU_SIZES = (512, 2048, 4096, 8192)
+CPU_PRIMES = (251, 65521, 8388593, 2147483647)
+
+
+def paper_method_kblk(p):
+    """Eq. (1) with gamma = 53 on positive residues: the largest lambda with
+    lambda (p-1)^2 < 2^53 (0: no product fits a double exactly)."""
+    return ((1 << 53) - 1) // ((p - 1) ** 2) if p > 2 else (1 << 53) - 1
+
+
+def paper_method_fgemm(A, B, C, p, alpha, beta):
+    """The paper's CPU design (sections 2.1.2 and 3.1) restated with torch's
+    float64 matmul: residues in [0, p) carried as doubles, products summed by
+    the BLAS over blocks of at most lambda = paper_method_kblk(p) terms, one
+    fmod per block; alpha and beta applied in int64.  None where eq. (1)
+    admits no block (p - 1 >= 2^26.5)."""
+    import torch
+    kb = paper_method_kblk(p)
+    if kb < 1:
+        return None
+    Af = torch.from_numpy((A % p).astype(np.float64))
+    Bf = torch.from_numpy((B % p).astype(np.float64))
+    k = Af.shape[1]
+    acc = None
+    for k0 in range(0, max(k, 1), kb):
+        part = torch.fmod(Af[:, k0:k0 + kb] @ Bf[k0:k0 + kb, :], float(p))
+        acc = part if acc is None else torch.fmod(acc + part, float(p))
+    r = acc.to(torch.int64)
+    out = (int(alpha) % p * r + int(beta) % p * torch.from_numpy((C % p).astype(np.int64))) % p
+    return out.numpy().astype(np.uint32)
+
+
+def run_cpu(args):
+    """Host-core timings: the oracle at n in CPU_SIZES for the CPU_PRIMES on all
+    cores and on one (a child process with OMP_NUM_THREADS=1), and the
+    paper-method baseline (float64 BLAS with eq. (1)'s blocking) where eq. (1)
+    admits it, each checked against the oracle on sampled rows.  Large cases
+    are timed on a bounded sample of rows (stated in each line)."""
+    import torch
+    import oracle
+    from paper_cs_0601133_gb300 import workloads as W
+    child = os.environ.get("FFGPU_CPU_CHILD") == "1"
+    if child:
+        torch.set_num_threads(1)
+    threads = oracle.num_threads()
+    target = 3.0 if child else 2.0
+
+    def timed(fn, rows, n):
+        t0 = time.perf_counter()
+        fn(rows)
+        return time.perf_counter() - t0
+
+    def scaled(fn, n):
+        rows = min(n, 8)
+        t = timed(fn, rows, n)
+        for _ in range(3):
+            if t >= 0.7 * target or rows >= n:
+                break
+            rows = int(max(1, min(n, rows * target / max(t, 1e-4))))
+            t = timed(fn, rows, n)
+        return rows, t
+
+    for n in CPU_SIZES:
+        for p in CPU_PRIMES:
+            A, B, C, alpha, beta = W.square_problem(n, p)
+            rows, t = scaled(lambda r: oracle.fgemm(A[:r], B, p, alpha, beta, C[:r]), n)
+            print(json.dumps({"workload": "cpu", "impl": "oracle", "n": n, "p": p, "threads": threads,
+                              "GOPS": 2.0 * rows * n * n / t / 1e9,
+                              "sample": "%d of %d rows of C, %.2f s" % (rows, n, t)}), flush=True)
+            if paper_method_kblk(p) < 1:
+                print(json.dumps({"workload": "cpu", "impl": "paper_method", "n": n, "p": p,
+                                  "threads": torch.get_num_threads(),
+                                  "unavailable": "eq. (1) with gamma = 53 admits no product: (p-1)^2 >= 2^53"}),
+                      flush=True)
+                continue
+            rows, t = scaled(lambda r: paper_method_fgemm(A[:r], B, C[:r], p, alpha, beta), n)
+            chk = min(rows, 4)
+            exact = bool(np.array_equal(paper_method_fgemm(A[:chk], B, C[:chk], p, alpha, beta),
+                                        oracle.fgemm(A[:chk], B, p, alpha, beta, C[:chk])))
+            print(json.dumps({"workload": "cpu", "impl": "paper_method", "n": n, "p": p,
+                              "threads": torch.get_num_threads(), "k_block": min(n, paper_method_kblk(p)),
+                              "GOPS": 2.0 * rows * n * n / t / 1e9, "exact_vs_oracle_rows": [chk, exact],
+                              "sample": "%d of %d rows of C, %.2f s" % (rows, n, t)}), flush=True)
+    if not child:
+        env = dict(os.environ, FFGPU_CPU_CHILD="1", OMP_NUM_THREADS="1")
+        return subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "cpu"], env=env).returncode
+    return 0
+
+
 def run_serve_full(args):
     from paper_cs_0601133_gb300 import serving
     r = serving.serve_benchmark(n_requests=2000, fracs=(0.5, 0.8, 0.95), streams=4)
@@ -695,6 +788,8 @@ def main():
         return run_batched(args)
     if args.workload == "multimod":
         return run_multimod(args)
+    if args.workload == "cpu":
+        return run_cpu(args)
     return run_own(args)
 
 
