@@ -166,6 +166,23 @@ def test_full_size_8192_sampled(p):
     assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
 
 
+@pytest.mark.parametrize("p", [251, 2147483647])
+def test_full_size_16384_sampled(p):
+    """The sweep's largest order (n = 16384, 1 GiB per matrix): sampled
+    entries recomputed by the oracle (random ones, and runs along the last
+    row and the last column), and Freivalds' test on the whole C."""
+    n = 16384
+    A, B, C, alpha, beta = W.square_problem(n, p)
+    got = run(A, B, C, p, alpha, beta)
+    rng = np.random.default_rng(16384)
+    edge = np.arange(n - 512, n)
+    rows = np.concatenate([rng.integers(0, n, 2048), np.full(512, n - 1), edge])
+    cols = np.concatenate([rng.integers(0, n, 2048), edge, np.full(512, n - 1)])
+    expect = oracle.fgemm_entries(A, B, p, alpha, beta, C, rows, cols)
+    assert np.array_equal(got[rows, cols], expect)
+    assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
+
+
 @pytest.mark.parametrize("kernel", ["single", "pair"])
 @pytest.mark.parametrize("shape,p", [((300, 1100, 520), 2147483647), ((129, 65, 257), 65521),
                                      ((2048, 256, 4096), 2147483647), ((600, 512, 1100), 2147483647),
