@@ -86,3 +86,32 @@ def test_simt_path_with_levels(p, levels):
     alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
     got = run(A, B, C, p, alpha, beta, "simt", levels)
     assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
+
+
+@pytest.mark.parametrize("path,p,k", [("rns", 2147483647, 65536), ("rns", 65521, 65536), ("fp64", 8388593, 8192),
+                                      ("fp64", 65521, 8192), ("fp32", 251, 65536)])
+def test_precision_config_full_size_sampled(path, p, k):
+    """The precision comparison at its own sizes (m = n = 8192, the longest
+    inner dimension each path is timed at), every Winograd depth it is timed
+    with: sampled entries recomputed by the oracle and Freivalds' test on the
+    whole result; alpha and beta are non-trivial here (the bench times 1, 0)."""
+    n = 8192
+    rng = W.rng_for("precision", 51, p, k)
+    A = W.uniform_residues(rng, (n, k), p)
+    B = W.uniform_residues(rng, (k, n), p)
+    C = W.uniform_residues(rng, (n, n), p)
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    dA, dB = to_dev(A), to_dev(B)
+    srng = np.random.default_rng(k + p)
+    rows = np.concatenate([srng.integers(0, n, 512), [0, n - 1, n - 1]])
+    cols = np.concatenate([srng.integers(0, n, 512), [n - 1, 0, n - 1]])
+    expect = oracle.fgemm_entries(A, B, p, alpha, beta, C, rows, cols)
+    for levels in (0, 1, 2):
+        dC = to_dev(C)
+        ff.fgemm_ex(dA, dB, p, alpha, beta, dC, path=path, winograd_levels=levels)
+        torch.cuda.synchronize()
+        assert ff.last_device_error() == 0
+        got = from_dev(dC)
+        assert np.array_equal(got[rows, cols], expect), (path, p, k, levels)
+        assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=1), (path, p, k, levels)
+        del dC
