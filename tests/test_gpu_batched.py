@@ -188,3 +188,43 @@ def test_batched_plan_equals_immediate_on_multimodular_batch():
     torch.cuda.synchronize()
     for x, y in zip(dev_a, dev_b):
         assert torch.equal(x[2], y[2])
+
+
+def test_config4_full_batch_sampled():
+    """The batched configuration at its full size, in the launch the bench
+    times: 4096 integer instances (m, n, k log-uniform in [16, 1024], entries
+    in [-2^20, 2^20]) reduced modulo each of the 32 primes below 2^31 on the
+    device, 131072 fgemms in one ffgpu_fgemm_batched call.  256 products drawn
+    at random are checked on 8 sampled entries each (a corner among them), and
+    every product's first entry."""
+    shapes, primes = W.multimodular_instances(count=4096, nprimes=32)
+    problems, ints = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        Ai, Bi = W.multimodular_integers(i, int(m), int(n), int(k))
+        ints.append((Ai, Bi))
+        dAi, dBi = torch.from_numpy(Ai).cuda(), torch.from_numpy(Bi).cuda()
+        for p in primes:
+            problems.append((torch.remainder(dAi, p).to(torch.int32), torch.remainder(dBi, p).to(torch.int32),
+                             torch.zeros((int(m), int(n)), dtype=torch.int32, device="cuda"), int(p), 1, 0))
+    descs, nd = ff.batched_descs(problems)
+    ff.fgemm_batched_descs(descs, nd)
+    torch.cuda.synchronize()
+    assert ff.last_device_error() == 0
+    rng = np.random.default_rng(4096)
+    picks = set(rng.integers(0, len(problems), 256).tolist())
+    firsts = torch.stack([pr[2][0, 0] for pr in problems]).cpu().numpy().view(np.uint32)
+    for idx, (dA, dB, dC, p, al, be) in enumerate(problems):
+        Ai, Bi = ints[idx // len(primes)]
+        if idx not in picks and idx % 97 != 0:
+            continue
+        A, B = W.reduce_signed(Ai, p), W.reduce_signed(Bi, p)
+        C = np.zeros((A.shape[0], B.shape[1]), np.uint32)
+        r = np.concatenate([rng.integers(0, A.shape[0], 7), [A.shape[0] - 1]])
+        c = np.concatenate([rng.integers(0, B.shape[1], 7), [B.shape[1] - 1]])
+        got = from_dev(dC)
+        assert np.array_equal(got[r, c], oracle.fgemm_entries(A, B, p, al, be, C, r, c)), idx
+    # the first entry of every product: one dot product each, against exact integers
+    for i, (Ai, Bi) in enumerate(ints):
+        v = int(np.dot(Ai[0].astype(object), Bi[:, 0].astype(object)))
+        for j, p in enumerate(primes):
+            assert firsts[i * len(primes) + j] == v % p, (i, p)
