@@ -4,7 +4,8 @@
 // two on a block boundary, solve the first half, update the other half of the
 // right-hand side with one fgemm (B2 <- B2 - T21 X1: alpha = p - 1, beta = 1),
 // solve the second half.  The recursion stops at diagonal blocks of L rows,
-// L between 128 and 1024 (about eight leaves), whose inverses are computed up
+// L between 128 and 1024 (two leaves up to 2048 rows, more beyond: the rule
+// and its measurements are at leaf_size), whose inverses are computed up
 // front: one kernel inverts every 128 x 128 diagonal block (one CTA per block,
 // eight lanes per column of the inverse, substitution mod p; non-unit
 // diagonals inverted by the extended Euclidean algorithm of section 2.1.1; a
@@ -31,10 +32,16 @@ namespace {
 constexpr int kBlk = 128;       // diagonal block inverted by substitution
 constexpr int kMaxLeaf = 1024;  // largest leaf
 
-// Leaf size for a triangle of size sz: about eight leaves, 128 to 1024 rows.
+// Leaf size for a triangle of size sz: the smallest power of two from 128
+// rows that covers half of it, at most 1024 rows (two leaves up to
+// sz = 2048, then more).  Each product costs tens of microseconds whatever
+// its size, so fewer, larger leaves win although a leaf's product does twice
+// its triangle's work: measured (ms, p = 65521, m = n, unit lower) with about
+// eight / four / two leaves: n = 2048 0.976 / 0.817 / 0.775, n = 4096 1.595 /
+// 1.331 / 1.333; n = 8192 takes eight leaves of 1024 rows either way.
 int64_t leaf_size(int64_t sz) {
     int64_t L = kBlk;
-    while (L < kMaxLeaf && L * 8 < sz) L *= 2;
+    while (L < kMaxLeaf && L * 2 < sz) L *= 2;
     return L;
 }
 
