@@ -70,7 +70,10 @@ def k_max_winograd(p: int, gamma: int, l: int, balanced: bool = False) -> int:
 
 
 def trsm_growth_positive(p: int, n: int) -> int:
-    """Corollary 4.4 / eq. (trsmboundpos): |x| <= (p-1)/2 * (p^(n-1) + (p-1)^(n-1))."""
+    """Corollary 4.4 / eq. (trsmboundpos) as printed:
+    |x| <= (p-1)/2 * (p^(n-1) + (p-1)^(n-1)).  Theorem 4.2 with entries in
+    [0, p-1] gives (p-2)^(n-1) in the second term, a tighter bound; the printed
+    form is kept because the paper's t_del values follow from it."""
     v = Fraction(p - 1, 2) * (p ** (n - 1) + (p - 1) ** (n - 1))
     return int(v) if v.denominator == 1 else v
 

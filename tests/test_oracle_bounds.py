@@ -76,3 +76,68 @@ def test_winograd_levels_formula():
     assert bounds.winograd_levels(999, 1000) == 0
     assert bounds.winograd_levels(4000, 1000) == 3
     assert bounds.winograd_levels(3999, 1000) == 2
+
+
+def _back_substitute(T, b):
+    """x with T x = b over Z for unit upper triangular T (exact integers)."""
+    n = len(b)
+    x = [0] * n
+    for i in range(n - 1, -1, -1):
+        x[i] = b[i] - sum(T[i][j] * x[j] for j in range(i + 1, n))
+    return x
+
+
+def _sign_chasing_system(n, m, M):
+    """The system of the optimality argument after Theorem 4.2: every entry at
+    the end of [m, M] that pushes the next unknown further from zero, the
+    unknowns alternating in sign (entries M at odd distance from the diagonal,
+    m at even distance; b ends in M and alternates upwards)."""
+    T = [[1 if j == i else (M if (j - i) % 2 else m) if j > i else 0 for j in range(n)] for i in range(n)]
+    b = [M if (n - 1 - i) % 2 == 0 else m for i in range(n)]
+    return T, b
+
+
+def _v(k, m, M):
+    from fractions import Fraction
+    return Fraction(M - m, 2) * (M + 1) ** k + Fraction(M + m, 2) * (M - 1) ** k
+
+
+@pytest.mark.parametrize("p", [3, 5, 7, 251, 1001, 65521])
+def test_trsm_growth_reached_with_balanced_residues(p):
+    # Corollary 4.3's bound is reached exactly for a range symmetric about
+    # zero: |x_{n-k}| = v_k for every k, so Corollary 4.5 (exponent n - 1) is
+    # the maximum for balanced residues
+    M = (p - 1) // 2
+    for n in range(1, 9):
+        x = _back_substitute(*_sign_chasing_system(n, -M, M))
+        assert [abs(x[n - 1 - k]) for k in range(n)] == [_v(k, -M, M) for k in range(n)]
+        assert max(abs(t) for t in x) == bounds.trsm_growth_balanced(p, n, exponent_n=False)
+
+
+@pytest.mark.parametrize("n,p", [(1, 11), (2, 11), (3, 11), (4, 11), (4, 7), (5, 5)])
+def test_trsm_growth_positive_residues(n, p):
+    # x is multilinear in the entries, so its extremes lie at the vertices
+    # {0, p - 1}.  The exhaustive maximum never exceeds Theorem 4.2's v_{n-1}
+    # for [m, M] = [0, p - 1], equals it up to n = 3 and stays strictly below
+    # from n = 4 on (the optimality stated after the theorem holds for ranges
+    # symmetric about zero); Corollary 4.4 as printed, with (p - 1)^(n-1)
+    # where the theorem gives (M - 1)^(n-1) = (p - 2)^(n-1), is looser still
+    # from n = 2 on.  Both stay upper bounds, which is all t_del needs.
+    import itertools
+    M = p - 1
+    pos = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    best = 0
+    for te in itertools.product((0, M), repeat=len(pos)):
+        T = [[1 if i == j else 0 for j in range(n)] for i in range(n)]
+        for (i, j), val in zip(pos, te):
+            T[i][j] = val
+        for b in itertools.product((0, M), repeat=n):
+            best = max(best, max(abs(t) for t in _back_substitute(T, list(b))))
+    theorem = _v(n - 1, 0, M)
+    printed = bounds.trsm_growth_positive(p, n)
+    assert best <= theorem <= printed
+    assert (best == theorem) == (n <= 3)
+    assert (theorem == printed) == (n == 1)
+    # the sign-chasing system attains the exhaustive maximum
+    x = _back_substitute(*_sign_chasing_system(n, 0, M))
+    assert max(abs(t) for t in x) == best
