@@ -182,6 +182,15 @@ int sm_count(int dev) {
 
 // Pool of (current device, stream); allocates the error word on first use and
 // grows the buffer to `need` bytes with stream-ordered allocation.
+// Host-side fault injection for tests: while FFGPU_INJECT_ALLOC_FAIL is set to
+// a non-empty value other than "0", every workspace growth fails as an
+// allocation failure would (FFGPU_ERR_NOMEM, the stream's pool left empty), so
+// the error path and the recovery after it can be exercised without a fault.
+static bool inject_alloc_failure() {
+    const char* e = std::getenv("FFGPU_INJECT_ALLOC_FAIL");
+    return e && *e && std::strcmp(e, "0") != 0;
+}
+
 ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
@@ -201,6 +210,7 @@ ffgpu_status pool_get(cudaStream_t s, size_t need, Pool** out) {
             pl.bytes = 0;
         }
         const size_t want = (need + (size_t(1) << 21) - 1) & ~((size_t(1) << 21) - 1);
+        if (inject_alloc_failure()) return FFGPU_ERR_NOMEM;
         if (cudaMallocAsync(&pl.ptr, want, s) != cudaSuccess) {
             cudaGetLastError();
             pl.ptr = nullptr;

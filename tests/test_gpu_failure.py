@@ -34,3 +34,27 @@ def test_wait_timeout_is_reported_and_context_survives():
 def test_selftest_rejects_bad_limits():
     with pytest.raises(ff.FFGPUError):
         ff.selftest_wait_timeout(0)
+
+
+def test_injected_allocation_failure_and_recovery(monkeypatch):
+    """A workspace allocation that fails (injected on the host) surfaces as
+    FFGPU_ERR_NOMEM with nothing launched, and the same call on the same
+    stream succeeds once allocation works again."""
+    p = 65521
+    rng = W.rng_for("smoke", 32)
+    A = W.uniform_residues(rng, (512, 700), p)   # 2.2e8 multiply-adds: the tensor-core
+    B = W.uniform_residues(rng, (700, 600), p)   # route, which needs a workspace
+    dA, dB = to_dev(A), to_dev(B)
+    dC = to_dev(np.full((512, 600), 7, np.uint32))
+    s = torch.cuda.Stream()                       # its workspace pool is still empty
+    monkeypatch.setenv("FFGPU_INJECT_ALLOC_FAIL", "1")
+    with pytest.raises(ff.FFGPUError) as e:
+        ff.fgemm(dA, dB, p, 1, 0, dC, stream=s)
+    assert e.value.status == -3                   # FFGPU_ERR_NOMEM
+    s.synchronize()
+    assert (from_dev(dC) == 7).all()              # C untouched
+    monkeypatch.delenv("FFGPU_INJECT_ALLOC_FAIL")
+    ff.fgemm(dA, dB, p, 1, 0, dC, stream=s)
+    s.synchronize()
+    assert ff.last_device_error() == 0
+    assert np.array_equal(from_dev(dC), oracle.fgemm(A, B, p))
