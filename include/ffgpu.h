@@ -224,8 +224,11 @@ FFGPU_API ffgpu_status ffgpu_fgemm_noalloc(int64_t m, int64_t n, int64_t k, uint
  * uplo 0 = lower, 1 = upper triangle of T is used (the other is not read);
  * diag 0 = non-unit, 1 = unit diagonal (diagonal entries are not read).
  * T (ldt) and B (ldb) are row-major device arrays; B is m x n.
- * Triangles of up to 64 rows are solved by substitution mod p; every other
- * step is an fgemm update on the same stream.  A non-invertible diagonal entry
+ * The recursion stops at diagonal blocks of 128 to 1024 rows, whose inverses
+ * are formed first (substitution mod p on 128-row blocks, then doubling with
+ * batched products); each such block is then one product with its inverse,
+ * and every other step is an fgemm update on the same stream.  A
+ * non-invertible diagonal entry
  * (non-unit) cannot be detected before the kernels run: it is recorded on the
  * device and ffgpu_last_device_error then returns FFGPU_ERR_INVALID (B is
  * undefined).
@@ -246,7 +249,7 @@ FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int6
  *                         so every output block is reduced exactly once (the
  *                         residue system keeps the whole accumulation exact).
  *   FFGPU_TRSM_DEFAULT    the recursive algorithm (measured the faster of the
- *                         two from n = 4096 on).
+ *                         two at every size tried, n = 2048 to 8192).
  * Same arguments, results and errors as ffgpu_ftrsm; FFGPU_ERR_INVALID for an
  * unknown algorithm.
  */
