@@ -96,3 +96,37 @@ def test_workspace_size_monotone():
     b = ff.fgemm_workspace_size(2048, 2048, 2048, 65521)
     assert 0 < a < b
     assert ff.fgemm_workspace_size(1024, 1024, 0, 65521) == 0
+
+
+def test_argument_checks_of_the_other_routines_without_device():
+    """ftrsm, LQUP and its derived routines, the batched call and the request
+    server reject bad arguments synchronously, before any device call (these
+    run here, on a host with no GPU).  Pointers are placeholders: nothing may
+    be dereferenced on these paths."""
+    import ctypes
+    L = ff.lib()
+    r, d, sv = ctypes.c_int64(0), ctypes.c_uint32(0), ctypes.c_void_p()
+    P = 8  # a placeholder device pointer
+    # ftrsm(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, stream)
+    assert L.ffgpu_ftrsm(0, 0, 1, 4, 4, 1, 1, P, 4, P, 4, None) == -2        # p < 2
+    assert L.ffgpu_ftrsm(2, 0, 1, 4, 4, 7, 1, P, 4, P, 4, None) == -1        # side
+    assert L.ffgpu_ftrsm(0, 0, 1, 4, 4, 7, 1, P, 3, P, 4, None) == -1        # ldt < m
+    assert L.ffgpu_ftrsm(0, 0, 1, 4, 4, 7, 1, P, 4, P, 3, None) == -1        # ldb < n
+    assert L.ffgpu_ftrsm(0, 0, 1, 4, 4, 7, 1, P, 4, None, 4, None) == -1     # null B
+    assert L.ffgpu_ftrsm_ex(0, 0, 1, 4, 4, 7, 1, P, 4, P, 4, 5, None) == -1  # unknown algorithm
+    # LQUP, rank, determinant, inverse: p must be prime
+    assert L.ffgpu_lqup(4, 4, 15, P, 4, ctypes.byref(r), P, P, None) == -2
+    assert L.ffgpu_lqup(-1, 4, 7, P, 4, ctypes.byref(r), P, P, None) == -1
+    assert L.ffgpu_lqup(4, 4, 7, P, 3, ctypes.byref(r), P, P, None) == -1    # lda < n
+    assert L.ffgpu_rank(4, 4, 9, P, 4, ctypes.byref(r), None) == -2
+    r.value = 5
+    assert L.ffgpu_rank(0, 4, 7, P, 4, ctypes.byref(r), None) == 0 and r.value == 0
+    assert L.ffgpu_det(-1, 7, P, 4, ctypes.byref(d), None) == -1
+    assert L.ffgpu_det(4, 21, P, 4, ctypes.byref(d), None) == -2
+    assert L.ffgpu_inverse(4, 7, P, 4, None, 4, None) == -1                   # null X
+    assert L.ffgpu_inverse(4, 7, P, 4, P, 3, None) == -1                      # ldx < n
+    # batched and the server
+    assert L.ffgpu_fgemm_batched(-1, None, None) == -1
+    assert L.ffgpu_fgemm_batched(0, None, None) == 0
+    assert L.ffgpu_server_create(0, 1 << 30, ctypes.byref(sv)) == -1          # no stream
+    assert L.ffgpu_server_create(2, 100, ctypes.byref(sv)) == -1              # budget below 1 MiB
