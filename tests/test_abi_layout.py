@@ -40,3 +40,15 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_argument_counts_match_the_header():
+    import re
+    txt = open(os.path.join(ROOT, "include", "ffgpu.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    decls = re.findall(r"FFGPU_API\s+[\w\s\*]+?\b(ffgpu_\w+)\s*\(([^)]*)\)\s*;", txt)
+    assert len(decls) >= 40
+    for name, params in decls:
+        params = " ".join(params.split())
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(binding.SIGNATURES[name]) == n, name
