@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <mutex>
 #include <queue>
 #include <unordered_map>
@@ -43,12 +44,24 @@ struct StageBuf {
     cudaEvent_t ev = nullptr;
     bool pending = false;
 };
+// One pair per device: a buffer's event belongs to the device whose stream
+// records it.
+struct StageSet {
+    StageBuf buf[2];
+    int next = 0;
+};
 std::mutex g_stage_mu;  // held from stage_get to stage_done
-StageBuf g_stage[2];
-int g_stage_next = 0;
+std::map<int, StageSet> g_stage_sets;
+
+StageSet& stage_set() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_stage_sets[dev];
+}
 
 unsigned char* stage_get(size_t bytes, int* idx) {
-    StageBuf& b = g_stage[g_stage_next];
+    StageSet& S = stage_set();
+    StageBuf& b = S.buf[S.next];
     if (b.pending) {
         cudaEventSynchronize(b.ev);
         b.pending = false;
@@ -70,13 +83,14 @@ unsigned char* stage_get(size_t bytes, int* idx) {
         }
         b.bytes = want;
     }
-    *idx = g_stage_next;
-    g_stage_next ^= 1;
+    *idx = S.next;
+    S.next ^= 1;
     return b.p;
 }
 
 void stage_done(int idx, cudaStream_t s) {
-    if (cudaEventRecord(g_stage[idx].ev, s) == cudaSuccess) g_stage[idx].pending = true;
+    StageBuf& b = stage_set().buf[idx];
+    if (cudaEventRecord(b.ev, s) == cudaSuccess) b.pending = true;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
