@@ -196,11 +196,12 @@ FFGPU_API ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t 
  * no cudaMalloc, cudaFree or allocating library routine and records no
  * profiling events.
  *
- * Limit: a problem whose scratch (bf16 channel planes of A and B, plus the
- * residue slots of at most 32 persistent CTAs) exceeds the array returns
- * FFGPU_ERR_NOMEM and enqueues nothing; ffgpu_fgemm_workspace_size gives the
- * order of magnitude (for p < 2^31 about 20*(m+n)*k bytes, so m = n = k = 1024
- * fits).
+ * Limit: a problem whose scratch exceeds the array returns FFGPU_ERR_NOMEM
+ * and enqueues nothing.  A product that runs on the CUDA cores (at most
+ * ffgpu_get_small_threshold() multiply-adds) needs only its k-split partial
+ * sums, a few MB at most.  Any other product needs the bf16 channel planes of
+ * A and B plus the residue slots of at most 32 persistent CTAs: for p < 2^31
+ * about 20*(m+n)*k + 21 MB bytes, so m = n = 1024 fits up to k = 1088.
  *
  * Set-up: the first call on a device looks up the array's device address on
  * that device (which may load the library's GPU code there); make that first

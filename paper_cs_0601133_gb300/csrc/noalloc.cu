@@ -71,8 +71,12 @@ extern "C" ffgpu_status ffgpu_fgemm_noalloc(int64_t m, int64_t n, int64_t k, uin
         cudaGetLastError();
         return FFGPU_ERR_CUDA;
     }
-    const int sms = std::min(sm_count(dev), kNoAllocMaxGrid);
-    const size_t need = fgemm_ws_bytes(m, n, k, p, sms);
+    // A product on the CUDA-core route needs only its k-split partial sums,
+    // sized with the SM count that route's launch uses; any other product
+    // needs the tensor-core layout (planes, and the slots of at most
+    // kNoAllocMaxGrid persistent CTAs).
+    const size_t need = fgemm_small(m, n, k) ? small_ws_bytes(m, n, k, sm_count(dev))
+                                             : fgemm_ws_bytes(m, n, k, p, kNoAllocMaxGrid);
     if (need > kNoAllocScratchBytes - kNoAllocErrBytes) return FFGPU_ERR_NOMEM;  // beyond the static maximum
     unsigned char* scratch = nullptr;
     st = scratch_address(&scratch);

@@ -24,7 +24,8 @@ import math
 import numpy as np
 
 SEED = 601133
-FAMILIES = ("square", "adversarial", "precision", "multimodular", "serving", "ftrsm", "smoke", "lqup")
+FAMILIES = ("square", "adversarial", "precision", "multimodular", "serving", "ftrsm", "smoke", "lqup",
+            "worstcase")
 
 
 def rng_for(family: str, *extra: int) -> np.random.Generator:
@@ -111,6 +112,32 @@ def adversarial_problem(m: int, n: int, k: int, p: int):
     B = np.full((k, n), p - 1, np.uint32)
     C = np.full((m, n), p - 1, np.uint32)
     return A, B, C
+
+
+def signed_word(v: int, p: int) -> int:
+    """The word in [0, p) that stands for the signed value v (|v| < p)."""
+    return v % p
+
+
+def sign_pattern_problem(rng: np.random.Generator, m: int, n: int, k: int, p: int, a: int, b: int):
+    """A[i][t] = s_i sigma_t a and B[t][j] = sigma_t t_j b as words mod p, with
+    random signs s (rows of A), t (columns of B) and sigma (the inner index).
+
+    Every product A[i][t] B[t][j] then equals s_i t_j a b: along each inner
+    index the terms of one output entry all carry the same sign, so every
+    partial sum of that entry grows monotonically to s_i t_j k a b, the largest
+    magnitude a sum of k such terms can reach, while the entries of A, B and
+    the result still vary in sign.  C is uniform in [0, p).  Returns
+    (A, B, C, s, t) with s and t as int64 arrays of +-1."""
+    s = rng.choice(np.array([-1, 1], np.int64), size=m)
+    t = rng.choice(np.array([-1, 1], np.int64), size=n)
+    sig = rng.choice(np.array([-1, 1], np.int64), size=k)
+    wa = np.array([signed_word(a, p), signed_word(-a, p)], np.uint32)
+    wb = np.array([signed_word(b, p), signed_word(-b, p)], np.uint32)
+    A = wa[((s[:, None] * sig[None, :]) < 0).astype(np.int64)]
+    B = wb[((sig[:, None] * t[None, :]) < 0).astype(np.int64)]
+    C = uniform_residues(rng, (m, n), p)
+    return A, B, C, s, t
 
 
 def log_uniform_int(rng: np.random.Generator, lo: int, hi: int, size) -> np.ndarray:

@@ -208,3 +208,158 @@ def test_both_kernels_adversarial(kernel, monkeypatch):
     A, B, C = W.adversarial_problem(m, n, k, p)
     got = run(A, B, C, p, p - 1, p - 1)
     assert np.all(got == ((p - 1) * k + (p - 1) * (p - 1)) % p)
+
+
+# ---------------------------------------------------------------------------
+# Worst cases of the two bounds the product rests on (section 2.1.2, eqs. 1-2,
+# restated for this design): (1) every partial sum of a channel's f32
+# accumulator is an integer below 2^24 between two in-place reductions, and
+# (2) the integer value |X| of a product entry stays within M/4, M the product
+# of the plan's moduli, where the reconstruction from the residues is exact.
+# Inputs of all-(p-1) do not reach either bound (p - 1 is centred to -1, so
+# every product is 1); the inputs below do, with the sign pattern of
+# workloads.sign_pattern_problem so that every sum grows monotonically.
+# ---------------------------------------------------------------------------
+
+def balanced(x: int, m: int) -> int:
+    r = x % m
+    return r - m if r > m // 2 else r
+
+
+def closed_form(s, t, k, a, b, p, alpha, beta, C):
+    """(alpha s_i t_j k a b + beta C) mod p, entry by entry, in Python integers."""
+    v = [(alpha * k * a * b) % p, (-alpha * k * a * b) % p]
+    X = np.where(np.outer(s, t) > 0, v[0], v[1]).astype(np.uint64)
+    return ((X + (beta % p) * C.astype(np.uint64)) % p).astype(np.uint32)
+
+
+def check_sampled(A, B, C, got, p, alpha, beta, seed, count=512):
+    rng = np.random.default_rng(seed)
+    m, n = got.shape
+    rows = np.concatenate([rng.integers(0, m, count), [0, m - 1, m - 1]])
+    cols = np.concatenate([rng.integers(0, n, count), [n - 1, 0, n - 1]])
+    expect = oracle.fgemm_entries(A, B, p, alpha, beta, C, rows, cols)
+    assert np.array_equal(got[rows, cols], expect)
+
+
+def largest_x_with_half_residues(p, moduli):
+    """x = -1/2 modulo the product of the leading moduli, as many of them as
+    keep x <= floor(p/2) (so that x is its own centred representative): the
+    balanced residue of x is +(m_c - 1)/2 in each of those channels."""
+    Mx, used = 1, 0
+    for mc in moduli:
+        if (Mx * mc - 1) // 2 > p // 2:
+            break
+        Mx *= mc
+        used += 1
+    assert used >= 1
+    return (Mx - 1) // 2, used
+
+
+@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
+def test_chunk_sums_reach_the_accumulator_bound(kernel, p, monkeypatch):
+    """Residues at +-(m_c - 1)/2 in the largest moduli (255, 253, ...): with
+    the sign pattern each chunk of a channel's accumulator sums chunk * 127^2
+    (channel 255) before the in-place reduction, 98 % of 2^24."""
+    monkeypatch.setenv("FFGPU_KERNEL", kernel)
+    m, n = 300, 520
+    plan = ff.fgemm_plan(m, n, 4096, p)
+    chunk, mods = plan["k_chunk"], plan["moduli"]
+    k = 3 * chunk + 300                        # three full chunks and a ragged one
+    plan = ff.fgemm_plan(m, n, k, p)
+    assert plan["k_chunk"] == chunk and plan["mode"] == 2
+    x, used = largest_x_with_half_residues(p, plan["moduli"])
+    assert all(balanced(x, mc) == (mc - 1) // 2 for mc in plan["moduli"][:used])
+    # host side: the chunk sum this input implies in each channel, plus the
+    # carried reduced value (at most (m_c + 1)/2)
+    peak = max(chunk * balanced(x, mc) ** 2 + (mc + 1) // 2 for mc in plan["moduli"])
+    assert 0.98 * 2**24 <= peak < 2**24, peak
+    rng = W.rng_for("worstcase", 1, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, x, x)
+    alpha, beta = int(rng.integers(1, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
+    assert np.array_equal(got, closed_form(s, t, k, x, x, p, alpha, beta, C))
+
+
+@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("p,v", [(251, 125), (255, 127), (253, 126), (3, 1)])
+def test_direct_mode_chunk_sums_at_the_bound(kernel, p, v, monkeypatch):
+    """One channel, the modulus p itself (p <= 255): entries +-floor(p/2), the
+    largest centred magnitude, so each chunk sums chunk * floor(p/2)^2 (for
+    p = 255: 1024 * 127^2 = 98.4 % of 2^24); three chunks and a ragged one."""
+    monkeypatch.setenv("FFGPU_KERNEL", kernel)
+    m, n = 260, 300
+    plan = ff.fgemm_plan(m, n, 4096, p)
+    assert plan["mode"] == 1 and plan["channels"] == 1
+    chunk = plan["k_chunk"]
+    k = 3 * chunk + 100
+    peak = chunk * v * v + v + 1
+    assert peak < 2**24
+    if p >= 251:
+        assert peak >= 0.95 * 2**24, peak
+    rng = W.rng_for("worstcase", 2, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, v, v)
+    got = run(A, B, C, p, p - 1, 7)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, p - 1, 7, C))
+    assert np.array_equal(got, closed_form(s, t, k, v, v, p, p - 1, 7, C))
+
+
+def channel_boundaries(p, k_hi):
+    """(c, k_max) for every channel count c the plan uses below k_hi: k_max is
+    the longest inner dimension summed with c channels (found by bisection on
+    the plan, a host-side call)."""
+    out = []
+    k = 1
+    while k <= k_hi:
+        c = ff.fgemm_plan(1, 1, k, p)["channels"]
+        lo, hi = k, k_hi + 1
+        while hi - lo > 1:                      # largest k with the same count
+            mid = (lo + hi) // 2
+            if ff.fgemm_plan(1, 1, mid, p)["channels"] == c:
+                lo = mid
+            else:
+                hi = mid
+        if lo < k_hi:
+            out.append((c, lo))
+        k = lo + 1
+    return out
+
+
+BOUNDARY_CASES = [(p, which) for p in (65521, 8388593, 2147483647) for which in (-2, -1)]
+
+
+@pytest.mark.parametrize("kernel", ["single", "pair"])
+@pytest.mark.parametrize("p,which", BOUNDARY_CASES)
+@pytest.mark.parametrize("past", [0, 1])
+def test_reconstruction_at_the_channel_boundaries(kernel, p, which, past, monkeypatch):
+    """Entries +-floor(p/2) (the largest centred magnitude) with the sign
+    pattern, so every entry of the product is +-k floor(p/2)^2.  At the
+    longest k a channel count admits (past = 0) that is at least 3/4 of M/4,
+    the reconstruction's limit; one more (past = 1) switches to the next
+    channel count.  The two largest switches below 200000 per prime (for
+    2^31 - 1: 9 -> 10 channels at k = 605 and 10 -> 11 at k = 134930)."""
+    monkeypatch.setenv("FFGPU_KERNEL", kernel)
+    bounds = channel_boundaries(p, 200000)
+    c, kmax = bounds[which]
+    k = kmax + past
+    plan = ff.fgemm_plan(1, 1, k, p)
+    assert plan["channels"] == c + past
+    h = p // 2
+    M = 1
+    for mc in plan["moduli"]:
+        M *= mc
+    X = k * h * h
+    assert X <= M // 4
+    if past == 0:
+        assert X >= 0.75 * (M // 4), (X, M // 4)
+    m, n = 288, 272
+    rng = W.rng_for("worstcase", 3, p, k)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, h, h)
+    alpha, beta = int(rng.integers(1, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta)
+    assert np.array_equal(got, closed_form(s, t, k, h, h, p, alpha, beta, C))
+    check_sampled(A, B, C, got, p, alpha, beta, seed=k)
+    if k < 1000:
+        assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))

@@ -115,3 +115,63 @@ def test_precision_config_full_size_sampled(path, p, k):
         assert np.array_equal(got[rows, cols], expect), (path, p, k, levels)
         assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=1), (path, p, k, levels)
         del dC
+
+
+# Worst cases of each comparison path's delayed-reduction bound (eqs. 1-2):
+# entries +-floor(p/2) (the largest centred magnitude) in the sign pattern of
+# workloads.sign_pattern_problem, so every partial sum between two reductions
+# is a sum of equal-signed products floor(p/2)^2 -- the largest value the
+# blocking admits.  (All entries p - 1 are centred to -1 and stress nothing.)
+
+def closed_form(s, t, k, a, p, alpha, beta, C):
+    v = [(alpha * k * a * a) % p, (-alpha * k * a * a) % p]
+    X = np.where(np.outer(s, t) > 0, v[0], v[1]).astype(np.uint64)
+    return ((X + (beta % p) * C.astype(np.uint64)) % p).astype(np.uint32)
+
+
+def test_fp32_path_at_its_block_bound():
+    """FP32: p = 251, entries +-125, reduced every R products with
+    R 125^2 + 2p <= 2^24 (R = 1072): each block sums 1072 * 15625 = 99.8 % of
+    2^24; three blocks and a ragged one."""
+    p, h = 251, 125
+    R = ((1 << 24) - 2 * p) // (h * h) // 8 * 8       # the path's block: whole k-tiles of 8
+    assert R == 1072 and R * h * h + p < 2**24 and R * h * h >= 0.99 * 2**24
+    m, n, k = 200, 136, 3 * R + 50
+    rng = W.rng_for("worstcase", 10, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, h, h)
+    got = run(A, B, C, p, 3, 5, "fp32", 0)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, 3, 5, C))
+    assert np.array_equal(got, closed_form(s, t, k, h, p, 3, 5, C))
+
+
+@pytest.mark.parametrize("p", [8388593, 33554393])
+def test_fp64_path_at_its_block_bound(p):
+    """FP64 DMMA: entries +-floor(p/2), 16-long k-tiles between reductions.
+    For p = 33554393 (the largest prime below 2^25, the path's limit) a tile
+    sums 16 floor(p/2)^2 = 50 % of 2^53; the accumulator keeps at most 1.5p
+    after a reduction."""
+    h = p // 2
+    assert 16 * h * h + 3 * p // 2 < 2**53
+    if p > 2**24:
+        assert 16 * h * h >= 0.49 * 2**53
+    m, n, k = 200, 136, 4096 + 13
+    rng = W.rng_for("worstcase", 11, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, h, h)
+    alpha, beta = int(rng.integers(1, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta, "fp64", 0)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
+    assert np.array_equal(got, closed_form(s, t, k, h, p, alpha, beta, C))
+
+
+@pytest.mark.parametrize("path,p", [("rns", 2147483647), ("fp64", 8388593), ("fp32", 251)])
+@pytest.mark.parametrize("levels", [1, 2])
+def test_winograd_levels_on_worst_case_inputs(path, p, levels):
+    """The same inputs through Winograd's levels: the pre-additions are
+    reduced mod p, so each base product sees residues anywhere in [0, p);
+    the result must still be exact."""
+    h = p // 2
+    m, n, k = 260, 264, 2200
+    rng = W.rng_for("worstcase", 12, p, levels)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, h, h)
+    got = run(A, B, C, p, 1, 1, path, levels)
+    assert np.array_equal(got, closed_form(s, t, k, h, p, 1, 1, C))

@@ -141,3 +141,33 @@ def test_trsm_growth_positive_residues(n, p):
     # the sign-chasing system attains the exhaustive maximum
     x = _back_substitute(*_sign_chasing_system(n, 0, M))
     assert max(abs(t) for t in x) == best
+
+
+@pytest.mark.parametrize("p", [3, 5, 251, 65521, 1048573, 8388593])
+@pytest.mark.parametrize("l", [1, 2, 3])
+@pytest.mark.parametrize("gamma", [53, 62])
+def test_k_max_winograd_balanced_by_search(p, l, gamma):
+    """k_max_winograd(balanced=True) against a search on Theorem 3.1 itself
+    with balanced ranges [-(p-1)/2, (p-1)/2] (the theorem is pinned by the
+    appendix's matrices in test_oracle_winograd.py): the largest k whose bound
+    stays below 2^gamma."""
+    h = (p - 1) // 2
+    ok = lambda k: bounds.winograd_bound(l, k, -h, h, -h, h) < 2**gamma
+    assert bounds.k_max_winograd(p, gamma, l, balanced=True) == _largest_k(ok, l)
+    # and the positive range [0, p-1] (Corollary 3.2) the same way
+    okp = lambda k: bounds.winograd_bound(l, k, 0, p - 1, 0, p - 1) < 2**gamma
+    assert bounds.k_max_winograd(p, gamma, l, balanced=False) == _largest_k(okp, l)
+
+
+def _largest_k(ok, l):
+    """Largest k with ok(k), for a predicate that holds below 2^l (the bound
+    depends on floor(k / 2^l)) and is monotone."""
+    if not ok(2**l):
+        return 2**l - 1
+    lo, hi = 2**l, 2**(l + 1)
+    while ok(hi):
+        lo, hi = hi, 2 * hi
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        lo, hi = (mid, hi) if ok(mid) else (lo, mid)
+    return lo

@@ -66,14 +66,34 @@ def test_against_oracle(p, levels, m, n, k):
 
 
 @pytest.mark.gpu
-def test_limit_boundary():
-    p, levels = 8388593, 3
+@pytest.mark.parametrize("p,levels", [(8388593, 3), (8388593, 2), (8388593, 1), (1048573, 2)])
+def test_limit_boundary(p, levels):
+    """The appendix's A_l, B_l for balanced residues (entries -(p-1)/2 and
+    (p-1)/2), every entry widened to a block so that the inner dimension is
+    the largest multiple of 2^l the admission limit allows: the unreduced
+    levels then reach Theorem 3.1's bound itself (the oracle's CPU model of
+    the schedule confirms the largest intermediate on a narrower copy), and
+    the result must still be exact.  One k past the limit is refused."""
+    from oracle.winograd import optimal_matrices, winograd_fgemm_z
     kmax = ff.winograd_unreduced_kmax(p, levels)
-    rng = W.rng_for("precision", 17)
-    # all entries at the balanced extreme (p-1)/2: the worst magnitudes
-    m, n = 9, 11
-    A = np.full((m, kmax), (p - 1) // 2, np.uint32)
-    B = np.full((kmax, n), (p - 1) // 2, np.uint32)
+    h = (p - 1) // 2
+    d = kmax // 2**levels
+    assert d >= 1
+    A_l, B_l = optimal_matrices(levels, -h, h, -h, h)
+    widen = lambda X, r, c: np.kron(X, np.ones((r, c), dtype=object))
+    # the bound with d inner blocks, checked against the CPU model at d = 1, 2
+    for dd in (1, 2):
+        _, zmax = winograd_fgemm_z(widen(A_l, 1, dd), widen(B_l, dd, 1), None, 1, 0, levels)
+        assert zmax == bounds.winograd_bound(levels, 2**levels * dd, -h, h, -h, h)
+    thm = bounds.winograd_bound(levels, 2**levels * d, -h, h, -h, h)
+    assert thm < 2**62 <= bounds.winograd_bound(levels, 2**levels * (d + 1), -h, h, -h, h)
+    r, s = 9, 11
+    A_w = np.kron(A_l.astype(np.int64), np.ones((r, d), np.int64))    # m = 2^l r, k = 2^l d
+    B_w = np.kron(B_l.astype(np.int64), np.ones((d, s), np.int64))    # n = 2^l s
+    A, B = (A_w % p).astype(np.uint32), (B_w % p).astype(np.uint32)
+    m, k, n = A.shape[0], A.shape[1], B.shape[1]
+    assert k == 2**levels * d <= kmax
+    rng = W.rng_for("precision", 17, p, levels)
     C = W.uniform_residues(rng, (m, n), p)
     assert np.array_equal(run(A, B, C, p, 1, 1, levels), oracle.fgemm(A, B, p, 1, 1, C))
     A2 = np.zeros((m, kmax + 1), np.uint32)
