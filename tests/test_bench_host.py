@@ -55,8 +55,13 @@ def test_clock_record_absent_without_samples():
 def test_measured_peak_and_fallback(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.measured_peak()[1].startswith("fallback")
-    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"bf16_tflops_sustained": 1661.8, "hbm_gbs": 6788.3}))
+    burst, sus, prov = bench.measured_peaks()
+    assert (burst, sus, prov["file"]) == (1900.0, 1700.0, None)
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps(
+        {"bf16_tflops": 1872.8, "bf16_tflops_sustained": 1661.8, "hbm_gbs": 6788.3, "sm_max_mhz": 2070.0}))
     assert bench.measured_peak() == (1661.8, "measured bf16 cuBLAS, sustained")
+    burst, sus, prov = bench.measured_peaks()
+    assert (burst, sus, prov["file"], prov["sm_max_mhz"]) == (1872.8, 1661.8, "MEASURED_PEAKS.json", 2070.0)
 
 
 def test_traffic_only_while_the_kernel_is_unchanged(tmp_path, monkeypatch):
