@@ -249,17 +249,43 @@ FFGPU_API ffgpu_status ffgpu_ftrsm(int side, int uplo, int diag, int64_t m, int6
  *                         once, X_i = [Inv_i | -Inv_i T_i,prev] [B_i ; X_prev],
  *                         so every output block is reduced exactly once (the
  *                         residue system keeps the whole accumulation exact).
- *   FFGPU_TRSM_DEFAULT    the recursive algorithm (measured the faster of the
- *                         two at every size tried, n = 2048 to 8192).
+ *   FFGPU_TRSM_CASCADE    Algorithms 2-3 (section 4.3) as the paper states
+ *                         them: blocks of t_split rows (Algorithm 2), each
+ *                         solved by the recursion of Algorithm 3 with its
+ *                         updates over Z (int64, exact products on the tensor
+ *                         cores, no reduction) and leaves of t_del rows solved
+ *                         over Z (eq. trsmboundcen), then reduced mod p; the
+ *                         rows below a block updated by one fgemm mod p.
+ *                         Non-unit diagonals are normalised first (T = D U,
+ *                         section 4.2).  ffgpu_ftrsm_cascade_params gives
+ *                         t_del, t_update and t_split for p.
+ *   FFGPU_TRSM_DEFAULT    the recursive algorithm (measured the fastest at
+ *                         every size tried, n = 2048 to 8192).
  * Same arguments, results and errors as ffgpu_ftrsm; FFGPU_ERR_INVALID for an
  * unknown algorithm.
  */
 #define FFGPU_TRSM_DEFAULT (-1)
 #define FFGPU_TRSM_RECURSIVE 0
 #define FFGPU_TRSM_DELAYED 1
+#define FFGPU_TRSM_CASCADE 2
 FFGPU_API ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
                                       const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, int algorithm,
                                       void* stream);
+
+/*
+ * The thresholds of FFGPU_TRSM_CASCADE for p (section 4.2-4.3, balanced
+ * residues |x| <= h = floor(p/2), carried in 64-bit signed integers):
+ *   t_del    the largest n with h (h+1)^n < 2^63 (eq. trsmboundcen with
+ *            gamma = 63): rows of a leaf solved over Z with no reduction;
+ *   t_update the largest t with t h^2 + h < 2^62 (eq. 2 with gamma = 63, one
+ *            term reserved for the right-hand side itself): products a
+ *            right-hand side entry accumulates over Z between reductions;
+ *   t_split  floor(t_update / t_del) t_del (Algorithm 2).
+ * t_del is capped at 128 rows and t_update at 2^31 - 1.  Host-only; no device
+ * is touched.  FFGPU_ERR_UNSUPPORTED_P outside 2 <= p < 2^31,
+ * FFGPU_ERR_INVALID for a null output pointer.
+ */
+FFGPU_API ffgpu_status ffgpu_ftrsm_cascade_params(uint32_t p, int64_t* t_del, int64_t* t_update, int64_t* t_split);
 
 /*
  * LQUP factorization over Z/pZ (section 5: A = L Q U P, L lower triangular,

@@ -582,7 +582,8 @@ ffgpu_status ffgpu_ftrsm_ex(int side, int uplo, int diag, int64_t m, int64_t n, 
                             const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, int algorithm, void* stream) {
     if (p < 2 || p > 0x7FFFFFFFu) return FFGPU_ERR_UNSUPPORTED_P;
     if (side < 0 || side > 1 || uplo < 0 || uplo > 1 || diag < 0 || diag > 1) return FFGPU_ERR_INVALID;
-    if (algorithm != FFGPU_TRSM_DEFAULT && algorithm != FFGPU_TRSM_RECURSIVE && algorithm != FFGPU_TRSM_DELAYED)
+    if (algorithm != FFGPU_TRSM_DEFAULT && algorithm != FFGPU_TRSM_RECURSIVE && algorithm != FFGPU_TRSM_DELAYED &&
+        algorithm != FFGPU_TRSM_CASCADE)
         return FFGPU_ERR_INVALID;
     if (m < 0 || n < 0 || m > INT32_MAX / 2 || n > INT32_MAX / 2) return FFGPU_ERR_INVALID;
     if (m == 0 || n == 0) return FFGPU_OK;

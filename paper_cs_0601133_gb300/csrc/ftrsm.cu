@@ -432,6 +432,7 @@ int ftrsm_algo(int algo) { return algo == FFGPU_TRSM_DEFAULT ? FFGPU_TRSM_RECURS
 
 // Workspace: leaf inverses | leaf panel | doubling temporaries | [Q] | the largest product's workspace.
 size_t ftrsm_ws_bytes(int side, int uplo, int algo, int64_t m, int64_t n, uint32_t p, int sms) {
+    if (ftrsm_algo(algo) == FFGPU_TRSM_CASCADE) return cascade_ws_bytes(side, m, n, p, sms);
     const TrsmLayout Y = trsm_layout(side, uplo, ftrsm_algo(algo), m, n, p, sms);
     return Y.rest + align256(Y.fg);
 }
@@ -441,6 +442,8 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
                        int* err, cudaStream_t s) {
     const int64_t sz = side == 0 ? m : n;
     algo = ftrsm_algo(algo);
+    if (algo == FFGPU_TRSM_CASCADE)
+        return cascade_run(side, uplo, diag, m, n, p, alpha, T, ldt, B, ldb, ws, ws_bytes, err, s);
     int dev = 0;
     cudaGetDevice(&dev);
     const TrsmLayout Y = trsm_layout(side, uplo, algo, m, n, p, sm_count(dev));

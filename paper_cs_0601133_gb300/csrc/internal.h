@@ -283,6 +283,11 @@ ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32
                           int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc,
                           void* ws, size_t ws_bytes, int* err, cudaStream_t s);
 uint32_t multimod_plan_modulus(int bits);
+// one exact integer product into (or added to) an int64 array (multimod.cu)
+size_t int_gemm_ws_bytes(int64_t m, int64_t n, int64_t k, int bits, int sms);
+ffgpu_status int_gemm_run(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda,
+                          const int32_t* B, int64_t ldb, long long* X, int64_t ldx, bool accumulate, void* ws,
+                          size_t ws_bytes, int* err, cudaStream_t s);
 // grouped fan-out over the instances of a batch (one wave)
 struct FanInst {
     const long long* X;
@@ -321,6 +326,18 @@ ffgpu_status batched_plan_run(BatchedPlan* plan, cudaStream_t s);
 ffgpu_status batched_plan_error(BatchedPlan* plan);
 void batched_plan_destroy(BatchedPlan* plan);
 void batched_plan_info(const BatchedPlan* plan, int* waves, int* singles, size_t* nodes, size_t* device_bytes);
+
+// ftrsm: the double cascade of Algorithms 2-3 (ftrsm_cascade.cu)
+struct CascadeParams {
+    int64_t t_del;     // rows of a leaf solved over Z with no reduction (eq. trsmboundcen, 63-bit carrier)
+    int64_t t_update;  // products an entry may accumulate over Z between reductions (eq. 2, 63-bit carrier)
+    int64_t t_split;   // floor(t_update / t_del) t_del: rows of one delayed block
+};
+CascadeParams cascade_params(uint32_t p);
+size_t cascade_ws_bytes(int side, int64_t m, int64_t n, uint32_t p, int sms);
+ffgpu_status cascade_run(int side, int uplo, int diag, int64_t m, int64_t n, uint32_t p, uint32_t alpha,
+                         const uint32_t* T, int64_t ldt, uint32_t* B, int64_t ldb, void* ws, size_t ws_bytes,
+                         int* err, cudaStream_t s);
 
 // ftrsm (ftrsm.cu)
 int ftrsm_algo(int algo);

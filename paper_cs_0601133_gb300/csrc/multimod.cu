@@ -242,24 +242,31 @@ cudaError_t launch_multimod_fanout(const long long* X, long long ldx, int m, int
     return cudaGetLastError();
 }
 
-ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda, const int32_t* B,
-                          int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc,
-                          void* ws, size_t ws_bytes, int* err, cudaStream_t s) {
-    if (m == 0 || n == 0) return FFGPU_OK;
+// Workspace of one exact integer product (planes and residue slots; the
+// int64 result is the caller's).
+size_t int_gemm_ws_bytes(int64_t m, int64_t n, int64_t k, int bits, int sms) {
+    if (m == 0 || n == 0) return 0;
+    RnsPlan pl;
+    make_plan(multimod_plan_modulus(bits), std::max<int64_t>(k, 1), pl);
+    const int64_t kp = (std::max<int64_t>(k, 1) + kTileK - 1) / kTileK * kTileK;
+    const int64_t tiles = ((m + kTileM - 1) / kTileM) * ((n + kTileN - 1) / kTileN);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
+    return align256(size_t(grid) * kSlotsPerCta * size_t(pl.nch) * kTileM * kTileN) +
+           align256(size_t(pl.nch) * m * kp * 2) + align256(size_t(pl.nch) * n * kp * 2);
+}
+
+// The exact integer product X = A B (int32 words taken as they are, |entries|
+// <= 2^bits, k 2^(2 bits) < 2^62) written to X (int64, ldx even and X 16-byte
+// aligned for vector stores), or added to it when accumulate is set (the sum
+// must stay below 2^63 in magnitude).  Conversions of both operands, then the
+// integer-mode tensor-core kernel.
+ffgpu_status int_gemm_run(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda,
+                          const int32_t* B, int64_t ldb, long long* X, int64_t ldx, bool accumulate, void* ws,
+                          size_t ws_bytes, int* err, cudaStream_t s) {
+    if (m == 0 || n == 0 || k == 0) return FFGPU_OK;
     int dev = 0;
     cudaGetDevice(&dev);
     const int sms = sm_count(dev);
-    FanoutParams F;
-    fanout_params(nprimes, primes, C, ldc, F);
-    const int64_t ldx = (n + 1) / 2 * 2;
-    if (k == 0) {  // X = 0
-        if (cudaMemsetAsync(ws, 0, size_t(m) * ldx * 8, s) != cudaSuccess) return FFGPU_ERR_CUDA;
-        return timed_launch("multimod_fanout", s, [&] {
-                   return launch_multimod_fanout(static_cast<const long long*>(ws), ldx, (int)m, (int)n, F, s);
-               }) == cudaSuccess
-                   ? FFGPU_OK
-                   : FFGPU_ERR_CUDA;
-    }
     RnsPlan pl;
     make_plan(multimod_plan_modulus(bits), k, pl);  // magnitudes up to 2^bits play the centred residues' part
     if (pl.mode != 2 || k > pl.k_slice) return FFGPU_ERR_INVALID;
@@ -270,9 +277,7 @@ ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32
     const size_t o_slots = 0;
     const size_t o_A = o_slots + align256(size_t(grid) * kSlotsPerCta * size_t(pl.nch) * kTileM * kTileN);
     const size_t o_B = o_A + align256(size_t(pl.nch) * m * kp * 2);
-    const size_t o_X = o_B + align256(size_t(pl.nch) * n * kp * 2);
-    if (ws_bytes < o_X + align256(size_t(m) * ldx * 8)) return FFGPU_ERR_NOMEM;
-    long long* X = reinterpret_cast<long long*>(w + o_X);
+    if (ws_bytes < o_B + align256(size_t(pl.nch) * n * kp * 2)) return FFGPU_ERR_NOMEM;
 
     ConvertParams cp;
     std::memset(&cp, 0, sizeof(cp));
@@ -302,14 +307,43 @@ ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32
     RnsGemmParams P;
     std::memset(&P, 0, sizeof(P));
     fill_inst_int(P.inst, m, n, kp, pl, X, ldx);
+    P.inst.beta = accumulate ? 1u : 0u;  // integer mode: add the int64 values already in X
     P.tiles_m = (int)((m + kTileM - 1) / kTileM);
     P.tiles_n = (int)((n + kTileN - 1) / kTileN);
     P.num_tiles = P.tiles_m * P.tiles_n;
     P.slots = w + o_slots;
     P.slot_stride = size_t(pl.nch) * kTileM * kTileN;
     P.err = err;
-    if (timed_launch("rns_gemm_int", s, [&] { return launch_rns_gemm_int(mapA, mapB, P, grid, s); }) != cudaSuccess)
-        return FFGPU_ERR_CUDA;
+    return timed_launch("rns_gemm_int", s, [&] { return launch_rns_gemm_int(mapA, mapB, P, grid, s); }) ==
+                   cudaSuccess
+               ? FFGPU_OK
+               : FFGPU_ERR_CUDA;
+}
+
+ffgpu_status multimod_run(int64_t m, int64_t n, int64_t k, int bits, const int32_t* A, int64_t lda, const int32_t* B,
+                          int64_t ldb, int nprimes, const uint32_t* primes, uint32_t* const* C, int64_t ldc,
+                          void* ws, size_t ws_bytes, int* err, cudaStream_t s) {
+    if (m == 0 || n == 0) return FFGPU_OK;
+    FanoutParams F;
+    fanout_params(nprimes, primes, C, ldc, F);
+    const int64_t ldx = (n + 1) / 2 * 2;
+    if (k == 0) {  // X = 0
+        if (cudaMemsetAsync(ws, 0, size_t(m) * ldx * 8, s) != cudaSuccess) return FFGPU_ERR_CUDA;
+        return timed_launch("multimod_fanout", s, [&] {
+                   return launch_multimod_fanout(static_cast<const long long*>(ws), ldx, (int)m, (int)n, F, s);
+               }) == cudaSuccess
+                   ? FFGPU_OK
+                   : FFGPU_ERR_CUDA;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // the product's planes and slots first, then the int64 result (the layout
+    // multimod_ws_bytes sizes)
+    const size_t o_X = int_gemm_ws_bytes(m, n, k, bits, sm_count(dev));
+    if (ws_bytes < o_X + align256(size_t(m) * ldx * 8)) return FFGPU_ERR_NOMEM;
+    long long* X = reinterpret_cast<long long*>(static_cast<unsigned char*>(ws) + o_X);
+    const ffgpu_status st = int_gemm_run(m, n, k, bits, A, lda, B, ldb, X, ldx, false, ws, o_X, err, s);
+    if (st != FFGPU_OK) return st;
     return timed_launch("multimod_fanout", s, [&] {
                return launch_multimod_fanout(X, ldx, (int)m, (int)n, F, s);
            }) == cudaSuccess

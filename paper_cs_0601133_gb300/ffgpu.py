@@ -130,6 +130,8 @@ SIGNATURES = {
     "ffgpu_fgemm_batched_plan_destroy": [_VP],
     "ffgpu_ftrsm": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _VP],
     "ffgpu_ftrsm_ex": [_I32, _I32, _I32, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _I32, _VP],
+    "ffgpu_ftrsm_cascade_params": [_U32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)],
     "ffgpu_selftest_wait_timeout": [_I64, _VP],
     "ffgpu_autotune": [_I64, _I64, _I64, _U32, _I32, _VP, ctypes.POINTER(Tuned)],
     "ffgpu_autotune_lookup": [_I64, _I64, _I64, _U32, _I32, ctypes.POINTER(Tuned)],
@@ -349,14 +351,23 @@ def fgemm_batched(problems, stream=None):
     return [pr[2] for pr in probs]
 
 
-TRSM_ALGORITHMS = {"default": -1, "recursive": 0, "delayed": 1}
+TRSM_ALGORITHMS = {"default": -1, "recursive": 0, "delayed": 1, "cascade": 2}
+
+
+def ftrsm_cascade_params(p: int) -> dict:
+    """t_del, t_update and t_split of the double cascade (Algorithms 2-3) for p."""
+    a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().ffgpu_ftrsm_cascade_params(p, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "ffgpu_ftrsm_cascade_params")
+    return {"t_del": a.value, "t_update": b.value, "t_split": c.value}
 
 
 def ftrsm(T, B, p: int, alpha: int = 1, side: str = "L", uplo: str = "L", diag: str = "U", stream=None,
           algorithm: str = "default"):
     """In place: B <- alpha*T^{-1}*B (side "L") or alpha*B*T^{-1} (side "R") mod p. Returns B.
     algorithm: "recursive" (Algorithm 1), "delayed" (left-looking, one reduction
-    per block) or "default"."""
+    per block), "cascade" (Algorithms 2-3: updates and leaves over Z) or
+    "default"."""
     m, n = B.shape
     nt = m if side == "L" else n
     if tuple(T.shape) != (nt, nt):
