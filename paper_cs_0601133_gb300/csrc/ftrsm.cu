@@ -66,14 +66,18 @@ struct Acc128 {
 // (exact 128-bit partial sums, reduced once, combined by shuffles), so the
 // sequential chain is one short step per row.
 constexpr int kInvThreads = 8 * kBlk;
+constexpr int kBX = kBlk + 1;  // padded column stride of the inverse in shared memory
 __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt,
                                                                   int size, int upper, int unit, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Inv, int leaf, int* err) {
     extern __shared__ uint32_t sm[];
-    uint32_t* sX = sm;                     // [kBlk][kBlk]: column j of the inverse at sX[i*kBlk + j]
-    uint32_t* sT = sm + kBlk * kBlk;       // [kBlk][kBlk]: the block of T
-    uint32_t* sD = sm + 2 * kBlk * kBlk;   // [kBlk] inverse diagonal
+    // column-major with a padded stride: entry (i, j) of the inverse at sX[j*kBX + i], so that the
+    // eight lanes of a column read consecutive words (distinct banks) in the dot products below and
+    // the final copy, which walks j, spreads over the banks too
+    uint32_t* sX = sm;
+    uint32_t* sT = sm + kBlk * kBX;              // [kBlk][kBlk]: the block of T
+    uint32_t* sD = sT + kBlk * kBlk;             // [kBlk] inverse diagonal
     const int b = blockIdx.x;
     const int base = b * kBlk;
     const int tb = min(kBlk, size - base);
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
             sD[i] = d;
         }
     }
-    for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) sX[idx] = 0u;
+    for (int idx = threadIdx.x; idx < kBlk * kBX; idx += blockDim.x) sX[idx] = 0u;
     __syncthreads();
     const int j = threadIdx.x >> 3, gl = threadIdx.x & 7;
     const bool col = j < tb;
@@ -103,7 +107,8 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
             // any 32-bit word times a residue < 2^31 stays below 2^63
             const uint32_t* Ti = sT + i * kBlk;
             const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
-            for (int l = lo + gl; l < hi; l += 8) acc.add((unsigned long long)Ti[l] * sX[l * kBlk + j]);
+            const uint32_t* Xj = sX + j * kBX;
+            for (int l = lo + gl; l < hi; l += 8) acc.add((unsigned long long)Ti[l] * Xj[l]);
         }
         uint32_t v = act ? acc.mod(p, mu, two64p) : 0u;
         for (int o = 4; o > 0; o >>= 1) {
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
         if (act && gl == 0) {
             const uint32_t rhs = (i == j) ? 1u : 0u;
             const uint32_t t = rhs >= v ? rhs - v : rhs + (p - v);
-            sX[i * kBlk + j] = mod_u64((unsigned long long)t * sD[i], p, mu);
+            sX[j * kBX + i] = mod_u64((unsigned long long)t * sD[i], p, mu);
         }
         __syncwarp();
     }
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
     uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
     for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) {
         const int r = idx / kBlk, c = idx % kBlk;
-        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[r * kBlk + c] : 0u;
+        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[c * kBX + r] : 0u;
     }
 }
 
@@ -473,7 +478,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
     }
     // leaf inverses: zero (the other triangle), 128-blocks by substitution, then doubling
     if (cudaMemsetAsync(inv, 0, size_t(Y.nl) * Y.L * Y.L * 4, s) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const size_t smem = 2 * size_t(kBlk) * kBlk * 4 + kBlk * 4;
+    const size_t smem = (size_t(kBlk) * kBX + size_t(kBlk) * kBlk + kBlk) * 4;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(trsm_invert_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
