@@ -573,7 +573,7 @@ def run_ftrsm(args):
             copy_ms = time_call(lambda: dB.copy_(dB0), torch, steps, 1)
             dC = torch.zeros((n, n), dtype=torch.int32, device="cuda")
             gemm_ms = time_call(lambda: ff.fgemm(dT, dB0, p, 1, 0, dC), torch, steps, 1)
-            for algo in ("recursive", "delayed"):
+            for algo in ("recursive", "delayed", "cascade"):
                 ms = time_call(lambda: (dB.copy_(dB0), ff.ftrsm(dT, dB, p, 1, "L", uplo, diag, algorithm=algo)),
                                torch, steps, 1)
                 ff.profile_enable(True)

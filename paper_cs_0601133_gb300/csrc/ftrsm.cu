@@ -60,25 +60,29 @@ struct Acc128 {
 
 // Inverse of diagonal block b of T (rows/cols [b kBlk, b kBlk + tb)), written
 // densely into the leaf-sized inverse that contains it (kBlk x kBlk, zeros
-// outside the triangle).  One CTA of 8 kBlk threads: eight lanes per column
-// j of the inverse, which solves T x = e_j by forward (lower) or back (upper)
-// substitution mod p; each step's dot product is split over the eight lanes
-// (exact 128-bit partial sums, reduced once, combined by shuffles), so the
-// sequential chain is one short step per row.
-constexpr int kInvThreads = 8 * kBlk;
+// outside the triangle).  Column j of the inverse solves T x = e_j by forward
+// (lower) or back (upper) substitution mod p, independently of the other
+// columns: a CTA takes kInvCols columns of one block (kBlk / kInvCols CTAs
+// per block, so that the sequential chains of many columns run on many SMs),
+// eight lanes per column; each step's dot product is split over the eight
+// lanes (exact 128-bit partial sums, reduced once, combined by shuffles), so
+// the chain is one short step per row, and it starts at the first row where
+// one of the CTA's columns has a non-zero entry.
+constexpr int kInvCols = 32;
+constexpr int kInvThreads = 8 * kInvCols;
 constexpr int kBX = kBlk + 1;  // padded column stride of the inverse in shared memory
 __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt,
                                                                   int size, int upper, int unit, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Inv, int leaf, int* err) {
     extern __shared__ uint32_t sm[];
-    // column-major with a padded stride: entry (i, j) of the inverse at sX[j*kBX + i], so that the
-    // eight lanes of a column read consecutive words (distinct banks) in the dot products below and
-    // the final copy, which walks j, spreads over the banks too
+    // this CTA's columns, column-major with a padded stride: entry (i, q kInvCols + jl) of the inverse at
+    // sX[jl*kBX + i], so that the eight lanes of a column read consecutive words (distinct banks) in the
+    // dot products below and the final copy, which walks the columns, spreads over the banks too
     uint32_t* sX = sm;
-    uint32_t* sT = sm + kBlk * kBX;              // [kBlk][kBlk]: the block of T
+    uint32_t* sT = sm + kInvCols * kBX;          // [kBlk][kBlk]: the block of T
     uint32_t* sD = sT + kBlk * kBlk;             // [kBlk] inverse diagonal
-    const int b = blockIdx.x;
+    const int b = blockIdx.x / (kBlk / kInvCols), q = blockIdx.x % (kBlk / kInvCols);
     const int base = b * kBlk;
     const int tb = min(kBlk, size - base);
     const uint32_t* Tb = T + (long long)base * ldt + base;
@@ -95,11 +99,15 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
             sD[i] = d;
         }
     }
-    for (int idx = threadIdx.x; idx < kBlk * kBX; idx += blockDim.x) sX[idx] = 0u;
+    for (int idx = threadIdx.x; idx < kInvCols * kBX; idx += blockDim.x) sX[idx] = 0u;
     __syncthreads();
-    const int j = threadIdx.x >> 3, gl = threadIdx.x & 7;
+    const int jl = threadIdx.x >> 3, gl = threadIdx.x & 7;
+    const int j = q * kInvCols + jl;
     const bool col = j < tb;
-    for (int s = 0; s < tb; ++s) {  // same trip count in every lane (shuffles below)
+    // rows above (lower) / below (upper) the CTA's first column are zero in all its columns
+    const int s0 = upper ? max(0, tb - (q + 1) * kInvCols) : q * kInvCols;
+    uint32_t* Xj = sX + jl * kBX;
+    for (int s = s0; s < tb; ++s) {  // same trip count in every lane (shuffles below)
         const int i = upper ? tb - 1 - s : s;
         const bool act = col && (upper ? i <= j : i >= j);
         Acc128 acc;
@@ -107,7 +115,6 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
             // any 32-bit word times a residue < 2^31 stays below 2^63
             const uint32_t* Ti = sT + i * kBlk;
             const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
-            const uint32_t* Xj = sX + j * kBX;
             for (int l = lo + gl; l < hi; l += 8) acc.add((unsigned long long)Ti[l] * Xj[l]);
         }
         uint32_t v = act ? acc.mod(p, mu, two64p) : 0u;
@@ -119,17 +126,17 @@ __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t
         if (act && gl == 0) {
             const uint32_t rhs = (i == j) ? 1u : 0u;
             const uint32_t t = rhs >= v ? rhs - v : rhs + (p - v);
-            sX[j * kBX + i] = mod_u64((unsigned long long)t * sD[i], p, mu);
+            Xj[i] = mod_u64((unsigned long long)t * sD[i], p, mu);
         }
         __syncwarp();
     }
     __syncthreads();
-    // dense kBlk x kBlk block (zero padding beyond tb)
+    // this CTA's columns of the dense kBlk x kBlk block (zero padding beyond tb)
     const int per = leaf / kBlk;
     uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
-    for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) {
-        const int r = idx / kBlk, c = idx % kBlk;
-        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[c * kBX + r] : 0u;
+    for (int idx = threadIdx.x; idx < kBlk * kInvCols; idx += blockDim.x) {
+        const int r = idx / kInvCols, cl = idx % kInvCols, c = q * kInvCols + cl;
+        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[cl * kBX + r] : 0u;
     }
 }
 
@@ -478,7 +485,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
     }
     // leaf inverses: zero (the other triangle), 128-blocks by substitution, then doubling
     if (cudaMemsetAsync(inv, 0, size_t(Y.nl) * Y.L * Y.L * 4, s) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const size_t smem = (size_t(kBlk) * kBX + size_t(kBlk) * kBlk + kBlk) * 4;
+    const size_t smem = (size_t(kInvCols) * kBX + size_t(kBlk) * kBlk + kBlk) * 4;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(trsm_invert_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -486,7 +493,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
             return FFGPU_ERR_CUDA;
         attr_set = true;
     }
-    const int nb = (int)((sz + kBlk - 1) / kBlk);
+    const int nb = (int)((sz + kBlk - 1) / kBlk) * (kBlk / kInvCols);  // CTAs: column groups of every block
     if (timed_launch("trsm_invert_blocks", s, [&] {
             trsm_invert_blocks<<<nb, kInvThreads, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p, inv, (int)Y.L,
                                                       err);
