@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="headline: run the default plan rules instead of the autotuned plan")
     ap.add_argument("--lqup-n", type=int, default=0,
                     help="--workload lqup: only this n (with --p), uniform matrix")
     ap.add_argument("--workload", choices=["headline", "sweep", "precision", "serve", "ftrsm", "batched", "multimod",
@@ -293,6 +295,19 @@ def run_own(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # the autotuner's plan for this shape and modulus (section 3.2.1 / 7:
+    # thresholds set by measurement), applied by ffgpu_fgemm from its cache;
+    # a plan with Winograd levels would change what the roofline counts, so
+    # the default rules stand in for one
+    plan_used = "default rules"
+    if not args.no_tune:
+        ff.autotune_clear()
+        tuned = ff.autotune(n, n, n, p)
+        if tuned["winograd_levels"] == 0:
+            plan_used = tuned
+        else:
+            ff.autotune_clear()
+            plan_used = {"default rules": "tuned plan had Winograd levels", "tuned": tuned}
     for _ in range(args.warmup):
         ff.fgemm(dA, dB, p, alpha, beta, dC)
     torch.cuda.synchronize()
@@ -378,7 +393,7 @@ def run_own(args):
             "config": {"workload": workload_name(n, p), "n": n, "p": p, "alpha": alpha, "beta": beta,
                        "channels": plan["channels"], "moduli": plan["moduli"],
                        "l2": "inputs 768 MiB > 129 MB L2: no flush between steps",
-                       "parallelism": "replicas x%d" % world},
+                       "parallelism": "replicas x%d" % world, "plan": plan_used},
             "roofline": roofline,
             "cpu_baseline": base,
             "e2e": e2e,
@@ -495,12 +510,18 @@ def run_sweep(args):
             dB = torch.from_numpy(B.view(np.int32)).cuda()
             dC = torch.from_numpy(C.view(np.int32)).cuda()
             steps = max(3, min(50, int(4e12 / (2.0 * n ** 3))))
+            ff.autotune_clear()
             ms = time_call(lambda: ff.fgemm(dA, dB, p, alpha, beta, dC), torch, steps, 2)
+            # the same point with the autotuner's plan (ffgpu_fgemm applies it from the cache)
+            tuned = ff.autotune(n, n, n, p)
+            tms = time_call(lambda: ff.fgemm(dA, dB, p, alpha, beta, dC), torch, steps, 2)
+            ff.autotune_clear()
             plan = ff.fgemm_plan(n, n, n, p)
             print(json.dumps({"workload": "sweep", "n": n, "p": p, "channels": plan["channels"],
                               "ms": ms, "GOPS": 2.0 * n ** 3 / (ms / 1e3) / 1e9,
                               "tensor_TFLOPs_incl_conversion": plan["mma_flops"] / (ms / 1e3) / 1e12,
-                              "frac_of_peak_incl_conversion": plan["mma_flops"] / (ms / 1e3) / 1e12 / peak}),
+                              "frac_of_peak_incl_conversion": plan["mma_flops"] / (ms / 1e3) / 1e12 / peak,
+                              "tuned": {"plan": tuned, "ms": tms, "GOPS": 2.0 * n ** 3 / (tms / 1e3) / 1e9}}),
                   flush=True)
             del dA, dB, dC
     return 0
@@ -671,6 +692,9 @@ def run_batched(args):
     ff.profile_enable(False)
     kern = {name: {"launches": v[0], "total_ms": round(v[1], 3)} for name, v in ff.profile_read().items()}
     dev_ms = sum(v["total_ms"] for v in kern.values())
+    # the batched launch's CUDA-core threshold measured on this batch, then the batch again
+    tuned_macs = ff.autotune_batched(descs, nd)
+    tuned_ms = time_call(lambda: ff.fgemm_batched_descs(descs, nd), torch, max(1, min(args.steps, 10)), 1)
     # the same batch as a plan captured once in a CUDA graph: one graph launch per step
     t0 = time.perf_counter()
     plan = ff.BatchedPlan(problems)
@@ -682,6 +706,8 @@ def run_batched(args):
     print(json.dumps({"workload": "batched", "instances": count, "primes": len(primes),
                       "fgemms": len(problems), "ms": ms, "GOPS": flops / (ms / 1e3) / 1e9,
                       "kernel_ms": dev_ms, "kernel_GOPS": flops / (dev_ms / 1e3) / 1e9,
+                      "tuned": {"batched_small_macs": tuned_macs, "ms": tuned_ms,
+                                "GOPS": flops / (tuned_ms / 1e3) / 1e9},
                       "host_enqueue_ms": host_ms, "python_descs_ms": marshal_ms,
                       "graph": {"ms": graph_ms, "GOPS": flops / (graph_ms / 1e3) / 1e9, "plan_create_ms": plan_ms,
                                 **info},

@@ -139,19 +139,31 @@ FFGPU_API ffgpu_status ffgpu_fgemm_ex(int64_t m, int64_t n, int64_t k, uint32_t 
 /*
  * Autotuner (the paper tunes its Winograd threshold experimentally, section
  * 3.2.1, and names self-adapting thresholds as further development, section
- * 7).  For a problem shape (bucketed to multiples of 256), modulus class
- * (number of channels) and path, ffgpu_autotune times every candidate
- * configuration on the device (tensor-core kernel variant, Winograd levels,
- * chunk length) on scratch data it allocates, and stores the fastest in an
- * in-memory plan cache.  ffgpu_fgemm_auto computes like ffgpu_fgemm_ex with the
- * cached plan (tuning first on a miss).  The cache can be saved to and loaded
- * from a JSON file.  Results never depend on the plan (every plan is exact).
+ * 7).  For a problem shape (m, n, k each bucketed to a multiple of 256), a
+ * modulus p and a path, ffgpu_autotune times every candidate plan on the
+ * device on scratch data it allocates (the route: tensor cores or, for
+ * products of at most 2^31 multiply-adds, the CUDA-core kernel; the tensor
+ * cores' tile shape, 128 x 256 on one CTA or 256 x 256 on a CTA pair; the
+ * tile order, in bands of 4, 16 or 64 tile rows; the chunk length between
+ * in-place reductions; 0-2 Winograd levels) and stores the fastest in an
+ * in-memory plan cache.  ffgpu_fgemm then runs every product of that bucket
+ * and modulus with the cached plan (Winograd levels included);
+ * ffgpu_fgemm_ws and the request server apply the plan's route, tile shape,
+ * tile order and chunk length (their workspace has no room for Winograd's
+ * temporaries); the batched launch sends an instance to the CUDA cores or the
+ * tensor cores as its cached plan says.  With an empty cache every call uses
+ * the default rules.  ffgpu_fgemm_auto computes like ffgpu_fgemm_ex with the
+ * cached plan (tuning first on a miss).  The cache can be saved to and
+ * loaded from a JSON file.  Results never depend on the plan (every plan is
+ * exact).
  */
 typedef struct {
-    int32_t kernel;            /* 0 = one-CTA 128x256 tiles, 1 = CTA-pair 256x256 tiles */
+    int32_t kernel;            /* 0 = one-CTA 128x256 tiles, 1 = CTA-pair 256x256 tiles, -1 = default rule */
     int32_t winograd_levels;
-    int32_t chunk_steps;       /* 64-long k-steps between in-place reductions */
-    int32_t reserved[5];
+    int32_t chunk_steps;       /* 64-long k-steps between in-place reductions (0 = longest exact) */
+    int32_t route;             /* 0 = tensor cores, 1 = CUDA-core kernel, -1 = default size rule */
+    int32_t raster_rows;       /* tile rows per band of the tile order (0 = 16) */
+    int32_t reserved[3];
     double ms;                 /* measured time of the plan */
 } ffgpu_tuned;
 
@@ -368,6 +380,19 @@ typedef struct {
  * anything is enqueued.
  */
 FFGPU_API ffgpu_status ffgpu_fgemm_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream);
+
+/*
+ * The batched launch's own threshold: products of at most that many
+ * multiply-adds (2^23 by default) run in the grouped CUDA-core launch, the
+ * rest in grouped tensor-core launches.  ffgpu_autotune_batched times this
+ * batch (as ffgpu_fgemm_batched would run it) for thresholds 2^20 .. 2^26,
+ * keeps the fastest for every later batched call (and in saved plan files),
+ * and returns it in *best_macs.  Every descriptor's C receives alpha A B
+ * (beta is taken as 0 so that the repeated runs agree): call it before the
+ * real computation.  Synchronous.
+ */
+FFGPU_API ffgpu_status ffgpu_autotune_batched(int64_t count, const ffgpu_fgemm_desc* descs, void* stream,
+                                              int64_t* best_macs);
 
 /*
  * Batched plan: the launch sequence of ffgpu_fgemm_batched for one fixed

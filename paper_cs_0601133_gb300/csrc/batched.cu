@@ -3,6 +3,7 @@
 // wave.  Host side only: plans, placement of every instance's channel planes in
 // per-k pools, cost-balanced job lists, tables copied to the device.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <functional>
@@ -423,7 +424,17 @@ ffgpu_status run_wave(std::vector<BInst>& w, cudaStream_t s, int sms, void* ws_i
 // output tile (the tensor-core route would spend a whole 128 x 256 tile and
 // its reconstruction on each).  Tables: the job records, then the tile -> job
 // map.
-constexpr int64_t kBatchSmallMacs = int64_t(1) << 23;  // measured best for the multi-modular batch (2^19 .. 2^24)
+// Products of at most this many multiply-adds take the grouped CUDA-core
+// launch: 2^23 measured best for the multi-modular batch (2^19 .. 2^24);
+// ffgpu_autotune_batched re-measures it for a given batch.
+static std::atomic<int64_t> g_batch_small_macs{int64_t(1) << 23};
+
+}  // namespace
+
+int64_t batched_small_macs() { return g_batch_small_macs.load(); }
+void set_batched_small_macs(int64_t macs) { g_batch_small_macs.store(macs < 0 ? 0 : macs); }
+
+namespace {
 
 // Two launches by tile size: products with a dimension of at most 32 on
 // 32 x 32 tiles (less padding), the others on 64 x 64 tiles.  Tables: per size
@@ -517,11 +528,16 @@ void split_batch(int64_t count, const ffgpu_fgemm_desc* descs, std::vector<std::
     std::vector<BInst> wave;
     std::unordered_set<int64_t> wave_k;
     size_t wave_bytes = 0;
-    const int64_t small_limit = std::min<int64_t>(kBatchSmallMacs, small_threshold());
+    const int64_t small_limit = std::min<int64_t>(g_batch_small_macs.load(), small_threshold());
     for (int64_t i = 0; i < count; ++i) {
         const ffgpu_fgemm_desc& d = descs[i];
         if (d.m == 0 || d.n == 0) continue;
-        if (small && d.k > 0 && double(d.m) * double(d.n) * double(d.k) <= double(small_limit)) {
+        // a cached plan for the instance's shape bucket and modulus decides its
+        // route; otherwise the size rule
+        const int tuned_route = autotune_route(d.m, d.n, d.k, d.p);
+        const bool to_small = tuned_route >= 0 ? tuned_route == 1
+                                               : double(d.m) * double(d.n) * double(d.k) <= double(small_limit);
+        if (small && d.k > 0 && to_small) {
             small->d.push_back(&d);
             continue;
         }

@@ -436,6 +436,7 @@ ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t
         P.slots = wsb + L.slots;
         P.slot_stride = slot_stride_for(pl.nch);
         P.err = err;
+        P.raster = g_tune_override.raster > 0 ? g_tune_override.raster : kRasterRows;
         if (pair) {
             const int pgrid = 2 * std::max(1, std::min(std::min(P.num_tiles, grid / 2), rns_gemm_pair_max_clusters()));
             if (launch("rns_gemm_pair", [&] { return launch_rns_gemm_pair(mapA, mapB, P, pgrid, s); }) != cudaSuccess)
@@ -519,6 +520,12 @@ ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
                             size_t workspace_bytes, void* stream) {
     ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
     if (st != FFGPU_OK || m == 0 || n == 0) return st;
+    // a cached plan's kernel, chunk, route and tile order (its Winograd depth
+    // needs workspace beyond the caller's and is not applied here)
+    TuneOverride tuned;
+    int levels = 0;
+    const bool have = k > 0 && autotune_settings(m, n, k, p, tuned, levels);
+    ScopedTune scope(have ? tuned : g_tune_override);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pool* pool = nullptr;
     st = pool_get(s, 0, &pool);
@@ -537,6 +544,14 @@ ffgpu_status ffgpu_fgemm(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t a
     ffgpu_status st = check_args(m, n, k, p, A, lda, B, ldb, C, ldc);
     if (st != FFGPU_OK || m == 0 || n == 0) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the plan cache (filled by ffgpu_autotune or ffgpu_autotune_load): its
+    // kernel, chunk, route, tile order and Winograd depth for this shape
+    // bucket and modulus, when it holds one
+    TuneOverride tuned;
+    int levels = 0;
+    const bool have = k > 0 && autotune_settings(m, n, k, p, tuned, levels);
+    ScopedTune scope(have ? tuned : g_tune_override);
+    if (have && levels > 0) return fgemm_ex_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, 0, levels, s);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return FFGPU_ERR_CUDA;
     const size_t need = fgemm_ws_bytes(m, n, k, p, sm_count(dev));

@@ -87,6 +87,7 @@ struct RnsGemmParams {
     unsigned char* slots;          // per-CTA residue slots: 2 x slot_stride bytes per CTA
     size_t slot_stride;            // bytes of one slot: channels x 128 x 256
     int* err;                      // device error word
+    int raster;                    // tile rows per band of the tile order (> 0)
 };
 
 // Grouped launch: jobs (instance, tile, channel), listed per CTA, with
@@ -169,13 +170,34 @@ cudaError_t launch_rns_gemm_pair(const CUtensorMap& mapA, const CUtensorMap& map
                                  int grid, cudaStream_t s);
 bool use_pair_kernel(int64_t m, int grid);
 
-// Autotuner overrides for the calling thread (autotune.cu): kernel 0 = one-CTA,
-// 1 = CTA pair, -1 = default choice; chunk_steps > 0 caps the chunk length.
+// Plan settings for the calling thread (autotune.cu): set while a tuned plan
+// or a tuning candidate runs.
+//   kernel       0 = one-CTA kernel (128 x 256 tiles), 1 = CTA pair (256 x 256), -1 = default choice
+//   chunk_steps  > 0 caps the chunk length between in-place reductions
+//   route        0 = tensor cores, 1 = CUDA-core kernel, -1 = the size rule (fgemm_small)
+//   raster       tile rows per band of the tile order (0 = kRasterRows)
 struct TuneOverride {
     int kernel = -1;
     int chunk_steps = 0;
+    int route = -1;
+    int raster = 0;
 };
 extern thread_local TuneOverride g_tune_override;
+// Installs a plan's settings for the calling thread until the scope ends.
+struct ScopedTune {
+    TuneOverride saved;
+    explicit ScopedTune(const TuneOverride& t) : saved(g_tune_override) { g_tune_override = t; }
+    ~ScopedTune() { g_tune_override = saved; }
+};
+// The cached plan for a product (path 0), if the plan cache holds one for its
+// shape bucket and modulus: its settings and Winograd depth.
+bool autotune_settings(int64_t m, int64_t n, int64_t k, uint32_t p, TuneOverride& o, int& levels);
+// Route the cache gives a product (-1: no entry, 0 tensor cores, 1 CUDA cores).
+int autotune_route(int64_t m, int64_t n, int64_t k, uint32_t p);
+// Largest product (multiply-adds) the batched launch sends to the grouped CUDA-core kernel.
+int64_t batched_small_macs();
+void set_batched_small_macs(int64_t macs);
+constexpr int kRasterRows = 16;  // default tile rows per band of the tile order
 int rns_gemm_pair_max_clusters();
 size_t rns_gemm_smem_bytes();
 

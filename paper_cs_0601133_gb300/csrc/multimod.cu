@@ -314,6 +314,7 @@ ffgpu_status int_gemm_run(int64_t m, int64_t n, int64_t k, int bits, const int32
     P.slots = w + o_slots;
     P.slot_stride = size_t(pl.nch) * kTileM * kTileN;
     P.err = err;
+    P.raster = kRasterRows;
     return timed_launch("rns_gemm_int", s, [&] { return launch_rns_gemm_int(mapA, mapB, P, grid, s); }) ==
                    cudaSuccess
                ? FFGPU_OK

@@ -48,17 +48,18 @@ constexpr uint32_t kABytes = kTileM * kTileK * 2;
 constexpr uint32_t kBBytes = kTileN * kTileK * 2;
 constexpr uint32_t kStageBytes = kABytes + kBBytes;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kGroupM = 16;  // tile rasterisation: bands of 16 tile rows
 // per-instance constants of the reconstruction (see stage_consts): one copy for
 // the combine warps, one per epilogue warp
 constexpr size_t kConstBytes = size_t(1 + kEpiWarps) * kMaxChannels * 16;
 constexpr size_t kSmemBytes = 1024 + size_t(kStages) * kStageBytes + kConstBytes + 256;
 
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
-    const int per_group = kGroupM * tiles_n;
+// Tile order: bands of `band` tile rows, column by column within a band (the
+// tiles running at once share B columns and A rows in L2).
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int band, int& tm, int& tn) {
+    const int per_group = band * tiles_n;
     const int g = t / per_group;
-    const int first = g * kGroupM;
-    const int gm = min(tiles_m - first, kGroupM);
+    const int first = g * band;
+    const int gm = min(tiles_m - first, band);
     const int r = t - g * per_group;
     tm = first + r % gm;
     tn = r / gm;
@@ -390,7 +391,7 @@ struct SingleSched {
                        ? (P.num_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
                        : 0;
         H = (P.inst.ksteps + P.inst.chunk_steps - 1) / P.inst.chunk_steps;
-        if (my_tiles > 0) tile_coords((int)blockIdx.x, P.tiles_m, P.tiles_n, tm, tn);
+        if (my_tiles > 0) tile_coords((int)blockIdx.x, P.tiles_m, P.tiles_n, P.raster, tm, tn);
     }
     __device__ int num_jobs() const { return my_tiles * P.inst.nch; }
     __device__ void fill(Job& d, int tile_ord, int ch, int tm_, int tn_) const {
@@ -416,12 +417,12 @@ struct SingleSched {
         fill(d, ti, c, tm, tn);
         if (++c == P.inst.nch) {
             c = 0;
-            if (++ti < my_tiles) tile_coords((int)blockIdx.x + ti * (int)gridDim.x, P.tiles_m, P.tiles_n, tm, tn);
+            if (++ti < my_tiles) tile_coords((int)blockIdx.x + ti * (int)gridDim.x, P.tiles_m, P.tiles_n, P.raster, tm, tn);
         }
     }
     __device__ void last_job(Job& d) const {
         int a, b;
-        tile_coords((int)blockIdx.x + (my_tiles - 1) * (int)gridDim.x, P.tiles_m, P.tiles_n, a, b);
+        tile_coords((int)blockIdx.x + (my_tiles - 1) * (int)gridDim.x, P.tiles_m, P.tiles_n, P.raster, a, b);
         fill(d, my_tiles - 1, P.inst.nch - 1, a, b);
     }
     __device__ unsigned char* slots() const { return P.slots; }
@@ -845,7 +846,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t issued = 0, last_parity = 0;
             bool ok = true;
             int it_t = 0, it_c = 0, tm = 0, tn = 0;  // job iterator: tile ordinal, channel
-            if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, tm, tn);
+            if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
                 int jc[2], jrA[2], jrB[2];
@@ -855,7 +856,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     jrB[s] = tn * kPairTile + (int)rank * 128;
                     if (++it_c == nch) {
                         it_c = 0;
-                        if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, tm, tn);
+                        if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
                     }
                 }
                 for (int h = 0; h < H && ok; ++h) {
@@ -1012,7 +1013,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
             const int ti = my_tiles - 1;
             int tm, tn;
-            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
+            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             uint4* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(I, kcw, lane);
             if (mbar_wait(&slot_full[ti & 1], (uint32_t)(ti >> 1) & 1u, abort_flag, err, kDevTimeoutEpilogue))
@@ -1031,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[slot] ^= 1u;
             int tm, tn;
-            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, tm, tn);
+            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
             combine_block<false>(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
                           size_t(kTileM) * kTileN, cw, ti == my_tiles - 1 ? kCombineWarps + kEpiWarps : kCombineWarps,

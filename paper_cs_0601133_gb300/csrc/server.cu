@@ -151,8 +151,16 @@ struct Server {
                 cudaMemcpy2DAsync(dC, r.n * 4, r.C_in, r.ldc_in * 4, r.n * 4, r.m, cudaMemcpyHostToDevice, s);
             else
                 cudaMemsetAsync(dC, 0, size_t(r.m) * r.n * 4, s);
-            st = fgemm_run(r.m, r.n, r.k, r.p, r.alpha, dA, std::max<int64_t>(r.k, 1), dB, r.n, r.beta, dC, r.n, ws,
-                           ws_bytes, errs[si], s, 0, false);
+            {
+                // the request's cached plan, if any (kernel, chunk, route, tile order; the
+                // arena block holds no room for Winograd's temporaries)
+                TuneOverride tuned;
+                int levels = 0;
+                const bool have = r.k > 0 && autotune_settings(r.m, r.n, r.k, r.p, tuned, levels);
+                ScopedTune scope(have ? tuned : g_tune_override);
+                st = fgemm_run(r.m, r.n, r.k, r.p, r.alpha, dA, std::max<int64_t>(r.k, 1), dB, r.n, r.beta, dC, r.n,
+                               ws, ws_bytes, errs[si], s, 0, false);
+            }
             cudaMemcpy2DAsync(r.out, r.ldo * 4, dC, r.n * 4, r.n * 4, r.m, cudaMemcpyDeviceToHost, s);
         } else {
             const int64_t nt = r.side == 0 ? r.m : r.n;

@@ -197,10 +197,11 @@ void set_small_threshold(int64_t macs) { g_small_macs.store(macs < 0 ? 0 : macs)
 int64_t small_threshold() { return g_small_macs.load(); }
 
 bool fgemm_small(int64_t m, int64_t n, int64_t k) {
+    const bool fits = k > 0 && k < (int64_t(1) << 31) && m <= int64_t(65535) * kSmT;
+    if (g_tune_override.route >= 0) return fits && g_tune_override.route == 1;  // a tuned plan's route
     if (g_tune_override.kernel >= 0) return false;
     const double macs = double(m) * double(n) * double(k);
-    return k > 0 && macs <= double(g_small_macs.load()) && k < (int64_t(1) << 31) &&
-           m <= int64_t(65535) * kSmT;
+    return fits && macs <= double(g_small_macs.load());
 }
 
 void small_job(SmallJob& J, const ffgpu_fgemm_desc& d, int tile0, int tile) {

@@ -79,7 +79,8 @@ class ServerStats(ctypes.Structure):
 
 class Tuned(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("winograd_levels", ctypes.c_int32),
-                ("chunk_steps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5), ("ms", ctypes.c_double)]
+                ("chunk_steps", ctypes.c_int32), ("route", ctypes.c_int32), ("raster_rows", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3), ("ms", ctypes.c_double)]
 
 
 class FgemmDesc(ctypes.Structure):
@@ -138,6 +139,7 @@ SIGNATURES = {
     "ffgpu_autotune_save": [ctypes.c_char_p],
     "ffgpu_autotune_load": [ctypes.c_char_p],
     "ffgpu_autotune_clear": [],
+    "ffgpu_autotune_batched": [_I64, ctypes.POINTER(FgemmDesc), _VP, ctypes.POINTER(ctypes.c_int64)],
     "ffgpu_fgemm_auto": [_I64, _I64, _I64, _U32, _U32, _VP, _I64, _VP, _I64, _U32, _VP, _I64, _I32, _VP],
     "ffgpu_profile_enable": [_I32],
     "ffgpu_profile_read": [ctypes.POINTER(KernelTime), _I32, ctypes.POINTER(ctypes.c_int)],
@@ -622,9 +624,23 @@ class Server:
         self.close()
 
 
+_KERNELS = {-1: "default", 0: "single", 1: "pair"}
+_ROUTES = {-1: "default", 0: "tensor", 1: "cuda_cores"}
+
+
 def _tuned(t: "Tuned") -> dict:
-    return dict(kernel=("single", "pair")[t.kernel] if t.kernel in (0, 1) else t.kernel,
-                winograd_levels=t.winograd_levels, chunk_steps=t.chunk_steps, ms=t.ms)
+    return dict(kernel=_KERNELS.get(t.kernel, t.kernel), winograd_levels=t.winograd_levels,
+                chunk_steps=t.chunk_steps, route=_ROUTES.get(t.route, t.route), raster_rows=t.raster_rows,
+                ms=t.ms)
+
+
+def autotune_batched(descs, count: int, stream=None) -> int:
+    """Time the batch (a prebuilt descriptor array, see batched_descs) for the
+    batched launch's CUDA-core threshold; keep and return the fastest.  Every
+    C receives alpha*A@B (beta taken as 0)."""
+    out = ctypes.c_int64(0)
+    check(lib().ffgpu_autotune_batched(count, descs, _stream_ptr(stream), ctypes.byref(out)), "autotune_batched")
+    return out.value
 
 
 def autotune(m: int, n: int, k: int, p: int, path: str = "rns", stream=None) -> dict:
