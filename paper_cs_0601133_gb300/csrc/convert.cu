@@ -210,6 +210,79 @@ __global__ void __launch_bounds__(256) scale_kernel(uint32_t* C, long long ldc, 
     }
 }
 
+// The word at (r, c) of a signed sum of blocks, reduced mod p: each term's
+// word reduced by the 32-bit Barrett step of residues8, added (or its
+// negative added) modulo p; the result is a canonical residue.
+__device__ __forceinline__ uint32_t sum_at(const SumSrc& S, long long r, int c, uint32_t p, uint32_t mu32) {
+    uint32_t acc = 0u;
+    for (int t = 0; t < S.n; ++t) {
+        const uint32_t x = __ldg(S.X[t] + r * S.ld[t] + c);
+        const uint32_t q = __umulhi(x, mu32);
+        uint32_t v = x - q * p;
+        if (v >= p) v -= p;
+        if (S.neg[t] && v != 0u) v = p - v;
+        acc += v;  // both below p < 2^31: no wrap
+        if (acc >= p) acc -= p;
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(256) convert_rows_sum_kernel(const __grid_constant__ SumSrc S, int rows, int cols,
+                                                               int colsp, const __grid_constant__ ConvertParams cp,
+                                                               uint4* __restrict__ planes) {
+    const size_t plane16 = (size_t)rows * colsp / 8;
+    const long long gpr = colsp / 8;
+    const long long total = (long long)rows * gpr;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(g / gpr);
+        const int c0 = (int)(g % gpr) * 8;
+        uint32_t x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = (c0 + e < cols) ? sum_at(S, r, c0 + e, cp.p, cp.mu32) : 0u;
+        residues8(cp, x, planes + ((size_t)r * colsp + c0) / 8, plane16);
+    }
+}
+
+__global__ void __launch_bounds__(256) convert_transpose_sum_kernel(const __grid_constant__ SumSrc S, int rows,
+                                                                    int cols, int rowsp,
+                                                                    const __grid_constant__ ConvertParams cp,
+                                                                    uint4* __restrict__ planes) {
+    __shared__ uint32_t tile[64][65];
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+#pragma unroll 1
+    for (int i = 0; i < 16; ++i) {
+        const int idx = threadIdx.x + 256 * i;
+        const int rr = idx >> 6, cc = idx & 63;
+        const int gr = r0 + rr, gc = c0 + cc;
+        tile[rr][cc] = (gr < rows && gc < cols) ? sum_at(S, gr, gc, cp.p, cp.mu32) : 0u;
+    }
+    __syncthreads();
+    const size_t plane16 = (size_t)cols * rowsp / 8;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        const int w = threadIdx.x + 256 * it;
+        const int cl = w >> 3, g = w & 7;
+        const int gc = c0 + cl;
+        if (gc >= cols) continue;
+        uint32_t x[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[e] = tile[g * 8 + e][cl];
+        residues8(cp, x, planes + ((size_t)gc * rowsp + r0 + g * 8) / 8, plane16);
+    }
+}
+
+__global__ void __launch_bounds__(256) sum_mod_kernel(const __grid_constant__ SumSrc S, int rows, int cols,
+                                                      uint32_t p, uint32_t mu32, uint32_t* __restrict__ Z,
+                                                      long long ldz) {
+    const long long total = (long long)rows * cols;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(g / cols), c = (int)(g - (long long)r * cols);
+        Z[(long long)r * ldz + c] = sum_at(S, r, c, p, mu32);
+    }
+}
+
 int grid_for(long long work, int per_block) {
     long long g = (work + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -235,6 +308,29 @@ cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows,
     dim3 grid((cols + 63) / 64, rowsp / 64);
     convert_transpose_kernel<<<grid, 256, 0, s>>>(X, ldx, rows, cols, rowsp, cp,
                                                    static_cast<uint4*>(planes));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_rows_sum(const SumSrc& X, int rows, int cols, int colsp, const ConvertParams& cp,
+                                    void* planes, cudaStream_t s) {
+    if (rows == 0 || colsp == 0) return cudaSuccess;
+    const long long work = (long long)rows * (colsp / 8);
+    convert_rows_sum_kernel<<<grid_for(work, 256), 256, 0, s>>>(X, rows, cols, colsp, cp, static_cast<uint4*>(planes));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_transpose_sum(const SumSrc& X, int rows, int cols, int rowsp, const ConvertParams& cp,
+                                         void* planes, cudaStream_t s) {
+    if (cols == 0 || rowsp == 0) return cudaSuccess;
+    dim3 grid((cols + 63) / 64, rowsp / 64);
+    convert_transpose_sum_kernel<<<grid, 256, 0, s>>>(X, rows, cols, rowsp, cp, static_cast<uint4*>(planes));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_mod(const SumSrc& X, int rows, int cols, uint32_t p, uint32_t* Z, long long ldz,
+                           cudaStream_t s) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    sum_mod_kernel<<<grid_for((long long)rows * cols, 256), 256, 0, s>>>(X, rows, cols, p, 0xFFFFFFFFu / p, Z, ldz);
     return cudaGetLastError();
 }
 

@@ -368,10 +368,33 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
     return fgemm_run_rns(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, ws, ws_bytes, err, s, max_grid, untimed);
 }
 
+static SumSrc single_src(const uint32_t* X, int64_t ld) {
+    SumSrc S;
+    std::memset(&S, 0, sizeof(S));
+    S.X[0] = X;
+    S.ld[0] = ld;
+    S.n = 1;
+    return S;
+}
+
+// The sum with every block shifted by (r rows, c columns).
+static SumSrc shifted(const SumSrc& S, int64_t r, int64_t c) {
+    SumSrc T = S;
+    for (int t = 0; t < S.n; ++t) T.X[t] = S.X[t] + r * S.ld[t] + c;
+    return T;
+}
+
 ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,
                            const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                            uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                            int* err, cudaStream_t s, int max_grid, bool untimed) {
+    return fgemm_run_rns_src(m, n, k, p, alpha, single_src(A, lda), single_src(B, ldb), beta, C, ldc, ws, ws_bytes,
+                             err, s, max_grid, untimed);
+}
+
+ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const SumSrc& A,
+                               const SumSrc& B, uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                               int* err, cudaStream_t s, int max_grid, bool untimed) {
     const unsigned long long mu = barrett_mu(p);
     auto launch = [&](const char* name, auto&& f) { return untimed ? f() : timed_launch(name, s, f); };
     const uint32_t al = alpha % p;
@@ -408,15 +431,31 @@ ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t
             cp.mod[c] = pl.mod[c];
             cp.magic32[c] = (uint32_t)(((1ull << 39) + pl.mod[c] - 1) / pl.mod[c]);
         }
-        if (launch("convert_rows", [&] {
-                return launch_convert_rows(A + k0, lda, (int)m, (int)ks, (int)kp, cp, wsb + L.planesA, s);
-            }) != cudaSuccess)
+        // one term: the caller's matrix; several: Winograd's pre-additions,
+        // summed mod p inside the conversion
+        if (A.n == 1) {
+            if (launch("convert_rows", [&] {
+                    return launch_convert_rows(A.X[0] + k0, A.ld[0], (int)m, (int)ks, (int)kp, cp, wsb + L.planesA, s);
+                }) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+        } else if (launch("convert_rows_sum", [&] {
+                       return launch_convert_rows_sum(shifted(A, 0, k0), (int)m, (int)ks, (int)kp, cp,
+                                                      wsb + L.planesA, s);
+                   }) != cudaSuccess) {
             return FFGPU_ERR_CUDA;
-        if (launch("convert_transpose", [&] {
-                return launch_convert_transpose(B + k0 * ldb, ldb, (int)ks, (int)n, (int)kp, cp, wsb + L.planesB,
-                                                s);
-            }) != cudaSuccess)
+        }
+        if (B.n == 1) {
+            if (launch("convert_transpose", [&] {
+                    return launch_convert_transpose(B.X[0] + k0 * B.ld[0], B.ld[0], (int)ks, (int)n, (int)kp, cp,
+                                                    wsb + L.planesB, s);
+                }) != cudaSuccess)
+                return FFGPU_ERR_CUDA;
+        } else if (launch("convert_transpose_sum", [&] {
+                       return launch_convert_transpose_sum(shifted(B, k0, 0), (int)ks, (int)n, (int)kp, cp,
+                                                           wsb + L.planesB, s);
+                   }) != cudaSuccess) {
             return FFGPU_ERR_CUDA;
+        }
 
         // CTA-pair kernel (256 x 256 tiles) unless the problem has a single row
         // block or the caller forces the one-CTA kernel

@@ -148,6 +148,19 @@ struct ConvJob {
     ConvertParams cp;
 };
 
+// An operand given as a signed sum of up to kMaxTerms blocks of the same
+// shape, sum_t (-1)^neg[t] X_t mod p (entries any uint32 words): the pre-added
+// operands of Winograd's levels (S1..S4, T1..T4 of Table 2 and, two levels
+// deep, their quadrants' sums), converted to channel planes in one pass
+// without being written out.
+constexpr int kMaxTerms = 16;
+struct SumSrc {
+    const uint32_t* X[kMaxTerms];
+    long long ld[kMaxTerms];
+    uint32_t neg[kMaxTerms];
+    int n;
+};
+
 // host launchers (implemented in the .cu files)
 long long convert_rows_grouped_blocks(int rows_pad);
 long long convert_transpose_grouped_blocks(int cols_pad, int kp);
@@ -161,6 +174,14 @@ cudaError_t launch_convert_transpose(const uint32_t* X, long long ldx, int rows,
                                      const ConvertParams& cp, void* planes, cudaStream_t s);
 cudaError_t launch_scale(uint32_t* C, long long ldc, int m, int n, uint32_t p, uint32_t beta,
                          unsigned long long mu, cudaStream_t s);
+// the same conversions with the words formed as a signed sum of blocks
+cudaError_t launch_convert_rows_sum(const SumSrc& X, int rows, int cols, int colsp, const ConvertParams& cp,
+                                    void* planes, cudaStream_t s);
+cudaError_t launch_convert_transpose_sum(const SumSrc& X, int rows, int cols, int rowsp, const ConvertParams& cp,
+                                         void* planes, cudaStream_t s);
+// Z = the sum (rows x cols) mod p, written out (canonical residues)
+cudaError_t launch_sum_mod(const SumSrc& X, int rows, int cols, uint32_t p, uint32_t* Z, long long ldz,
+                           cudaStream_t s);
 cudaError_t launch_rns_gemm(const CUtensorMap& mapA, const CUtensorMap& mapB,
                             const RnsGemmParams& prm, int grid, cudaStream_t s);
 cudaError_t launch_rns_gemm_grouped(const GroupGemmParams& prm, int grid, cudaStream_t s, bool int_out = false);
@@ -224,6 +245,10 @@ ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t
                            const uint32_t* A, int64_t lda, const uint32_t* B, int64_t ldb,
                            uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                            int* err, cudaStream_t s, int max_grid, bool untimed);
+// The tensor-core route with operands given as sums of blocks.
+ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const SumSrc& A,
+                               const SumSrc& B, uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
+                               int* err, cudaStream_t s, int max_grid, bool untimed);
 // small contractions on the CUDA cores (small_gemm.cu)
 bool fgemm_small(int64_t m, int64_t n, int64_t k);
 void set_small_threshold(int64_t macs);

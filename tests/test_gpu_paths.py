@@ -175,3 +175,25 @@ def test_winograd_levels_on_worst_case_inputs(path, p, levels):
     A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, h, h)
     got = run(A, B, C, p, 1, 1, path, levels)
     assert np.array_equal(got, closed_form(s, t, k, h, p, 1, 1, C))
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("threshold", [0, 2**30])
+def test_fused_pre_additions_on_both_routes(levels, threshold):
+    """The residue path's Winograd levels pass S1..S4 and T1..T4 down as sums
+    of quadrants, summed inside the conversions; sub-products small enough
+    for the CUDA cores have their sums written out first.  Threshold 0: every
+    sub-product on the tensor cores; 2^30: every one on the CUDA cores.  Odd
+    dimensions at both levels (peeling with summed operands)."""
+    p = 2147483647
+    rng = W.rng_for("precision", 60, levels, threshold % 1000)
+    m, k, n = 523, 611, 457
+    A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    old = ff.get_small_threshold()
+    ff.set_small_threshold(threshold)
+    try:
+        got = run(A, B, C, p, alpha, beta, "rns", levels)
+    finally:
+        ff.set_small_threshold(old)
+    assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
