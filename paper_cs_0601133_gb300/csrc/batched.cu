@@ -89,9 +89,19 @@ unsigned char* stage_get(size_t bytes, int* idx) {
     return b.p;
 }
 
+// Called with g_stage_mu held, right after the copy from buffer idx was
+// enqueued on s.  If the event cannot be recorded (for instance on a stream of
+// another device), the copy is waited for here instead, so that the next
+// stage_get cannot overwrite a buffer a copy still reads.
 void stage_done(int idx, cudaStream_t s) {
     StageBuf& b = stage_set().buf[idx];
-    if (cudaEventRecord(b.ev, s) == cudaSuccess) b.pending = true;
+    if (cudaEventRecord(b.ev, s) == cudaSuccess) {
+        b.pending = true;
+        return;
+    }
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    b.pending = false;
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

@@ -6,11 +6,13 @@
 // pre-additions S1..S4, T1..T4 and the post-additions are elementwise kernels
 // mod p (so, unlike the paper's delayed version, intermediate values do not
 // grow: Theorem 3.1's bound is not needed), the seven products recurse.
-// On the residue-number-system path (up to two levels) the pre-additions are
-// not written out at all: each product's operands are passed down as signed
-// sums of quadrants of A and B (S4 = A12 - A21 - A22 + A11, ...), summed mod p
-// inside the conversion that writes the product's channel planes, so a level
-// costs its seven products' conversions and the post-additions only.
+// On the residue-number-system path the last level's pre-additions are not
+// written out at all: each product's operands are passed down as signed sums
+// of quadrants (S4 = A12 - A21 - A22 + A11, ...), summed mod p inside the
+// conversion that writes the product's channel planes, so that level costs its
+// seven products' conversions and the post-additions only.  (Fusing two levels
+// was measured slower: the deepest operands are sums of up to 16 blocks, each
+// read by every product that uses it.)
 // Row 16 is taken with A22 (P4 = alpha*A22*T4 - beta*C21), the reading under
 // which the schedule computes A*B.  Odd dimensions are handled by dynamic
 // peeling (appendix, "case of an arbitrary k"): the even top-left block by
@@ -127,10 +129,19 @@ ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, cons
         if (st_ != FFGPU_OK) return st_;      \
     } while (0)
 
+SumSrc src_of(const uint32_t* X, int64_t ld);
+ffgpu_status wino_src(WinoCtx& c, int level, int64_t m, int64_t n, int64_t k, uint32_t al, const SumSrc& A,
+                      const SumSrc& B, uint32_t be, uint32_t* C, int64_t ldc, size_t tmp_off);
+
 ffgpu_status wino(WinoCtx& c, int level, int64_t m, int64_t n, int64_t k, uint32_t al, const uint32_t* A,
                   int64_t lda, const uint32_t* B, int64_t ldb, uint32_t be, uint32_t* C, int64_t ldc,
                   size_t tmp_off) {
     if (level == 0 || m < 2 || n < 2 || k < 2) return base(c, m, n, k, al, A, lda, B, ldb, be, C, ldc);
+    // the residue path's last level: pre-additions summed inside the conversions
+    // (deeper sums would read up to 4^levels blocks per entry; the levels above
+    // write their S and T out once)
+    if (c.path == 0 && level == 1)
+        return wino_src(c, 1, m, n, k, al, src_of(A, lda), src_of(B, ldb), be, C, ldc, tmp_off);
     const int64_t m2 = m & ~int64_t(1), n2 = n & ~int64_t(1), k2 = k & ~int64_t(1);
     if (m2 != m || n2 != n || k2 != k) {  // dynamic peeling
         FF_TRY(wino(c, level, m2, n2, k2, al, A, lda, B, ldb, be, C, ldc, tmp_off));
@@ -295,10 +306,6 @@ ffgpu_status wino_src(WinoCtx& c, int level, int64_t m, int64_t n, int64_t k, ui
     return FFGPU_OK;
 }
 
-// Levels whose operand sums stay within kMaxTerms blocks (4^levels terms at
-// the deepest products): the fused schedule.
-constexpr int kMaxFusedLevels = 2;
-
 }  // namespace
 
 ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha, const uint32_t* A,
@@ -323,11 +330,7 @@ ffgpu_status fgemm_ex_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t 
     c.need_fg = 0;
     c.need_tmp = 0;
     const uint32_t al = alpha % p, be = beta % p;
-    const bool fused = path == 0 && levels <= kMaxFusedLevels;
-    auto run = [&]() {
-        return fused ? wino_src(c, levels, m, n, k, al, src_of(A, lda), src_of(B, ldb), be, C, ldc, 0)
-                     : wino(c, levels, m, n, k, al, A, lda, B, ldb, be, C, ldc, 0);
-    };
+    auto run = [&]() { return wino(c, levels, m, n, k, al, A, lda, B, ldb, be, C, ldc, 0); };
     FF_TRY(run());
     const size_t fg = (c.need_fg + 255) & ~size_t(255);
     Pool* pool = nullptr;

@@ -17,6 +17,11 @@
 // product).  alpha and beta are applied with the final reduction:
 // C = (alpha (A B mod p) + beta C) mod p.
 //
+// Leaves of at least 2^24 multiply-adds run on the tensor cores as exact
+// integer products (the integer mode of the residue-number-system kernel,
+// channels sized for operands below 2^bits, bits from the 4^l growth of the
+// operands), the smaller ones on the CUDA cores in int64.
+//
 // This is the variant the paper analyses, kept for fidelity: on this GPU the
 // reductions it saves are free inside the memory-bound addition kernels, so
 // the default route reduces mod p at every level (winograd.cu).
@@ -153,6 +158,9 @@ struct ZCtx {
     size_t used, cap;
     bool dry;              // size the workspace only
     size_t peak;
+    int bits;              // the leaves' operands are below 2^bits in magnitude (31: CUDA cores only)
+    int sms;
+    int* err;
 };
 
 template <class T>
@@ -164,9 +172,44 @@ T* zalloc(ZCtx& c, int64_t count) {
     return p;
 }
 
+// C = -C (int64).
+__global__ void zneg64_kernel(int rows, int cols, long long* C, long long ldc) {
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), q = (int)(e - (long long)r * cols);
+        C[r * ldc + q] = -C[r * ldc + q];
+    }
+}
+
+// Leaves at least this large (multiply-adds) go to the tensor cores as exact
+// integer products (the integer mode of the residue-number-system kernel).
+constexpr double kZTensorMacs = double(int64_t(1) << 24);
+
 ffgpu_status zgemm(ZCtx& c, int64_t m, int64_t n, int64_t k, const int32_t* A, int64_t lda, const int32_t* B,
                    int64_t ldb, long long* C, int64_t ldc, int b) {
-    if (c.dry || m == 0 || n == 0) return FFGPU_OK;  // k = 0 leaves C = b C
+    if (m == 0 || n == 0) return FFGPU_OK;  // k = 0 leaves C = b C
+    if (k > 0 && c.bits <= 30 && double(m) * double(n) * double(k) >= kZTensorMacs) {
+        // the exact product X = A B on the tensor cores, written (b = 0) or
+        // added (b = 1) to C; b = -1 negates C first.  Exact: every value is
+        // within Theorem 3.1's bound, below 2^62.
+        const size_t mark = c.used;
+        const size_t wsb = int_gemm_ws_bytes(m, n, k, c.bits, c.sms);
+        unsigned char* ws = zalloc<unsigned char>(c, (int64_t)wsb);
+        ffgpu_status st = FFGPU_OK;
+        if (!c.dry) {
+            if (b == -1 && timed_launch("winograd_z_add", c.s, [&] {
+                    zneg64_kernel<<<blocks_for(m * n), 256, 0, c.s>>>((int)m, (int)n, C, ldc);
+                    return cudaGetLastError();
+                }) != cudaSuccess)
+                st = FFGPU_ERR_CUDA;
+            if (st == FFGPU_OK)
+                st = int_gemm_run(m, n, k, c.bits, A, lda, B, ldb, C, ldc, b != 0, ws, wsb, c.err, c.s);
+        }
+        c.used = mark;
+        return st;
+    }
+    if (c.dry) return FFGPU_OK;
     const dim3 grid((unsigned)((n + kZT - 1) / kZT), (unsigned)((m + kZT - 1) / kZT));
     if (grid.y > 65535u) return FFGPU_ERR_INVALID;
     return timed_launch("winograd_z_gemm", c.s, [&] {
@@ -293,6 +336,18 @@ ffgpu_status winograd_z_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
     c.cap = 0;
     c.dry = true;
     c.peak = 0;
+    c.err = nullptr;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        c.sms = sm_count(dev);
+        // the leaves' operands: sums of up to 4^levels balanced residues
+        unsigned long long bound = p == 2 ? 1ull : (p - 1) / 2;
+        for (int i = 0; i < levels; ++i) bound *= 4;
+        int b = 0;
+        while (b < 31 && (1ull << b) < bound) ++b;
+        c.bits = std::max(b, 1);
+    }
     // workspace: balanced A and B, the int64 product, the levels' temporaries
     auto plan = [&](ZCtx& z, int32_t** Ac, int32_t** Bc, long long** X) {
         *Ac = zalloc<int32_t>(z, m * k);
@@ -306,6 +361,7 @@ ffgpu_status winograd_z_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
     Pool* pool = nullptr;
     ZTRY(pool_get(s, c.peak, &pool));
     c.dry = false;
+    c.err = pool->err;
     c.base = static_cast<unsigned char*>(pool->ptr);
     c.cap = pool->bytes;
     c.used = 0;

@@ -108,3 +108,33 @@ def test_large_prime_refused():
     A = np.ones((4, 4), np.uint32)
     with pytest.raises(ff.FFGPUError):
         run(A, A, A, 2147483647, 1, 0, 1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("p,levels", [(65521, 1), (65521, 2), (8388593, 2), (251, 3)])
+def test_tensor_core_leaves(p, levels):
+    """Leaves of at least 2^24 multiply-adds run on the tensor cores as exact
+    integer products (int64 results added into the level's sums, negated
+    first where the schedule subtracts); odd dimensions peel at every level."""
+    m, n, k = 1031, 1029, 2051
+    assert k <= ff.winograd_unreduced_kmax(p, levels)
+    rng = W.rng_for("precision", 90, p, levels)
+    A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    assert np.array_equal(run(A, B, C, p, alpha, beta, levels), oracle.fgemm(A, B, p, alpha, beta, C))
+
+
+@pytest.mark.gpu
+def test_tensor_core_leaves_at_the_limit():
+    """The widened A_l, B_l of the appendix at the admission limit with
+    leaves large enough for the tensor cores (p = 65521, one level)."""
+    from oracle.winograd import optimal_matrices
+    p, levels = 65521, 1
+    h = (p - 1) // 2
+    A_l, B_l = optimal_matrices(levels, -h, h, -h, h)
+    r, d, s = 300, 2048, 260                 # m = 600, k = 4096, n = 520
+    A = (np.kron(A_l.astype(np.int64), np.ones((r, d), np.int64)) % p).astype(np.uint32)
+    B = (np.kron(B_l.astype(np.int64), np.ones((d, s), np.int64)) % p).astype(np.uint32)
+    rng = W.rng_for("precision", 91)
+    C = W.uniform_residues(rng, (A.shape[0], B.shape[1]), p)
+    assert np.array_equal(run(A, B, C, p, 1, 1, levels), oracle.fgemm(A, B, p, 1, 1, C))
