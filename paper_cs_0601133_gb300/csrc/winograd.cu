@@ -33,7 +33,8 @@ cudaError_t launch_dmma_fgemm(int m, int n, int k, const uint32_t* A, long long 
                               cudaStream_t s);
 cudaError_t launch_sgemm_fgemm(int m, int n, int k, const uint32_t* A, long long lda, const uint32_t* B,
                                long long ldb, uint32_t* C, long long ldc, uint32_t p, uint32_t al, uint32_t be,
-                               cudaStream_t s);
+                               void* ws, cudaStream_t s);
+size_t sgemm_ws_bytes(int64_t m, int64_t n, int64_t k);
 
 namespace {
 
@@ -105,7 +106,10 @@ ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, cons
                    ? FFGPU_OK
                    : FFGPU_ERR_CUDA;
     }
-    if (c.dry) return FFGPU_OK;
+    if (c.dry) {
+        if (c.path == 2 && k > 0) c.need_fg = std::max(c.need_fg, sgemm_ws_bytes(m, n, k));
+        return FFGPU_OK;
+    }
     if (k == 0)
         return timed_launch("scale_mod_p", c.s, [&] { return launch_scale(C, ldc, (int)m, (int)n, c.p, be, c.mu, c.s); }) ==
                        cudaSuccess
@@ -118,7 +122,7 @@ ffgpu_status base(WinoCtx& c, int64_t m, int64_t n, int64_t k, uint32_t al, cons
         });
     else
         e = timed_launch("sgemm_fgemm", c.s, [&] {
-            return launch_sgemm_fgemm((int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, c.p, al, be, c.s);
+            return launch_sgemm_fgemm((int)m, (int)n, (int)k, A, lda, B, ldb, C, ldc, c.p, al, be, c.fg_ws, c.s);
         });
     return e == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA;
 }

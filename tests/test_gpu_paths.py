@@ -134,7 +134,7 @@ def test_fp32_path_at_its_block_bound():
     R 125^2 + 2p <= 2^24 (R = 1072): each block sums 1072 * 15625 = 99.8 % of
     2^24; three blocks and a ragged one."""
     p, h = 251, 125
-    R = ((1 << 24) - 2 * p) // (h * h) // 8 * 8       # the path's block: whole k-tiles of 8
+    R = ((1 << 24) - 2 * p) // (h * h) // 16 * 16     # the path's block: whole k-tiles of 16
     assert R == 1072 and R * h * h + p < 2**24 and R * h * h >= 0.99 * 2**24
     m, n, k = 200, 136, 3 * R + 50
     rng = W.rng_for("worstcase", 10, p)
