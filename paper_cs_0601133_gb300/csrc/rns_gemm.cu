@@ -347,16 +347,20 @@ __device__ __forceinline__ void store_digits(const uint32_t* v, float mf, float 
 }
 
 // After the last chunk: CRT digits (one byte per entry) to the residue slot.
+// Only what the reconstruction reads is stored: nothing for a row at or past
+// the instance's last row (row_ok false), nothing for a 32-column group that
+// starts at or past col_lim (columns counted from this warp's first one); the
+// tensor-memory loads stay warp-wide.
 __device__ __forceinline__ void epi_digits(uint32_t tbase, float mf, float im, float uf, float uim,
-                                           unsigned char* dst) {
+                                           unsigned char* dst, bool row_ok, int col_lim) {
 #pragma unroll 1
     for (int cc = 0; cc < 4; cc += 2) {
         uint32_t v[32], v2[32];
         tc_ld32(tbase + cc * 32, v);
         tc_ld32(tbase + cc * 32 + 32, v2);
         tc_wait_ld();
-        store_digits(v, mf, im, uf, uim, dst + cc * 32);
-        store_digits(v2, mf, im, uf, uim, dst + cc * 32 + 32);
+        if (row_ok && cc * 32 < col_lim) store_digits(v, mf, im, uf, uim, dst + cc * 32);
+        if (row_ok && cc * 32 + 32 < col_lim) store_digits(v2, mf, im, uf, uim, dst + cc * 32 + 32);
     }
 }
 
@@ -677,7 +681,9 @@ __device__ __forceinline__ void rns_gemm_body(const CUtensorMap* mapA, const CUt
                             sep[d.slot] ^= 1u;
                         }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
-                        epi_digits(tbase, mf, im, uf, uim, dst);
+                        const InstInfo& I = *d.inst;
+                        epi_digits(tbase, mf, im, uf, uim, dst, d.tm * kTileM + row_local < I.m,
+                                   I.n - d.tn * kTileN - half * 128);
                     }
                     tc_fence_before();
                     if (last_chunk && c == d.nch - 1) __threadfence_block();
@@ -956,15 +962,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t sep[2] = {0u, 0u};
         bool ok = true;
         int it_t = 0, it_c = 0;  // job iterator: tile ordinal, channel
+        int cur_tm = 0, cur_tn = 0;  // coordinates of tile it_t
+        if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, P.raster, cur_tm, cur_tn);
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
-            int jc[2], jslot[2];
+            int jc[2], jslot[2], jtm[2], jtn[2];
             for (int s = 0; s < nj; ++s) {
                 jc[s] = it_c;
                 jslot[s] = it_t & 1;
+                jtm[s] = cur_tm;
+                jtn[s] = cur_tn;
                 if (++it_c == nch) {
                     it_c = 0;
-                    ++it_t;
+                    if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, P.raster, cur_tm, cur_tn);
                 }
             }
             for (int h = 0; h < H && ok; ++h) {
@@ -994,7 +1004,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             sep[slot] ^= 1u;
                         }
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
-                        epi_digits(tbase, mf, im, uf, uim, dst);
+                        epi_digits(tbase, mf, im, uf, uim, dst, (2 * jtm[s] + (int)rank) * kTileM + row_local < I.m,
+                                   I.n - jtn[s] * kTileN - half * 128);
                     }
                     tc_fence_before();
                     if (last_chunk && c == nch - 1) __threadfence_block();
