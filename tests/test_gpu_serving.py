@@ -74,3 +74,39 @@ def test_singular_solve_reported_in_completion(pool):
         while not comps:
             comps = sv.poll(wait_ms=100)
         assert comps[0][0] == 42 and comps[0][1] == -1   # FFGPU_ERR_INVALID
+
+
+def test_requests_run_with_cached_plans(tmp_path):
+    """With plans in the cache for the requests' shape buckets (the CUDA-core
+    route for a product the size rule sends to the tensor cores, one-CTA tiles
+    with bands of 4 tile rows for another), the server applies them and every
+    result still equals the oracle's."""
+    import json
+    p = 2147483647
+    rng = W.rng_for("serving", 78)
+    shapes = [(600, 520, 700), (300, 280, 260)]       # (m, k, n)
+    b = lambda x: (x + 255) // 256 * 256
+    plans = [{"key": "0:%d:%d:%d:%d" % (b(600), b(700), b(520), p), "kernel": -1, "winograd_levels": 0,
+              "chunk_steps": 0, "route": 1, "raster_rows": 0, "ms": 1.0},
+             {"key": "0:%d:%d:%d:%d" % (b(300), b(260), b(280), p), "kernel": 0, "winograd_levels": 0,
+              "chunk_steps": 16, "route": 0, "raster_rows": 4, "ms": 1.0}]
+    src = tmp_path / "plans.json"
+    src.write_text('{"version": 2, "plans": [\n' + ",\n".join(json.dumps(x) for x in plans) + "\n]}\n")
+    ff.autotune_clear()
+    ff.autotune_load(str(src))
+    try:
+        probs = []
+        for m, k, n in shapes:
+            A, B = W.uniform_residues(rng, (m, k), p), W.uniform_residues(rng, (k, n), p)
+            probs.append((A, B, np.zeros((m, n), np.uint32)))
+        with ff.Server(streams=2, budget_bytes=2 << 30) as sv:
+            for i, (A, B, out) in enumerate(probs):
+                sv.submit_fgemm(A, B, out, p, 3, 0, tag=i)
+            done = []
+            while len(done) < len(probs):
+                done += sv.poll(wait_ms=100)
+        assert all(c[1] == 0 for c in done)
+        for A, B, out in probs:
+            assert np.array_equal(out, oracle.fgemm(A, B, p, 3, 0))
+    finally:
+        ff.autotune_clear()
