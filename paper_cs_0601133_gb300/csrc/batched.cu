@@ -441,7 +441,8 @@ static std::atomic<int64_t> g_batch_small_macs{int64_t(1) << 23};
 
 }  // namespace
 
-int64_t batched_small_macs() { return g_batch_small_macs.load(); }
+thread_local int64_t g_batch_small_scoped = -1;
+int64_t batched_small_macs() { return g_batch_small_scoped >= 0 ? g_batch_small_scoped : g_batch_small_macs.load(); }
 void set_batched_small_macs(int64_t macs) { g_batch_small_macs.store(macs < 0 ? 0 : macs); }
 
 namespace {
@@ -538,7 +539,7 @@ void split_batch(int64_t count, const ffgpu_fgemm_desc* descs, std::vector<std::
     std::vector<BInst> wave;
     std::unordered_set<int64_t> wave_k;
     size_t wave_bytes = 0;
-    const int64_t small_limit = std::min<int64_t>(g_batch_small_macs.load(), small_threshold());
+    const int64_t small_limit = std::min<int64_t>(batched_small_macs(), small_threshold());
     for (int64_t i = 0; i < count; ++i) {
         const ffgpu_fgemm_desc& d = descs[i];
         if (d.m == 0 || d.n == 0) continue;

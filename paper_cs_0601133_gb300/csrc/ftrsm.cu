@@ -368,12 +368,15 @@ TrsmLayout trsm_layout(int side, int uplo, int algo, int64_t m, int64_t n, uint3
         else
             fg = std::max(fg, std::max(fgemm_ws_bytes(m, r, h, p, sms), fgemm_ws_bytes(m, h, r, p, sms)));
     }
-    for (int64_t s = kBlk; s < Y.L; s *= 2)
-        for (int step = 0; step < 2; ++step) {
-            std::vector<ffgpu_fgemm_desc> d;
-            doubling_descs(sz, Y.L, s, uplo, p, nullptr, sz, nullptr, nullptr, step, d);
-            if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
-        }
+    {
+        ScopedBatchSmall route(small_threshold());  // as the doubling levels run them (ftrsm_run)
+        for (int64_t s = kBlk; s < Y.L; s *= 2)
+            for (int step = 0; step < 2; ++step) {
+                std::vector<ffgpu_fgemm_desc> d;
+                doubling_descs(sz, Y.L, s, uplo, p, nullptr, sz, nullptr, nullptr, step, d);
+                if (!d.empty()) fg = std::max(fg, batched_ws_bytes((int64_t)d.size(), d.data(), sms));
+            }
+    }
     if (algo == 1) {
         std::vector<ffgpu_fgemm_desc> d;
         delayed_w_descs(side, geo, Y.L, p, nullptr, sz, nullptr, nullptr, d);
@@ -500,13 +503,18 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
             return cudaGetLastError();
         }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
-    for (int64_t lv = kBlk; lv < Y.L; lv *= 2) {
-        for (int step = 0; step < 2; ++step) {
-            std::vector<ffgpu_fgemm_desc> d;
-            doubling_descs(sz, Y.L, lv, uplo, p, T, ldt, inv, tmp, step, d);
-            if (d.empty()) continue;
-            const ffgpu_status st = batched_run_ws((int64_t)d.size(), d.data(), c.ws, c.ws_bytes, err, s);
-            if (st != FFGPU_OK) return st;
+    {
+        // a doubling level is a batch of equal products: the single-product
+        // crossover decides their route (CUDA cores up to 2^27 multiply-adds)
+        ScopedBatchSmall route(small_threshold());
+        for (int64_t lv = kBlk; lv < Y.L; lv *= 2) {
+            for (int step = 0; step < 2; ++step) {
+                std::vector<ffgpu_fgemm_desc> d;
+                doubling_descs(sz, Y.L, lv, uplo, p, T, ldt, inv, tmp, step, d);
+                if (d.empty()) continue;
+                const ffgpu_status st = batched_run_ws((int64_t)d.size(), d.data(), c.ws, c.ws_bytes, err, s);
+                if (st != FFGPU_OK) return st;
+            }
         }
     }
     if (algo == FFGPU_TRSM_DELAYED)

@@ -218,6 +218,15 @@ int autotune_route(int64_t m, int64_t n, int64_t k, uint32_t p);
 // Largest product (multiply-adds) the batched launch sends to the grouped CUDA-core kernel.
 int64_t batched_small_macs();
 void set_batched_small_macs(int64_t macs);
+// A threshold for the calling thread's batched launches until the scope ends
+// (the ftrsm's doubling products: one batch of equal products, where the
+// single-product crossover applies rather than the mixed batch's).
+extern thread_local int64_t g_batch_small_scoped;
+struct ScopedBatchSmall {
+    int64_t saved;
+    explicit ScopedBatchSmall(int64_t macs) : saved(g_batch_small_scoped) { g_batch_small_scoped = macs; }
+    ~ScopedBatchSmall() { g_batch_small_scoped = saved; }
+};
 constexpr int kRasterRows = 16;  // default tile rows per band of the tile order
 int rns_gemm_pair_max_clusters();
 size_t rns_gemm_smem_bytes();
