@@ -31,6 +31,7 @@ namespace {
 
 constexpr int kBlk = 128;       // diagonal block inverted by substitution
 constexpr int kMaxLeaf = 1024;  // largest leaf
+constexpr int64_t kDoublingSmallMacs = int64_t(1) << 24;  // doubling products routed to the CUDA cores
 
 // Leaf size for a triangle of size sz: the smallest power of two from 128
 // rows that covers half of it, at most 1024 rows (two leaves up to
@@ -369,7 +370,7 @@ TrsmLayout trsm_layout(int side, int uplo, int algo, int64_t m, int64_t n, uint3
             fg = std::max(fg, std::max(fgemm_ws_bytes(m, r, h, p, sms), fgemm_ws_bytes(m, h, r, p, sms)));
     }
     {
-        ScopedBatchSmall route(small_threshold());  // as the doubling levels run them (ftrsm_run)
+        ScopedBatchSmall route(kDoublingSmallMacs);  // as the doubling levels run them (ftrsm_run)
         for (int64_t s = kBlk; s < Y.L; s *= 2)
             for (int step = 0; step < 2; ++step) {
                 std::vector<ffgpu_fgemm_desc> d;
@@ -504,9 +505,12 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
         }) != cudaSuccess)
         return FFGPU_ERR_CUDA;
     {
-        // a doubling level is a batch of equal products: the single-product
-        // crossover decides their route (CUDA cores up to 2^27 multiply-adds)
-        ScopedBatchSmall route(small_threshold());
+        // a doubling level is a batch of equal products: up to 256^3 (2^24
+        // multiply-adds) each on the CUDA cores, larger ones on the tensor
+        // cores (measured, n = 2048 / 4096 / 8192, p = 65521: 0.675 / 1.229 /
+        // 4.348 ms; with the batch default 2^23: 0.719 / 1.280 / 4.432 ms;
+        // with 2^27: 0.677 / 1.322 / 4.642 ms)
+        ScopedBatchSmall route(kDoublingSmallMacs);
         for (int64_t lv = kBlk; lv < Y.L; lv *= 2) {
             for (int step = 0; step < 2; ++step) {
                 std::vector<ffgpu_fgemm_desc> d;
