@@ -563,14 +563,18 @@ ffgpu_status ffgpu_fgemm_ws(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_
     // needs workspace beyond the caller's and is not applied here)
     TuneOverride tuned;
     int levels = 0;
-    const bool have = k > 0 && autotune_settings(m, n, k, p, tuned, levels);
-    ScopedTune scope(have ? tuned : g_tune_override);
+    bool have = k > 0 && autotune_settings(m, n, k, p, tuned, levels);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Pool* pool = nullptr;
     st = pool_get(s, 0, &pool);
     if (st != FFGPU_OK) return st;
     int dev = 0;
     cudaGetDevice(&dev);
+    if (have) {  // a plan whose route needs more than the workspace sized by the default rules is not used
+        ScopedTune probe(tuned);
+        have = workspace_bytes >= fgemm_ws_bytes(m, n, k, p, sm_count(dev));
+    }
+    ScopedTune scope(have ? tuned : g_tune_override);
     if (workspace_bytes < fgemm_ws_bytes(m, n, k, p, sm_count(dev))) return FFGPU_ERR_NOMEM;
     if (workspace_bytes && (reinterpret_cast<uintptr_t>(workspace) & 255)) return FFGPU_ERR_INVALID;
     return fgemm_run(m, n, k, p, alpha, A, lda, B, ldb, beta, C, ldc, workspace, workspace_bytes,
