@@ -3,10 +3,9 @@
 // The tensor-core path pays fixed costs per call (two conversion launches,
 // one product per residue channel, the CRT epilogue) that dwarf the
 // arithmetic of a small product such as the 64 x 64 x 64 multiplier blocks of
-// LQUP.  Here every output is an exact dot product: the words reduced mod p
-// as they are staged, multiplied into 64 bits, four products summed in 64
-// bits and the sums added into a 96-bit accumulator (three 32-bit words with
-// carry chains), which stays exact for any k < 2^32, reduced
+// LQUP.  Here every output is an exact dot product: 32-bit words multiplied
+// into 64 bits and summed in a 96-bit accumulator (three 32-bit words with
+// carry chains), which stays exact for any inputs and any k < 2^32, reduced
 // mod p once, then alpha and beta applied (the delayed reduction of section
 // 3.1 taken to its limit: one reduction per output).  64 x 64 output tiles,
 // 256 threads with 4 x 4 outputs each, k staged through shared memory 32 at a
@@ -30,12 +29,12 @@ constexpr int kSmT = 64;   // output tile (rows and columns)
 constexpr int kSmK = 32;   // k chunk
 constexpr int kSmThreads = 256;
 
-__device__ __forceinline__ void add96(uint32_t& lo, uint32_t& mid, uint32_t& hi, unsigned long long t) {
-    asm("add.cc.u32 %0, %0, %3;\n\t"
-        "addc.cc.u32 %1, %1, %4;\n\t"
+__device__ __forceinline__ void mac96(uint32_t& lo, uint32_t& mid, uint32_t& hi, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
         "addc.u32 %2, %2, 0;"
         : "+r"(lo), "+r"(mid), "+r"(hi)
-        : "r"((uint32_t)t), "r"((uint32_t)(t >> 32)));
+        : "r"(a), "r"(b));
 }
 
 // (hi 2^64 + mid 2^32 + lo) mod p, then alpha v + beta c mod p
@@ -60,18 +59,9 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
                                            uint32_t two64p, uint32_t alpha, uint32_t beta) {
     constexpr int NT = T * T / 16;       // threads
     constexpr int PER = T * kSmK / NT;   // staged words per thread and operand (8 for T = 64, 16 for T = 32)
-    __shared__ __align__(16) uint32_t As[kSmK][T];  // As[kk][row], reduced mod p
-    __shared__ __align__(16) uint32_t Bs[kSmK][T];  // Bs[kk][col], reduced mod p
+    __shared__ __align__(16) uint32_t As[kSmK][T];  // As[kk][row]
+    __shared__ __align__(16) uint32_t Bs[kSmK][T];  // Bs[kk][col]
     const int tid = threadIdx.x, tx = tid % (T / 4), ty = tid / (T / 4);
-    // words are reduced mod p as they are staged (32-bit Barrett: floor((2^32 - 1) / p)
-    // is the high word of floor((2^64 - 1) / p)), so that every product is below
-    // 2^62 and four of them sum in 64 bits
-    const uint32_t mu32 = (uint32_t)(mu >> 32);
-    auto red = [&](uint32_t x) {
-        const uint32_t q = __umulhi(x, mu32);
-        const uint32_t r = x - q * p;
-        return r >= p ? r - p : r;
-    };
     uint32_t lo[4][4], mid[4][4], hi[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -84,7 +74,7 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
                 const int gk = k0 + kk0 + e;
-                As[kk0 + e][r] = (gi < m && gk < kend) ? red(__ldg(A + (long long)gi * lda + gk)) : 0u;
+                As[kk0 + e][r] = (gi < m && gk < kend) ? __ldg(A + (long long)gi * lda + gk) : 0u;
             }
         }
         {
@@ -92,33 +82,19 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
 #pragma unroll
             for (int e = 0; e < PER; ++e) {
                 const int gj = col0 + c0 + e;
-                Bs[kk][c0 + e] = (gk < kend && gj < n) ? red(__ldg(B + (long long)gk * ldb + gj)) : 0u;
+                Bs[kk][c0 + e] = (gk < kend && gj < n) ? __ldg(B + (long long)gk * ldb + gj) : 0u;
             }
         }
         __syncthreads();
-        // groups of four products summed exactly in 64 bits (one wide
-        // multiply-add each, no carry chain), then added to the 96-bit sums
-#pragma unroll 1
-        for (int kq = 0; kq < kSmK; kq += 4) {
-            unsigned long long t[4][4];
+#pragma unroll 4
+        for (int kk = 0; kk < kSmK; ++kk) {
+            const uint4 a = *reinterpret_cast<const uint4*>(&As[kk][ty * 4]);
+            const uint4 b = *reinterpret_cast<const uint4*>(&Bs[kk][tx * 4]);
+            const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) t[i][j] = 0ull;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint4 a = *reinterpret_cast<const uint4*>(&As[kq + u][ty * 4]);
-                const uint4 b = *reinterpret_cast<const uint4*>(&Bs[kq + u][tx * 4]);
-                const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) t[i][j] += (unsigned long long)av[i] * bv[j];
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) add96(lo[i][j], mid[i][j], hi[i][j], t[i][j]);
+                for (int j = 0; j < 4; ++j) mac96(lo[i][j], mid[i][j], hi[i][j], av[i], bv[j]);
         }
         __syncthreads();
     }
