@@ -392,7 +392,9 @@ def run_own(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": workload_name(n, p), "n": n, "p": p, "alpha": alpha, "beta": beta,
                        "channels": plan["channels"], "moduli": plan["moduli"],
-                       "l2": "inputs 768 MiB > 129 MB L2: no flush between steps",
+                       "l2": ("inputs %d MiB > 129 MB L2: no flush between steps" % (3 * n * n * 4 >> 20))
+                             if 3 * n * n * 4 > 129e6 else
+                             "inputs %d MiB fit the 129 MB L2 (a step re-reads them from L2)" % (3 * n * n * 4 >> 20),
                        "parallelism": "replicas x%d" % world, "plan": plan_used},
             "roofline": roofline,
             "cpu_baseline": base,
