@@ -107,10 +107,16 @@ void stage_done(int idx, cudaStream_t s) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
+// One tensor-core instance of a wave.  mpad / npad: the rows and columns its
+// tiles cover (whole 128 x 256 tiles); mst / nst: the plane rows it stores
+// (m and n rounded to 8).  A tile that reaches past the stored rows reads the
+// next instance's planes (or the pool's zero fill): those rows and columns
+// of the tile are never reconstructed, so only the inner dimension's padding
+// must be zeros -- and the conversions write it.
 struct BInst {
     const ffgpu_fgemm_desc* d;
     RnsPlan pl;
-    int64_t kp, mpad, npad;
+    int64_t kp, mpad, npad, mst, nst;
     int bucket;
     int64_t rowA, rowB;
 };
@@ -159,8 +165,8 @@ void layout_wave(std::vector<BInst>& w, int sms, WaveLayout& L, const MultiCtx* 
         B.nch = std::max(B.nch, b.pl.nch);
         b.rowA = B.rowsA;
         b.rowB = B.rowsB;
-        B.rowsA += b.mpad;
-        B.rowsB += b.npad;
+        B.rowsA += b.mst;
+        B.rowsB += b.nst;
     }
     // tiles and their cost (channels x k-steps), longest first onto the least-loaded CTA
     struct Tile {
@@ -297,7 +303,7 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
         a.ldx = d.lda;
         a.rows = (int)d.m;
         a.cols = (int)d.k;
-        a.rows_pad = (int)b.mpad;
+        a.rows_pad = (int)b.mst;
         a.kp = (int)b.kp;
         a.vec_ok = ((reinterpret_cast<uintptr_t>(d.A) & 15) == 0) && (d.lda % 4 == 0);
         a.dst = reinterpret_cast<uint4*>(planes + B.offA + size_t(b.rowA) * b.kp * 2);
@@ -308,7 +314,7 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
         c2.ldx = d.ldb;
         c2.rows = (int)d.k;
         c2.cols = (int)d.n;
-        c2.rows_pad = (int)b.npad;
+        c2.rows_pad = (int)b.nst;
         c2.kp = (int)b.kp;
         c2.vec_ok = 0;
         c2.dst = reinterpret_cast<uint4*>(planes + B.offB + size_t(b.rowB) * b.kp * 2);
@@ -316,8 +322,8 @@ ffgpu_status fill_wave_tables(const std::vector<BInst>& w, WaveLayout& L, unsign
         c2.cp = cp;
         bbA[i] = nbA;
         bbB[i] = nbB;
-        nbA += convert_rows_grouped_blocks((int)b.mpad);
-        nbB += convert_transpose_grouped_blocks((int)b.npad, (int)b.kp);
+        nbA += convert_rows_grouped_blocks((int)b.mst);
+        nbB += convert_transpose_grouped_blocks((int)b.nst, (int)b.kp);
     }
     bbA[n_inst] = nbA;
     bbB[n_inst] = nbB;
@@ -564,13 +570,15 @@ void split_batch(int64_t count, const ffgpu_fgemm_desc* descs, std::vector<std::
         b.kp = round_up(d.k, kTileK);
         b.mpad = round_up(d.m, kTileM);
         b.npad = round_up(d.n, kTileN);
+        b.mst = round_up(d.m, 8);
+        b.nst = round_up(d.n, 8);
         b.bucket = 0;
         b.rowA = b.rowB = 0;
         if (b.mpad / kTileM > 0xFFFF || b.npad / kTileN > 0xFFFF) {  // tile indices are packed in 16 bits
             singles.push_back(&d);
             continue;
         }
-        const size_t bytes = size_t(pl.nch) * (b.mpad + b.npad) * b.kp * 2;
+        const size_t bytes = size_t(pl.nch) * (b.mst + b.nst) * b.kp * 2;
         const bool new_k = wave_k.find(b.kp) == wave_k.end();
         if (!wave.empty() && (wave_bytes + bytes > wave_plane_budget() || (new_k && wave_k.size() >= 0xFFFF))) {
             waves.push_back(std::move(wave));
