@@ -67,12 +67,13 @@ constexpr int kWinThreads = 512;
 constexpr int64_t kGWords = int64_t(1) << 21;  // scratch for a small G product (h2 r1 r1 <= 2^27, r1 > 64)
 
 // A leaf's outcome, written by the window kernel (and the failure fields by
-// the rest kernel); the first four ints are read back by the host.
+// the rest kernel); the first five ints are read back by the host.
 struct LeafInfo {
     int rank;                 // pivots found in the window
     int fail;                 // some non-pivot row has a non-zero residual beyond the window
     int ident;                // the window's columns keep their order
     int firstnz;              // smallest column of such a residual (absolute index)
+    int timeout;              // a bounded wait of the window kernel ran out
     int prow[kLeafRows];      // pivot rows (leaf-relative), in pivot order
     int newrow[kLeafRows];    // new leaf row i = old leaf row newrow[i]
     int newcol[kMaxWin];      // new window column q = old window column newcol[q]
@@ -97,375 +98,359 @@ __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uns
 }
 
 // Window factorization of one leaf (one CTA of kWinThreads).  A points at
-// (rb, c); the tile is h x WS (W real columns, zero padding up to WS, a
-// multiple of 32).
+// (rb, c); the leaf's tile is h x W (zero padding up to WS, a multiple of 32).
 //
-// Fraction-free elimination, so that no row waits for a modular inverse: row
-// t' below pivot k (row t, column j, scaled value P) becomes
-// P row_t' - a row_t with a its scaled entry in column j, and its scale d_t'
-// (the factor by which the stored row exceeds the true Schur complement) is
-// multiplied by P (recovered afterwards from which steps touched the row).
-// The pivot row is published with the Shoup quotients of its values, so a
-// row's update needs no quotient of its own multiplier.  The rows live in registers (warp w holds rows w, w + 16,
-// w + 32, w + 48; lane l columns l, l + 32, ...); per row one barrier: the
-// pivot row and its pivot are published in shared memory, every warp updates
-// its rows below it, and the warp that owns the next row updates that row
-// first, finds its pivot (warp ballots) and publishes it.  Afterwards one
-// batched inversion of the pivots (prefix and suffix products over a warp, one
-// extended-Euclid inverse) gives the true multipliers
-// l_t'k = a d_t / (P d_t') (prefix products of the inverse pivots per row) and
-// the true U rows.  The leaf's elimination matrix E = (I + N)^{-1}
-// (N[t'][t] = l_t'k, unit lower triangular) and the inverse of its pivot block
-// U11 (r x r, upper triangular) are formed by doubling: [[A, 0], [C, D]]^{-1}
-// has off-diagonal block -D^{-1} C A^{-1} (upper: -A^{-1} C D^{-1}), each level
-// two small products over all pairs at once.
+// Arithmetic.  For odd p the kernel works in Montgomery form with R = 2^32
+// (x held as x R mod p): a product is one 64-bit multiply and one reduction,
+// with no precomputed quotient of either factor, and the update
+// P v - a u of an entry is a single reduction of P v + a (p - u) < 2 p^2 < p R.
+// p = 2 works on plain bits (product AND, difference XOR).
+//
+// Elimination.  Fraction-free and row by row, so that no row waits for a
+// modular inverse: row t' below pivot k (row t, column j, stored value P)
+// becomes P row_t' - a row_t with a its stored entry in column j, and its
+// scale d_t' (the factor by which the stored row exceeds the true Schur
+// complement) is multiplied by P.  Each row is extended by the identity row
+// of the leaf, so that the same operations turn the extension into d_t times
+// row t of the leaf's elimination matrix E (E times the leaf's rows gives its
+// eliminated rows).  Warp w holds rows w, w + 16, w + 32, w + 48 in registers
+// (lane l columns l, l + 32, ...).  Rows are published in shared memory once
+// final: row t is final after the pivots of rows 0 .. t-1, and its owner
+// publishes it (values, pivot column, stored pivot, scale) and arrives on
+// row t's mbarrier.  Every warp takes the rows in order, waits for each on its
+// mbarrier (a bounded wait), and updates its own rows below it; the owner of
+// row t + 1 updates that row first and publishes it at once, so that the chain
+// of pivot decisions passes from warp to warp without a barrier of the CTA.
+//
+// Afterwards one batched inversion of the pivots (prefix and suffix products
+// over a warp, one extended-Euclid inverse) gives the true multipliers
+// l_t'k = a d_t / (P d_t') (prefix products of the inverse pivots per row),
+// the true U rows and E (each stored row times 1 / d_t).  The inverse of the
+// pivot block U11 (r x r, upper triangular) is formed by doubling:
+// [[A, C], [0, D]]^{-1} has off-diagonal block -A^{-1} C D^{-1}, each level two
+// products over all pairs at once, on 64 x 64 zero-padded blocks so that every
+// dot product has the level's full length and no bounds.
 //
 // Writes the leaf's new rows on the window (rows points at column c of the
 // scratch rows), E (h x h, original row order), U11^{-1} (r x r, zeros below
 // the diagonal, leading dimension ldu; skipped when Uig is null) and the
 // LeafInfo.
-constexpr int kRowsPerWarp = kLeafRows / (kWinThreads / 32);
-// Doubling scratch per triangle: at level s the pairs' s x s products, at most
-// kLeafRows^2 / 2 words for any h <= kLeafRows.
-constexpr int kTmWords = kLeafRows * kLeafRows / 2;
+constexpr int kWinWarps = kWinThreads / 32;
+constexpr int kRowsPerWarp = kLeafRows / kWinWarps;
+constexpr int kExt = kLeafRows;              // columns of the identity extension
+constexpr int kTmWords = kLeafRows * kLeafRows / 4;  // doubling products of one level (npairs s^2 <= 32 s)
 
-template <int NC>
-__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[NC], int c) {
+template <bool kBin>
+struct WinField {
+    uint32_t p, pinv, r2, one;  // pinv = -p^{-1} mod 2^32, r2 = R^2 mod p, one = R mod p
+    __device__ __forceinline__ WinField(uint32_t p_, uint32_t two64p, unsigned long long mu) : p(p_) {
+        if (kBin) {
+            pinv = 0u;
+            r2 = one = 1u;
+        } else {
+            uint32_t x = p;  // Newton's iteration for p^{-1} mod 2^32 (3, 6, 12, 24, 48 bits)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x *= 2u - p * x;
+            pinv = 0u - x;
+            r2 = two64p;
+            one = mod_u64(1ull << 32, p, mu);
+        }
+    }
+    __device__ __forceinline__ uint32_t redc(unsigned long long t) const {  // t < p R
+        const uint32_t m = (uint32_t)t * pinv;
+        const unsigned long long u = (t + (unsigned long long)m * p) >> 32;
+        return u >= p ? (uint32_t)(u - p) : (uint32_t)u;
+    }
+    __device__ __forceinline__ uint32_t mul(uint32_t a, uint32_t b) const {
+        return kBin ? (a & b) : redc((unsigned long long)a * b);
+    }
+    // P v + a w (w = neg(u)): the update P v - a u
+    __device__ __forceinline__ uint32_t fma2(uint32_t P, uint32_t v, uint32_t a, uint32_t w) const {
+        return kBin ? ((P & v) ^ (a & w)) : redc((unsigned long long)P * v + (unsigned long long)a * w);
+    }
+    __device__ __forceinline__ uint32_t neg(uint32_t u) const { return kBin || u == 0u ? u : p - u; }
+    __device__ __forceinline__ uint32_t to(uint32_t x) const { return kBin ? x : redc((unsigned long long)x * r2); }
+    __device__ __forceinline__ uint32_t from(uint32_t x) const { return kBin ? x : redc(x); }
+    __device__ __forceinline__ uint32_t inv(uint32_t x) const { return kBin ? x : to(inv_mod_dev(from(x), p)); }
+};
+
+template <int N, int NA>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&v)[NA], int c) {
     uint32_t x = 0u;
 #pragma unroll
-    for (int i = 0; i < NC; ++i)
+    for (int i = 0; i < N; ++i)
         if (i == c) x = v[i];
     return x;
 }
 
-// Publish row trow (held by this warp in vrow): its values, pivot column and
-// pivot, in slot `slot`; the pivot becomes number kk.
-template <int NC>
-__device__ __forceinline__ void win_publish(const uint32_t (&vrow)[NC], int trow, int kk, int slot, uint32_t p,
-                                            unsigned long long mu, uint32_t* s_row, uint32_t* s_rowq, int* s_j,
-                                            uint32_t* s_Pv, uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P,
-                                            int* s_colpiv, int* s_rowpiv) {
+// Shared state of the elimination.
+struct WinState {
+    uint32_t* U;     // [h][WA]: published rows (window, then the identity extension)
+    uint32_t* Lsm;   // [h][h]: numerators a (row t, pivot k), then the true multipliers
+    uint64_t* bar;   // [h]: row t published
+    int* jp;         // pivot column of row t (-1: none)
+    uint32_t* Pv;    // stored pivot of row t
+    uint32_t* dv;    // scale of row t
+    int* pre;        // pivots above row t
+    int* prow;       // pivot k's row
+    int* pcol;       // pivot k's column
+    uint32_t* P;     // pivot k's stored value
+    int* colpiv;     // window column -> pivot number (-1: none)
+    int* rowpiv;     // row -> pivot number (-1: none)
+    volatile int* abort_flag;
+};
+
+// Publish row t (this warp's registers v; kk pivots above it; scale d).
+template <int NCW, int NCA>
+__device__ __forceinline__ void win_publish(const uint32_t (&v)[NCA], int t, int kk, uint32_t d, const WinState& S,
+                                            int WA) {
     const int lane = threadIdx.x & 31;
     int j = -1;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const unsigned bal = __ballot_sync(0xffffffffu, vrow[c] != 0u);
+    for (int c = 0; c < NCW; ++c) {
+        const unsigned bal = __ballot_sync(0xffffffffu, v[c] != 0u);
         if (j < 0 && bal) j = 32 * c + __ffs(bal) - 1;
     }
-    // the row's values and their Shoup quotients: every later row's update
-    // multiplies them by its own entry a, so no quotient of a is needed
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        s_row[slot * kMaxWin + lane + 32 * c] = vrow[c];
-        s_rowq[slot * kMaxWin + lane + 32 * c] = vrow[c] ? shoup_quot(vrow[c], p, mu) : 0u;
-    }
-    const uint32_t P = __shfl_sync(0xffffffffu, pick<NC>(vrow, j >> 5), j & 31);
+    for (int c = 0; c < NCA; ++c) S.U[t * WA + lane + 32 * c] = v[c];
+    const uint32_t P = j >= 0 ? __shfl_sync(0xffffffffu, pick<NCW>(v, j >> 5), j & 31) : 0u;
     if (lane == 0) {
-        s_j[slot] = j;
+        S.jp[t] = j;
+        S.Pv[t] = P;
+        S.dv[t] = d;
+        S.pre[t] = kk;
         if (j >= 0) {
-            s_Pv[slot] = P;
-            s_Ps[slot] = shoup_quot(P, p, mu);
-            s_prow[kk] = trow;
-            s_pcol[kk] = j;
-            s_P[kk] = P;
-            s_colpiv[j] = kk;
-            s_rowpiv[trow] = kk;
+            S.prow[kk] = t;
+            S.pcol[kk] = j;
+            S.P[kk] = P;
+            S.colpiv[j] = kk;
+            S.rowpiv[t] = kk;
         }
     }
+    __syncwarp();
+    mbar_arrive(&S.bar[t]);  // each lane releases its own stores
 }
 
-// Row update: v <- P v - a u (mod p) with a = v[j].  Returns false if a = 0.
-template <int NC>
-__device__ __forceinline__ bool win_update(uint32_t (&v)[NC], const uint32_t (&u)[NC], const uint32_t (&uq)[NC],
-                                           int jc, int jl, uint32_t P, uint32_t Ps, uint32_t p, uint32_t& a_out) {
-    const uint32_t a = __shfl_sync(0xffffffffu, pick<NC>(v, jc), jl);
-    a_out = a;
-    if (a == 0u) return false;
+// Row update by pivot row u (w = its negated values): v <- P v - a u with
+// a = v[j]; the numerator goes to *lnum.  Nothing when a = 0.
+template <bool kBin, int NCW, int NCA>
+__device__ __forceinline__ void win_update(const WinField<kBin>& F, uint32_t (&v)[NCA], uint32_t& d,
+                                           const uint32_t (&w)[NCA], int j, uint32_t P, uint32_t* lnum) {
+    const uint32_t a = __shfl_sync(0xffffffffu, pick<NCW>(v, j >> 5), j & 31);
+    if (a == 0u) return;
+    if ((threadIdx.x & 31) == 0) *lnum = a;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-        const uint32_t x = shoup_mul(v[c], P, Ps, p), y = shoup_mul(a, u[c], uq[c], p);
-        v[c] = x >= y ? x - y : x + (p - y);
-    }
-    return true;
+    for (int c = 0; c < NCA; ++c) v[c] = F.fma2(P, v[c], a, w[c]);
+    d = F.mul(d, P);
 }
 
-template <int NC>
-__device__ __forceinline__ int win_eliminate(uint32_t* T, int WS, int W, int h, uint32_t p, unsigned long long mu,
-                                             uint32_t* Lsm, uint32_t* s_row, uint32_t* s_rowq, int* s_j,
-                                             uint32_t* s_Pv, uint32_t* s_Ps, int* s_prow, int* s_pcol, uint32_t* s_P,
-                                             int* s_colpiv, int* s_rowpiv) {
+// The elimination; returns the rank on the window, or -1 if a wait ran out.
+template <bool kBin, int NCW>
+__device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* __restrict__ A, long long lda, int h, int W,
+                             const WinState& S, int* timeout) {
+    constexpr int NCA = NCW + kExt / 32;
+    constexpr int WA = 32 * NCA;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int nw = kWinThreads / 32;
-    uint32_t v[kRowsPerWarp][NC];
+    uint32_t v[kRowsPerWarp][NCA], d[kRowsPerWarp];
 #pragma unroll
     for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-        const int tt = warp + nw * rr;
+        const int tt = warp + kWinWarps * rr;
+        d[rr] = F.one;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < NCW; ++c) {
             const int q = lane + 32 * c;
-            v[rr][c] = (tt < h && q < W) ? T[tt * WS + q] : 0u;
+            v[rr][c] = (tt < h && q < W) ? F.to(__ldg(A + (long long)tt * lda + q)) : 0u;
         }
+#pragma unroll
+        for (int c = NCW; c < NCA; ++c) v[rr][c] = (lane + 32 * (c - NCW) == tt) ? F.one : 0u;
     }
+    if (warp == 0) win_publish<NCW, NCA>(v[0], 0, 0, d[0], S, WA);
     int k = 0;
-    if (warp == 0)
-        win_publish<NC>(v[0], 0, 0, 0, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol, s_P, s_colpiv,
-                        s_rowpiv);
-    __syncthreads();
     for (int t = 0; t < h; ++t) {
-        const int b = t & 1;
-        const int j = s_j[b];
+        if (t % kWinWarps != warp && !mbar_wait(&S.bar[t], 0u, S.abort_flag, timeout, 1)) return -1;
+        const int j = S.jp[t];
         const int tn = t + 1;
-        const bool owner = tn < h && (tn % nw) == warp;
-        const int rn = tn / nw;
+        const bool own_next = tn < h && tn % kWinWarps == warp;
+        const int rn = tn / kWinWarps;
         if (j >= 0) {  // same value in every thread
-            const uint32_t P = s_Pv[b], Ps = s_Ps[b];
-            uint32_t u[NC];
+            const uint32_t P = S.Pv[t];
+            uint32_t w[NCA];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) u[c] = s_row[b * kMaxWin + lane + 32 * c];
-            uint32_t uq[NC];
-#pragma unroll
-            for (int c = 0; c < NC; ++c) uq[c] = s_rowq[b * kMaxWin + lane + 32 * c];
-            const int jc = j >> 5, jl = j & 31;
-            // the next row first (its owner publishes it right after), then the others
+            for (int c = 0; c < NCA; ++c) w[c] = F.neg(S.U[t * WA + lane + 32 * c]);
+            // the next row first (published right away), then the others
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-                if (!(owner && rr == rn)) continue;
-                uint32_t a;
-                if (win_update<NC>(v[rr], u, uq, jc, jl, P, Ps, p, a) && lane == 0) Lsm[tn * h + k] = a;
-                win_publish<NC>(v[rr], tn, k + 1, tn & 1, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol,
-                                s_P, s_colpiv, s_rowpiv);
+                if (!(own_next && rr == rn)) continue;
+                win_update<kBin, NCW, NCA>(F, v[rr], d[rr], w, j, P, S.Lsm + tn * h + k);
+                win_publish<NCW, NCA>(v[rr], tn, k + 1, d[rr], S, WA);
             }
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-                const int tt = warp + nw * rr;
+                const int tt = warp + kWinWarps * rr;
                 if (tt <= tn || tt >= h) continue;  // warp-uniform
-                uint32_t a;
-                if (win_update<NC>(v[rr], u, uq, jc, jl, P, Ps, p, a) && lane == 0) Lsm[tt * h + k] = a;
+                win_update<kBin, NCW, NCA>(F, v[rr], d[rr], w, j, P, S.Lsm + tt * h + k);
             }
             ++k;
-        } else if (owner) {
+        } else if (own_next) {
 #pragma unroll
             for (int rr = 0; rr < kRowsPerWarp; ++rr)
-                if (rr == rn)
-                    win_publish<NC>(v[rr], tn, k, tn & 1, p, mu, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow, s_pcol,
-                                    s_P, s_colpiv, s_rowpiv);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int rr = 0; rr < kRowsPerWarp; ++rr) {
-        const int tt = warp + nw * rr;
-        if (tt >= h) continue;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int q = lane + 32 * c;
-            if (q < WS) T[tt * WS + q] = v[rr][c];
+                if (rr == rn) win_publish<NCW, NCA>(v[rr], tn, k, d[rr], S, WA);
         }
     }
     return k;
 }
 
-__global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint32_t* __restrict__ A, long long lda,
-                                                                  int h, int W, int WS, uint32_t p,
-                                                                  unsigned long long mu, uint32_t two64p,
-                                                                  uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
-                                                                  long long ldu, uint32_t* __restrict__ rows,
-                                                                  long long ldr, LeafInfo* __restrict__ info) {
+template <bool kBin>
+__device__ __forceinline__ void window_body(const uint32_t* __restrict__ A, long long lda, int h, int W, int WS,
+                                            uint32_t p, unsigned long long mu, uint32_t two64p,
+                                            uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig, long long ldu,
+                                            uint32_t* __restrict__ rows, long long ldr,
+                                            LeafInfo* __restrict__ info) {
     extern __shared__ uint32_t sm[];
-    uint32_t* T = sm;              // [h][WS]
-    uint32_t* Lsm = T + h * WS;    // [h][h]: numerators a, then true multipliers (row t, pivot k)
-    uint32_t* Es = Lsm + h * h;    // [h][h]: E
-    uint32_t* Nd = Es + h * h;     // [h][h]: N by pivot row
-    uint32_t* Ui = Nd + h * h;     // [h][h]: U11^{-1}
-    uint32_t* TmE = Ui + h * h;          // [kTmWords]: doubling products (lower)
-    uint32_t* TmU = TmE + kTmWords;      // [kTmWords]: doubling products (upper)
-    __shared__ uint32_t s_row[2 * kMaxWin], s_rowq[2 * kMaxWin];
-    __shared__ uint32_t s_d[kLeafRows], s_invd[kLeafRows];
-    __shared__ uint32_t s_P[kLeafRows], s_invP[kLeafRows], s_c[kLeafRows];
-    __shared__ int s_prow[kLeafRows], s_pcol[kLeafRows], s_pre[kLeafRows + 1];
+    const int WA = WS + kExt;
+    uint32_t* U = sm;                          // [h][WA]
+    uint32_t* Lsm = U + h * WA;                // [h][h]
+    uint32_t* Us = Lsm + h * h;                // [64][64]: U11 (true values, plain form)
+    uint32_t* Ui = Us + kLeafRows * kLeafRows; // [64][64]: U11^{-1}
+    uint32_t* Tm = Ui + kLeafRows * kLeafRows; // [kTmWords]: doubling products
+    __shared__ uint64_t s_bar[kLeafRows];
+    __shared__ uint32_t s_Pv[kLeafRows], s_dv[kLeafRows], s_P[kLeafRows], s_invP[kLeafRows];
+    __shared__ int s_jp[kLeafRows], s_pre[kLeafRows], s_prow[kLeafRows], s_pcol[kLeafRows];
     __shared__ int s_rowpiv[kLeafRows], s_colpiv[kMaxWin];
     __shared__ int s_newrow[kLeafRows], s_newcol[kMaxWin];
-    __shared__ int s_j[2];
-    __shared__ uint32_t s_Pv[2], s_Ps[2];
-    __shared__ int s_cnt[kWinThreads / 32];
+    __shared__ int s_cnt[kWinWarps];
+    __shared__ int s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = kWinThreads / 32;
-    const uint32_t one = 1u % p;
+    const WinField<kBin> F(p, two64p, mu);
 
-    // eight independent loads in flight per thread before their stores
-    for (int base = 0; base < h * WS; base += 8 * blockDim.x) {
-        uint32_t v[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int idx = base + e * blockDim.x + tid;
-            const int r = idx / WS, q = idx - r * WS;
-            v[e] = (idx < h * WS && q < W) ? __ldg(A + (long long)r * lda + q) : 0u;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int idx = base + e * blockDim.x + tid;
-            if (idx < h * WS) T[idx] = v[e];
-        }
+    for (int idx = tid; idx < h * h; idx += blockDim.x) Lsm[idx] = 0u;
+    for (int idx = tid; idx < kLeafRows * kLeafRows; idx += blockDim.x) Us[idx] = Ui[idx] = 0u;
+    for (int x = tid; x < h; x += blockDim.x) {
+        s_rowpiv[x] = -1;
+        mbar_init(&s_bar[x], 32);
     }
-    for (int idx = tid; idx < h * h; idx += blockDim.x) {
-        Lsm[idx] = 0u;
-        Nd[idx] = 0u;
-        Ui[idx] = 0u;
-        const int r = idx / h;
-        Es[idx] = (idx - r * h == r) ? one : 0u;
-    }
-    for (int x = tid; x < h; x += blockDim.x) s_rowpiv[x] = -1;
     for (int x = tid; x < kMaxWin; x += blockDim.x) s_colpiv[x] = -1;
+    if (tid == 0) {
+        s_abort = 0;
+        info->timeout = 0;
+    }
     __syncthreads();
 
-    const int r = WS <= 64   ? win_eliminate<2>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
-                                                s_pcol, s_P, s_colpiv, s_rowpiv)
-                  : WS <= 96 ? win_eliminate<3>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
-                                                s_pcol, s_P, s_colpiv, s_rowpiv)
-                             : win_eliminate<8>(T, WS, W, h, p, mu, Lsm, s_row, s_rowq, s_j, s_Pv, s_Ps, s_prow,
-                                                s_pcol, s_P, s_colpiv, s_rowpiv);
+    const WinState S{U, Lsm, s_bar, s_jp, s_Pv, s_dv, s_pre, s_prow, s_pcol, s_P, s_colpiv, s_rowpiv, &s_abort};
+    int r;
+    if (kBin)
+        r = win_eliminate<kBin, 8>(F, A, lda, h, W, S, &info->timeout);
+    else
+        r = WS <= 64   ? win_eliminate<kBin, 2>(F, A, lda, h, W, S, &info->timeout)
+            : WS <= 96 ? win_eliminate<kBin, 3>(F, A, lda, h, W, S, &info->timeout)
+                       : win_eliminate<kBin, 8>(F, A, lda, h, W, S, &info->timeout);
     __syncthreads();
+    if (s_abort) {  // a wait ran out (info->timeout is set): nothing else is written
+        if (tid == 0) {
+            info->rank = 0;
+            info->fail = 0;
+            info->ident = 1;
+            info->firstnz = INT_MAX;
+        }
+        return;
+    }
 
     // 1 / P_k for every pivot: prefix and suffix products over warp 0 (two per lane), one inverse
     if (warp == 0) {
-        const uint32_t v0 = 2 * lane < r ? s_P[2 * lane] : one;
-        const uint32_t v1 = 2 * lane + 1 < r ? s_P[2 * lane + 1] : one;
-        const uint32_t loc = mulm(v0, v1, p, mu);
+        const uint32_t v0 = 2 * lane < r ? s_P[2 * lane] : F.one;
+        const uint32_t v1 = 2 * lane + 1 < r ? s_P[2 * lane + 1] : F.one;
+        const uint32_t loc = F.mul(v0, v1);
         uint32_t inc = loc, sinc = loc;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc = mulm(inc, x, p, mu);
+            if (lane >= o) inc = F.mul(inc, x);
             const uint32_t y = __shfl_down_sync(0xffffffffu, sinc, o);
-            if (lane + o < 32) sinc = mulm(sinc, y, p, mu);
+            if (lane + o < 32) sinc = F.mul(sinc, y);
         }
         uint32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
         uint32_t sexc = __shfl_down_sync(0xffffffffu, sinc, 1);
-        if (lane == 0) exc = one;
-        if (lane == 31) sexc = one;
+        if (lane == 0) exc = F.one;
+        if (lane == 31) sexc = F.one;
         const uint32_t total = __shfl_sync(0xffffffffu, inc, 31);
-        uint32_t itot = lane == 0 ? inv_mod_dev(total, p) : 0u;
+        uint32_t itot = lane == 0 ? F.inv(total) : 0u;
         itot = __shfl_sync(0xffffffffu, itot, 0);
-        const uint32_t base = mulm(mulm(itot, exc, p, mu), sexc, p, mu);
-        if (2 * lane < r) s_invP[2 * lane] = mulm(base, v1, p, mu);
-        if (2 * lane + 1 < r) s_invP[2 * lane + 1] = mulm(base, v0, p, mu);
-    }
-    // number of pivot rows above each row
-    for (int x = tid; x <= h; x += blockDim.x) {
-        int cnt = 0;
-        for (int q = 0; q < r; ++q) cnt += s_prow[q] < x;
-        s_pre[x] = cnt;
+        const uint32_t base = F.mul(F.mul(itot, exc), sexc);
+        if (2 * lane < r) s_invP[2 * lane] = F.mul(base, v1);
+        if (2 * lane + 1 < r) s_invP[2 * lane + 1] = F.mul(base, v0);
     }
     __syncthreads();
-    // scale of each row: the product of the pivots of the steps that touched it
-    // (those whose numerator is non-zero), one warp per row
-    for (int t = warp; t < h; t += nwarps) {
-        const int pre = s_pre[t];
-        const uint32_t g0 = lane < pre && Lsm[t * h + lane] ? s_P[lane] : one;
-        const uint32_t g1 = lane + 32 < pre && Lsm[t * h + lane + 32] ? s_P[lane + 32] : one;
-        uint32_t g = mulm(g0, g1, p, mu);
-        for (int o = 16; o > 0; o >>= 1) g = mulm(g, __shfl_xor_sync(0xffffffffu, g, o), p, mu);
-        if (lane == 0) s_d[t] = g;
-    }
-    __syncthreads();
-    // c_k = d_{prow k} / P_k = 1 / (true pivot k)
-    for (int x = tid; x < r; x += blockDim.x) {
-        s_c[x] = mulm(s_d[s_prow[x]], s_invP[x], p, mu);
-        Ui[x * h + x] = s_c[x];
-    }
-    __syncthreads();
-    // true multipliers l_tk = a_tk c_k / (d_t before step k), one warp per row:
-    // 1 / d_t before step k is the product of 1 / P_k' over the earlier steps
-    // that touched row t (exclusive prefix products over the pivots)
-    for (int t = warp; t < h; t += nwarps) {
+    // per row (one warp each): the true multipliers l_tk = a_tk c_k / (d_t
+    // before step k), c_k = d_{prow k} / P_k = 1 / (true pivot k); 1 / d_t
+    // before step k is the product of 1 / P_k' over the earlier steps that
+    // touched row t (exclusive prefix products); then the stored row times
+    // 1 / d_t: the true U row (pivot rows) and row t of E
+    for (int t = warp; t < h; t += kWinWarps) {
         const int pre = s_pre[t];
         const uint32_t n0 = lane < pre ? Lsm[t * h + lane] : 0u;
         const uint32_t n1 = lane + 32 < pre ? Lsm[t * h + lane + 32] : 0u;
-        const uint32_t f0 = n0 ? s_invP[lane] : one, f1 = n1 ? s_invP[lane + 32] : one;
+        const uint32_t f0 = n0 ? s_invP[lane] : F.one, f1 = n1 ? s_invP[lane + 32] : F.one;
         uint32_t i0 = f0, i1 = f1;
+#pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x0 = __shfl_up_sync(0xffffffffu, i0, o);
             const uint32_t x1 = __shfl_up_sync(0xffffffffu, i1, o);
             if (lane >= o) {
-                i0 = mulm(i0, x0, p, mu);
-                i1 = mulm(i1, x1, p, mu);
+                i0 = F.mul(i0, x0);
+                i1 = F.mul(i1, x1);
             }
         }
         const uint32_t tot0 = __shfl_sync(0xffffffffu, i0, 31), tot1 = __shfl_sync(0xffffffffu, i1, 31);
         uint32_t e0 = __shfl_up_sync(0xffffffffu, i0, 1), e1 = __shfl_up_sync(0xffffffffu, i1, 1);
-        if (lane == 0) {
-            e0 = one;
-            e1 = one;
-        }
-        e1 = mulm(e1, tot0, p, mu);
-        if (n0) {
-            const uint32_t l = mulm(mulm(n0, s_c[lane], p, mu), e0, p, mu);
-            Lsm[t * h + lane] = l;
-            Nd[t * h + s_prow[lane]] = l;
-        }
-        if (n1) {
-            const uint32_t l = mulm(mulm(n1, s_c[lane + 32], p, mu), e1, p, mu);
-            Lsm[t * h + lane + 32] = l;
-            Nd[t * h + s_prow[lane + 32]] = l;
-        }
-        if (lane == 0) s_invd[t] = mulm(tot0, tot1, p, mu);
+        if (lane == 0) e0 = e1 = F.one;
+        e1 = F.mul(e1, tot0);
+        if (n0) Lsm[t * h + lane] = F.mul(F.mul(n0, F.mul(s_dv[s_prow[lane]], s_invP[lane])), e0);
+        if (n1) Lsm[t * h + lane + 32] = F.mul(F.mul(n1, F.mul(s_dv[s_prow[lane + 32]], s_invP[lane + 32])), e1);
+        const uint32_t invd = F.mul(tot0, tot1);
+        for (int q = lane; q < WA; q += 32) U[t * WA + q] = F.mul(U[t * WA + q], invd);
     }
     __syncthreads();
-    // true U rows (the other rows are zero on the window)
-    for (int idx = tid; idx < h * WS; idx += blockDim.x) {
-        const int t = idx / WS;
-        if (s_rowpiv[t] >= 0 && T[idx]) T[idx] = mulm(T[idx], s_invd[t], p, mu);
+    // U11 and the diagonal of its inverse (plain form, zero outside r x r)
+    for (int idx = tid; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, q = idx - i * r;
+        if (q > i) Us[i * kLeafRows + q] = F.from(U[s_prow[i] * WA + s_pcol[q]]);
+        else if (q == i) {
+            Us[i * kLeafRows + i] = F.from(U[s_prow[i] * WA + s_pcol[i]]);
+            Ui[i * kLeafRows + i] = F.from(F.mul(s_dv[s_prow[i]], s_invP[i]));
+        }
     }
     __syncthreads();
-    // doubling for E (h x h, unit lower) and U11^{-1} (r x r, upper); level s
-    // pairs the blocks [b0, b0 + s) and [b0 + s, b0 + 2s), b0 = 2 s pr
-    for (int ls = 0; (1 << ls) < h; ++ls) {
+    // doubling for U11^{-1}: level s pairs the blocks [b0, b0 + s) and
+    // [b0 + s, b0 + 2 s), b0 = 2 s pr (b0 + 2 s <= 64 at every level)
+    for (int ls = 0; (1 << ls) < r; ++ls) {
         const int s = 1 << ls;
-        const int npE = (h - s + 2 * s - 1) / (2 * s);
-        const int npU = r > s ? (r - s + 2 * s - 1) / (2 * s) : 0;
-        // phase A: TmE = N21 E11 (ds x s per pair), TmU = U12 D^{-1} (s x du per pair)
-        for (int idx = tid; idx < (npE + npU) << (2 * ls); idx += blockDim.x) {
-            const bool lower = idx < (npE << (2 * ls));
-            const int li = lower ? idx : idx - (npE << (2 * ls));
-            const int pr = li >> (2 * ls), rem = li & ((s << ls) - 1);
+        const int np = (r - s + 2 * s - 1) / (2 * s);
+        const int nout = np << (2 * ls);
+        // Tm = C D^{-1} (s x s per pair)
+        for (int idx = tid; idx < nout; idx += blockDim.x) {
+            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
             const int i = rem >> ls, jj = rem & (s - 1);
             const int b0 = 2 * s * pr;
+            const uint32_t* crow = Us + (b0 + i) * kLeafRows + b0 + s;
+            const uint32_t* dcol = Ui + (b0 + s) * kLeafRows + b0 + s + jj;
             Acc128 acc;
-            if (lower) {
-                if (i >= min(s, h - b0 - s)) continue;
-                const uint32_t* nrow = Nd + (b0 + s + i) * h + b0;
-                for (int l = jj; l < s; ++l) acc.add((unsigned long long)nrow[l] * Es[(b0 + l) * h + b0 + jj]);
-                TmE[li] = acc.mod(p, mu, two64p);
-            } else {
-                if (jj >= min(s, r - b0 - s)) continue;
-                const uint32_t* urow = T + s_prow[b0 + i] * WS;
-                for (int l = 0; l <= jj; ++l)
-                    acc.add((unsigned long long)urow[s_pcol[b0 + s + l]] * Ui[(b0 + s + l) * h + b0 + s + jj]);
-                TmU[li] = acc.mod(p, mu, two64p);
-            }
+#pragma unroll 8
+            for (int l = 0; l < s; ++l) acc.add((unsigned long long)crow[l] * dcol[l * kLeafRows]);
+            Tm[idx] = acc.mod(p, mu, two64p);
         }
         __syncthreads();
-        // phase B: E21 = -E22 TmE, (U11^{-1})12 = -A^{-1} TmU
-        for (int idx = tid; idx < (npE + npU) << (2 * ls); idx += blockDim.x) {
-            const bool lower = idx < (npE << (2 * ls));
-            const int li = lower ? idx : idx - (npE << (2 * ls));
-            const int pr = li >> (2 * ls), rem = li & ((s << ls) - 1);
+        // (U11^{-1})12 = -A^{-1} Tm
+        for (int idx = tid; idx < nout; idx += blockDim.x) {
+            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
             const int i = rem >> ls, jj = rem & (s - 1);
             const int b0 = 2 * s * pr;
-            const int base = pr << (2 * ls);
+            const uint32_t* arow = Ui + (b0 + i) * kLeafRows + b0;
+            const uint32_t* tcol = Tm + (pr << (2 * ls)) + jj;
             Acc128 acc;
-            if (lower) {
-                if (i >= min(s, h - b0 - s)) continue;
-                const uint32_t* erow = Es + (b0 + s + i) * h + b0 + s;
-                for (int l = 0; l <= i; ++l) acc.add((unsigned long long)erow[l] * TmE[base + (l << ls) + jj]);
-                const uint32_t v = acc.mod(p, mu, two64p);
-                Es[(b0 + s + i) * h + b0 + jj] = v ? p - v : 0u;
-            } else {
-                if (jj >= min(s, r - b0 - s)) continue;
-                const uint32_t* arow = Ui + (b0 + i) * h + b0;
-                for (int l = i; l < s; ++l) acc.add((unsigned long long)arow[l] * TmU[base + (l << ls) + jj]);
-                const uint32_t v = acc.mod(p, mu, two64p);
-                Ui[(b0 + i) * h + b0 + s + jj] = v ? p - v : 0u;
-            }
+#pragma unroll 8
+            for (int l = 0; l < s; ++l) acc.add((unsigned long long)arow[l] * tcol[l << ls]);
+            const uint32_t v = acc.mod(p, mu, two64p);
+            Ui[(b0 + i) * kLeafRows + b0 + s + jj] = v ? p - v : 0u;
         }
         __syncthreads();
     }
@@ -510,11 +495,14 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
         if (x < r) info->prow[x] = s_prow[x];
     }
     for (int x = tid; x < W; x += blockDim.x) info->newcol[x] = s_newcol[x];
-    for (int idx = tid; idx < h * h; idx += blockDim.x) Eg[idx] = Es[idx];
+    for (int idx = tid; idx < h * h; idx += blockDim.x) {
+        const int t = idx / h, q = idx - t * h;
+        Eg[idx] = F.from(U[t * WA + WS + q]);
+    }
     if (Uig)
         for (int idx = tid; idx < r * r; idx += blockDim.x) {
             const int i = idx / r, q = idx - i * r;
-            Uig[(long long)i * ldu + q] = Ui[i * h + q];
+            Uig[(long long)i * ldu + q] = Ui[i * kLeafRows + q];
         }
     // the leaf's new rows on the window: multipliers left of the diagonal of
     // the first r columns, the pivot rows' values on and right of it
@@ -523,11 +511,23 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
         const int t = s_newrow[i];
         uint32_t v;
         if (q < min(i, r))
-            v = Lsm[t * h + q];
+            v = F.from(Lsm[t * h + q]);
         else
-            v = i < r ? T[t * WS + s_newcol[q]] : 0u;
+            v = i < r ? F.from(U[t * WA + s_newcol[q]]) : 0u;
         rows[(long long)i * ldr + q] = v;
     }
+}
+
+__global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint32_t* __restrict__ A, long long lda,
+                                                                  int h, int W, int WS, uint32_t p,
+                                                                  unsigned long long mu, uint32_t two64p,
+                                                                  uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
+                                                                  long long ldu, uint32_t* __restrict__ rows,
+                                                                  long long ldr, LeafInfo* __restrict__ info) {
+    if (p == 2u)
+        window_body<true>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info);
+    else
+        window_body<false>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info);
 }
 
 // The rest of the leaf's rows.  Blocks [0, nleft): columns [0, c), the rows
@@ -878,7 +878,9 @@ const SideRes* side_resources() {
 
 ffgpu_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA; }
 
-size_t smem_window(int h, int WS) { return (size_t(h) * WS + 4 * size_t(h) * h + 2 * size_t(kTmWords)) * 4; }
+size_t smem_window(int h, int WS) {
+    return (size_t(h) * (WS + kExt) + size_t(h) * h + 2 * size_t(kLeafRows) * kLeafRows + size_t(kTmWords)) * 4;
+}
 size_t smem_rest(int h) { return size_t(h) * kRestCols * 4 + size_t(h) * h * 4; }
 
 ffgpu_status set_attrs() {
@@ -900,7 +902,8 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
                   int64_t ldu) {
     const int64_t w = x.n - c;
     const int W = (int)std::min<int64_t>(x.win, w);
-    const int WS = (W + 31) & ~31;
+    // the kernel's register layouts: 64, 96 or 256 window columns (p = 2: 256)
+    const int WS = x.p == 2 ? kMaxWin : W <= 64 ? 64 : W <= 96 ? 96 : kMaxWin;
     uint32_t* Ab = x.A + rb * x.lda;
     ffgpu_status st = cuda_ok(timed_launch("lqup_window", x.s, [&] {
         lqup_window_kernel<<<1, kWinThreads, smem_window((int)h, WS), x.s>>>(
@@ -912,9 +915,10 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     // non-zero, so the rest of the leaf needs no second round trip.  (A
     // pending side-stream update runs meanwhile: the window kernel reads and
     // writes only this leaf's rows and the leaf's scratch.)
-    if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) != FFGPU_OK)
+    if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 5 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) != FFGPU_OK)
         return st;
     if ((st = cuda_ok(cudaStreamSynchronize(x.s))) != FFGPU_OK) return st;
+    if (x.host[4]) return FFGPU_ERR_TIMEOUT;
     const int r = x.host[0];
     if ((st = join(x)) != FFGPU_OK) return st;
     const int nleft = (int)((c + kThreads - 1) / kThreads);
