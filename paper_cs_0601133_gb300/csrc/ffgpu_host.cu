@@ -340,15 +340,94 @@ bool use_pair_kernel(int64_t m, int grid) {
     return m > kTileM;
 }
 
-// Workspace bytes for the largest launch of a problem.
-size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
+// Schedule of a CTA-pair launch: np pairs, tiles dealt round-robin, and a
+// cut last wave (split > 1): when the last wave has rem tiles, at most half
+// the pairs, each of them is cut into split = min(pairs / rem, H, 4) parts of
+// its H chunks, so that that wave takes ceil(H / split) chunks instead of H.
+// A problem with fewer tiles than pairs is one such wave, on rem x split
+// pairs.  An even channel count is required (the kernel's job pairs never
+// mix two segments).  FFGPU_STREAMK=0 keeps the round-robin schedule.
+struct PairSched {
+    int np = 1;
+    int dp = 0, split = 0, rem = 0;
+};
+
+static int64_t pair_tiles(int64_t m, int64_t n) {
+    return ((m + 2 * kTileM - 1) / (2 * kTileM)) * ((n + kTileN - 1) / kTileN);
+}
+
+// T tiles, at most np_max pairs, H chunks per tile, nch channels; cut = false
+// gives the round-robin schedule.
+static PairSched pair_sched(int64_t T, int np_max, int64_t H, int nch, bool cut) {
+    PairSched s;
+    np_max = std::max(1, np_max);
+    s.np = (int)std::max<int64_t>(1, std::min<int64_t>(T, np_max));
+    const char* e = std::getenv("FFGPU_STREAMK");
+    if (!cut || (e && std::strcmp(e, "0") == 0) || np_max < 2 || H < 2 || (nch & 1)) return s;
+    const int64_t rem = T < np_max ? T : T % np_max;
+    if (rem == 0) return s;
+    const int64_t split = std::min<int64_t>(std::min<int64_t>(np_max / rem, H), 4);
+    if (split < 2) return s;
+    if (T < np_max) s.np = (int)(T * split);
+    s.dp = (int)(T - rem);
+    s.split = (int)split;
+    s.rem = (int)rem;
+    return s;
+}
+
+// Pairs a launch may use: at most cap CTAs, and no more clusters than fit at once.
+static int pair_limit(int cap) { return std::max(1, std::min(cap / 2, rns_gemm_pair_max_clusters())); }
+
+// Bytes of the cut tiles' residues and flags for np pairs (one flag per
+// pair, CTA, channel and epilogue warp).
+static size_t sk_part_bytes(int np, int nch) { return size_t(np) * 2 * nch * kTileM * kTileN * sizeof(short); }
+static size_t sk_flag_bytes(int np, int nch) { return size_t(np) * 2 * nch * kSkFlagsPerCta * sizeof(int); }
+
+// Workspace of a launch: the layout (residue slots for max(grid, 2 np) CTAs,
+// the planes), then the residues and flags of a cut last wave.
+struct LaunchLayout {
+    Layout L;
+    size_t part_off = 0, flag_off = 0, total = 0;
+};
+
+static LaunchLayout launch_layout(int64_t m, int64_t n, int64_t kp, int nch, int grid, bool pair,
+                                  const PairSched& ps) {
+    LaunchLayout X;
+    X.L = layout_for(m, n, kp, nch, pair ? std::max(grid, 2 * ps.np) : grid);
+    X.total = X.L.total;
+    if (pair && ps.split > 1) {
+        X.part_off = align256(X.total);
+        X.flag_off = X.part_off + align256(sk_part_bytes(ps.np, nch));
+        X.total = X.flag_off + align256(sk_flag_bytes(ps.np, nch));
+    }
+    return X;
+}
+
+static size_t fgemm_ws_bytes_impl(int64_t m, int64_t n, int64_t k, uint32_t p, int sms, bool cut) {
     if (m == 0 || n == 0 || k == 0) return 0;
     RnsPlan pl;
     make_plan(p, k, pl);
-    const int64_t ks = std::min<int64_t>(k, pl.k_slice);
-    const size_t rns = layout_for(m, n, round64(ks), pl.nch, grid_for_tiles(m, n, sms)).total;
+    const int64_t ks = std::min<int64_t>(k, pl.k_slice), kp = round64(ks);
+    const int grid = grid_for_tiles(m, n, sms);
+    const bool pair = use_pair_kernel(m, grid);
+    const int64_t cs = chunk_steps_for(pl);
+    const PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(sms), (kp / kTileK + cs - 1) / cs, pl.nch, cut)
+                              : PairSched();
+    const size_t rns = launch_layout(m, n, kp, pl.nch, grid, pair, ps).total;
     // a small product runs on the CUDA cores, its k-split partial sums in the workspace
     return fgemm_small(m, n, k) ? std::max(rns, small_ws_bytes(m, n, k, sms)) : rns;
+}
+
+// Workspace bytes for the largest launch of a problem (with the residues of a
+// cut last wave where that schedule applies).
+size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
+    return fgemm_ws_bytes_impl(m, n, k, p, sms, true);
+}
+
+// The same for the round-robin schedule: a launch whose workspace has no room
+// for a cut last wave keeps that schedule.
+size_t fgemm_ws_bytes_min(int64_t m, int64_t n, int64_t k, uint32_t p, int sms) {
+    return fgemm_ws_bytes_impl(m, n, k, p, sms, false);
 }
 
 // The launch sequence: per slice of the inner dimension, convert A and B to
@@ -416,8 +495,21 @@ ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint
         RnsPlan pl;
         make_plan(p, ks, pl);
         const int64_t kp = round64(ks);
-        const Layout L = layout_for(m, n, kp, pl.nch, grid);
-        if (L.total > ws_bytes) return FFGPU_ERR_NOMEM;
+        // CTA-pair kernel (256 x 256 tiles) unless the problem has a single row
+        // block or the caller forces the one-CTA kernel; its schedule sets the
+        // number of residue slots, so it is chosen before the layout
+        const bool pair = use_pair_kernel(m, grid);
+        const int64_t cs = chunk_steps_for(pl);
+        const int64_t H = (kp / kTileK + cs - 1) / cs;
+        const int cap = max_grid > 0 ? std::min(sm_count(dev), max_grid) : sm_count(dev);
+        PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(cap), H, pl.nch, true) : PairSched();
+        LaunchLayout X = launch_layout(m, n, kp, pl.nch, grid, pair, ps);
+        if (X.total > ws_bytes && ps.split > 1) {  // no room for a cut last wave: round-robin
+            ps = pair_sched(pair_tiles(m, n), pair_limit(cap), H, pl.nch, false);
+            X = launch_layout(m, n, kp, pl.nch, grid, pair, ps);
+        }
+        if (X.total > ws_bytes) return FFGPU_ERR_NOMEM;
+        const Layout& L = X.L;
         unsigned char* wsb = static_cast<unsigned char*>(ws);
 
         ConvertParams cp;
@@ -457,9 +549,6 @@ ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint
             return FFGPU_ERR_CUDA;
         }
 
-        // CTA-pair kernel (256 x 256 tiles) unless the problem has a single row
-        // block or the caller forces the one-CTA kernel
-        const bool pair = use_pair_kernel(m, grid);
         CUtensorMap mapA, mapB;
         if (!encode_planes(&mapA, wsb + L.planesA, kp, m, pl.nch, kTileM) ||
             !encode_planes(&mapB, wsb + L.planesB, kp, n, pl.nch, pair ? 128 : kTileN))
@@ -477,8 +566,17 @@ ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint
         P.err = err;
         P.raster = g_tune_override.raster > 0 ? g_tune_override.raster : kRasterRows;
         if (pair) {
-            const int pgrid = 2 * std::max(1, std::min(std::min(P.num_tiles, grid / 2), rns_gemm_pair_max_clusters()));
-            if (launch("rns_gemm_pair", [&] { return launch_rns_gemm_pair(mapA, mapB, P, pgrid, s); }) != cudaSuccess)
+            if (ps.split > 1) {
+                P.sk_dp = ps.dp;
+                P.sk_split = ps.split;
+                P.sk_rem = ps.rem;
+                P.sk_part = reinterpret_cast<short*>(wsb + X.part_off);
+                P.sk_flags = reinterpret_cast<int*>(wsb + X.flag_off);
+                if (cudaMemsetAsync(P.sk_flags, 0, sk_flag_bytes(ps.np, pl.nch), s) != cudaSuccess)
+                    return FFGPU_ERR_CUDA;
+            }
+            const int np = ps.np;
+            if (launch("rns_gemm_pair", [&] { return launch_rns_gemm_pair(mapA, mapB, P, 2 * np, s); }) != cudaSuccess)
                 return FFGPU_ERR_CUDA;
         } else if (launch("rns_gemm", [&] { return launch_rns_gemm(mapA, mapB, P, grid, s); }) != cudaSuccess) {
             return FFGPU_ERR_CUDA;

@@ -35,6 +35,7 @@ enum DevErr : int {
     kDevTimeoutEpilogue = 3,
     kDevTimeoutDrain = 4,
     kDevSingular = 5,  // a non-unit triangular solve met a non-invertible diagonal entry
+    kDevTimeoutStreamK = 6,  // a cut tile's head waited too long for its tail's residues
 };
 
 struct RnsPlan {
@@ -88,7 +89,13 @@ struct RnsGemmParams {
     size_t slot_stride;            // bytes of one slot: channels x 128 x 256
     int* err;                      // device error word
     int raster;                    // tile rows per band of the tile order (> 0)
+    // CTA-pair kernel, cut last wave (sk_split > 1): the sk_rem tiles from
+    // sk_dp on, each in sk_split parts of its chunks
+    int sk_dp, sk_split, sk_rem;
+    short* sk_part;                // tails' residues: pairs x 2 x channels x 128 x 256 int16
+    int* sk_flags;                 // pairs x 2 x channels x kSkFlagsPerCta, zero at launch
 };
+constexpr int kSkFlagsPerCta = 8;  // one per epilogue warp
 
 // Grouped launch: jobs (instance, tile, channel), listed per CTA, with
 // everything the producer, MMA and epilogue roles need packed in 32 bytes so
@@ -248,6 +255,7 @@ ffgpu_status fgemm_run(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alp
                        uint32_t beta, uint32_t* C, int64_t ldc, void* ws, size_t ws_bytes,
                        int* err, cudaStream_t s, int max_grid, bool untimed);
 size_t fgemm_ws_bytes(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);
+size_t fgemm_ws_bytes_min(int64_t m, int64_t n, int64_t k, uint32_t p, int sms);  // without stream-K residues
 // The tensor-core route alone (fgemm_run dispatches small products to the
 // CUDA-core kernel of small_gemm.cu, everything else here).
 ffgpu_status fgemm_run_rns(int64_t m, int64_t n, int64_t k, uint32_t p, uint32_t alpha,

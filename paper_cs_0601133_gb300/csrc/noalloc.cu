@@ -76,7 +76,7 @@ extern "C" ffgpu_status ffgpu_fgemm_noalloc(int64_t m, int64_t n, int64_t k, uin
     // needs the tensor-core layout (planes, and the slots of at most
     // kNoAllocMaxGrid persistent CTAs).
     const size_t need = fgemm_small(m, n, k) ? small_ws_bytes(m, n, k, sm_count(dev))
-                                             : fgemm_ws_bytes(m, n, k, p, kNoAllocMaxGrid);
+                                             : fgemm_ws_bytes_min(m, n, k, p, kNoAllocMaxGrid);
     if (need > kNoAllocScratchBytes - kNoAllocErrBytes) return FFGPU_ERR_NOMEM;  // beyond the static maximum
     unsigned char* scratch = nullptr;
     st = scratch_address(&scratch);

@@ -41,6 +41,7 @@ namespace ffgpu {
 namespace {
 
 constexpr int kEpiWarps = 8;
+static_assert(kEpiWarps == kSkFlagsPerCta, "one stream-K flag per epilogue warp");
 constexpr int kCombineWarps = 6;
 constexpr int kThreads = 32 * (2 + kEpiWarps + kCombineWarps);  // 2 control warps
 constexpr int kFirstCombineWarp = 10;
@@ -778,12 +779,156 @@ __global__ void __launch_bounds__(kThreads, 1)
 // leader's full[] barrier; the leader's commits arrive on empty[] and
 // acc_full[] in both CTAs; both CTAs' epilogues arrive on the leader's
 // acc_empty[] (16 warps).
+//
+// Schedule.  Tiles are dealt round-robin to the pairs.  When the last wave
+// has fewer tiles (rem) than half the pairs, its tiles are instead cut along
+// the inner dimension into sk_split equal parts of their chunks, part j of
+// tile r on pair r + j rem, so that the last wave keeps rem x sk_split pairs
+// busy for a fraction of the time.  The parts of a wave run together, at the
+// same offsets of the inner dimension, as the tiles of a full wave do (their
+// operand blocks are shared through L2 the same way).  Parts j > 0 ("tails")
+// reduce each channel's accumulator mod m_c and hand the residues (int16) to
+// part 0 (the "head") through global memory, raising a flag per channel and
+// epilogue warp; the head adds them to its own accumulators before that
+// channel's CRT digits.
+// The head's wait is bounded and nothing waits on a head.
 constexpr int kPStages = 6;
 constexpr uint32_t kPABytes = 128 * kTileK * 2;
 constexpr uint32_t kPBBytes = 128 * kTileK * 2;
 constexpr uint32_t kPStageBytes = kPABytes + kPBBytes;
 constexpr size_t kPairSmemBytes = 1024 + size_t(kPStages) * kPStageBytes + kConstBytes + 256;
 constexpr int kPairTile = 256;
+
+// The segments of one pair (the same in every role of both CTAs): its
+// round-robin tiles, then, in a cut last wave, one part of a tile.
+struct PairSegs {
+    int pair, np, H, ndp, split, rem;
+    __device__ PairSegs(const RnsGemmParams& P, int pair_, int np_, int H_) : pair(pair_), np(np_), H(H_) {
+        if (P.sk_split > 1) {
+            ndp = P.sk_dp / np;
+            split = P.sk_split;
+            rem = P.sk_rem;
+        } else {
+            ndp = pair < P.num_tiles ? (P.num_tiles - 1 - pair) / np + 1 : 0;
+            split = 0;
+            rem = 1;
+        }
+    }
+    __device__ bool in_split() const { return split > 1 && pair < rem * split; }
+    __device__ int count() const { return ndp + (in_split() ? 1 : 0); }
+    // segment j: tile t, chunks [hb, he), kind 0 whole, 1 head, 2 tail
+    __device__ void get(int j, int& t, int& hb, int& he, int& kind) const {
+        if (j < ndp) {
+            t = pair + j * np;
+            hb = 0;
+            he = H;
+            kind = 0;
+            return;
+        }
+        const int part = pair / rem;
+        t = ndp * np + pair % rem;
+        hb = part * H / split;
+        he = (part + 1) * H / split;
+        kind = part == 0 ? 1 : 2;
+    }
+    __device__ bool has_tail() const { return in_split() && pair >= rem; }  // the last segment
+    __device__ int digit_ord(int j) const { return j; }
+    __device__ int digit_tiles() const { return count() - (has_tail() ? 1 : 0); }
+};
+
+// Partial residues of a tail: int16 per entry, [pair][rank][channel][128][256].
+__device__ __forceinline__ short* sk_part_at(const RnsGemmParams& P, int pair, uint32_t rank, int c) {
+    return P.sk_part + ((size_t(pair) * 2 + rank) * P.inst.nch + c) * size_t(kTileM) * kTileN;
+}
+
+__device__ __forceinline__ uint32_t pack_s16(float a, float b) {
+    return (uint32_t)(uint16_t)(short)__float2int_rn(a) | ((uint32_t)(uint16_t)(short)__float2int_rn(b) << 16);
+}
+
+// Tail of a cut tile: this lane's 128 columns reduced mod m_c (|r| <= m_c/2 + 1)
+// and stored as int16 at dst.
+__device__ __forceinline__ void epi_partial(uint32_t tbase, float mf, float im, short* dst) {
+#pragma unroll 1
+    for (int cc = 0; cc < 4; cc += 2) {
+        uint32_t v[32], v2[32];
+        tc_ld32(tbase + cc * 32, v);
+        tc_ld32(tbase + cc * 32 + 32, v2);
+        tc_wait_ld();
+        uint32_t w[32];
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+            const float x0 = __uint_as_float(v[i]), x1 = __uint_as_float(v[i + 1]);
+            const float y0 = __uint_as_float(v2[i]), y1 = __uint_as_float(v2[i + 1]);
+            w[i / 2] = pack_s16(fmaf(-(fmaf(x0, im, kRoundMagic) - kRoundMagic), mf, x0),
+                                fmaf(-(fmaf(x1, im, kRoundMagic) - kRoundMagic), mf, x1));
+            w[16 + i / 2] = pack_s16(fmaf(-(fmaf(y0, im, kRoundMagic) - kRoundMagic), mf, y0),
+                                     fmaf(-(fmaf(y1, im, kRoundMagic) - kRoundMagic), mf, y1));
+        }
+        uint4* d4 = reinterpret_cast<uint4*>(dst + cc * 32);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) d4[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    }
+}
+
+__device__ __forceinline__ void add_s16(uint32_t (&v)[32], const uint4* src) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 q = __ldcg(src + i);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = 8 * i + 2 * e;
+            v[j] = __float_as_uint(__uint_as_float(v[j]) + (float)(short)(w[e] & 0xFFFFu));
+            v[j + 1] = __float_as_uint(__uint_as_float(v[j + 1]) + (float)(short)(w[e] >> 16));
+        }
+    }
+}
+
+// Head of a cut tile: epi_digits on the accumulator plus the residues of the
+// tails on pairs tp0, tp0 + step, ... below tp_end (this lane's 128 int16 of
+// each), one 32-column load at a time (a head is at most one tile per pair).
+// The sums stay below 2^24 in magnitude (at most three tails of |r| <= 129).
+__device__ __forceinline__ void epi_digits_sk(uint32_t tbase, float mf, float im, float uf, float uim,
+                                              unsigned char* dst, bool row_ok, int col_lim, const RnsGemmParams& P,
+                                              int tp0, int tp_end, int step, uint32_t rank, int c, size_t row_off) {
+#pragma unroll 1
+    for (int cc = 0; cc < 4; ++cc) {
+        uint32_t v[32];
+        tc_ld32(tbase + cc * 32, v);
+        tc_wait_ld();
+#pragma unroll 1
+        for (int tp = tp0; tp < tp_end; tp += step)
+            add_s16(v, reinterpret_cast<const uint4*>(sk_part_at(P, tp, rank, c) + row_off + cc * 32));
+        if (row_ok && cc * 32 < col_lim) store_digits(v, mf, im, uf, uim, dst + cc * 32);
+    }
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait for a tail's flag (every lane polls); false on timeout or abort.
+__device__ __forceinline__ bool sk_wait(const int* flag, volatile int* abort_flag, int* err) {
+    if (ld_acquire_gpu(flag)) return true;
+    const long long t0 = clock64();
+    uint32_t it = 0;
+    while (true) {
+        if (ld_acquire_gpu(flag)) return true;
+        if ((++it & 63u) == 0) {
+            if (*abort_flag) return false;
+            if (clock64() - t0 > kWaitLimitCycles) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, (int)kDevTimeoutStreamK);
+                return false;
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     rns_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -813,11 +958,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     int* err = P.err;
 
     const int pair = (int)blockIdx.x >> 1, npairs = (int)gridDim.x >> 1;
-    const int my_tiles = pair < P.num_tiles ? (P.num_tiles - 1 - pair) / npairs + 1 : 0;
     const int nch = I.nch;
-    const int J = my_tiles * nch;
     const int CS = I.chunk_steps;
     const int H = (I.ksteps + CS - 1) / CS;
+    const PairSegs G(P, pair, npairs, H);
+    const int nseg = G.count();
+    const int J = nseg * nch;  // jobs: (segment, channel); a job pair never mixes two chunk ranges
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < kPStages; ++i) {
@@ -851,21 +997,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued = 0, last_parity = 0;
             bool ok = true;
-            int it_t = 0, it_c = 0, tm = 0, tn = 0;  // job iterator: tile ordinal, channel
-            if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                int jc[2], jrA[2], jrB[2];
+                int jc[2], jrA[2], jrB[2], hb = 0, he = H;
                 for (int s = 0; s < nj; ++s) {
-                    jc[s] = it_c;
+                    const int j = (2 * pi + s) / nch;
+                    int t, kind, tm, tn;
+                    G.get(j, t, hb, he, kind);
+                    tile_coords(t, P.tiles_m, P.tiles_n, P.raster, tm, tn);
+                    jc[s] = (2 * pi + s) % nch;
                     jrA[s] = tm * kPairTile + (int)rank * 128;
                     jrB[s] = tn * kPairTile + (int)rank * 128;
-                    if (++it_c == nch) {
-                        it_c = 0;
-                        if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
-                    }
                 }
-                for (int h = 0; h < H && ok; ++h) {
+                for (int h = hb; h < he && ok; ++h) {
                     const int k0 = h * CS;
                     const int steps = min(CS, I.ksteps - k0);
                     for (int s = 0; s < nj && ok; ++s) {
@@ -909,7 +1053,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool any = false;
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                for (int h = 0; h < H && ok; ++h) {
+                int t, kind, hb, he;
+                G.get((2 * pi) / nch, t, hb, he, kind);
+                for (int h = hb; h < he && ok; ++h) {
                     const int steps = min(CS, I.ksteps - h * CS);
                     for (int s = 0; s < nj && ok; ++s) {
                         if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
@@ -928,7 +1074,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t b0 = smem_addr(sB + stage * kPBBytes);
 #pragma unroll
                             for (int kk = 0; kk < kTileK / 16; ++kk) {
-                                const uint32_t acc = (h > 0 || st > 0 || kk > 0) ? 1u : 0u;
+                                const uint32_t acc = (h > hb || st > 0 || kk > 0) ? 1u : 0u;
                                 tc_mma_bf16_pair(dt, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
                                                  acc);
                             }
@@ -961,27 +1107,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t accp[2] = {0u, 0u};
         uint32_t sep[2] = {0u, 0u};
         bool ok = true;
-        int it_t = 0, it_c = 0;  // job iterator: tile ordinal, channel
-        int cur_tm = 0, cur_tn = 0;  // coordinates of tile it_t
-        if (my_tiles > 0) tile_coords(pair, P.tiles_m, P.tiles_n, P.raster, cur_tm, cur_tn);
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
-            int jc[2], jslot[2], jtm[2], jtn[2];
+            int jc[2], jslot[2], jtm[2], jtn[2], jkind[2], hb = 0, he = H;
             for (int s = 0; s < nj; ++s) {
-                jc[s] = it_c;
-                jslot[s] = it_t & 1;
-                jtm[s] = cur_tm;
-                jtn[s] = cur_tn;
-                if (++it_c == nch) {
-                    it_c = 0;
-                    if (++it_t < my_tiles) tile_coords(pair + it_t * npairs, P.tiles_m, P.tiles_n, P.raster, cur_tm, cur_tn);
-                }
+                const int j = (2 * pi + s) / nch;
+                int t;
+                G.get(j, t, hb, he, jkind[s]);
+                tile_coords(t, P.tiles_m, P.tiles_n, P.raster, jtm[s], jtn[s]);
+                jc[s] = (2 * pi + s) % nch;
+                jslot[s] = G.digit_ord(j) & 1;
             }
-            for (int h = 0; h < H && ok; ++h) {
-                const bool last_chunk = (h == H - 1);
+            for (int h = hb; h < he && ok; ++h) {
+                const bool last_chunk = (h == he - 1);
                 for (int s = 0; s < nj; ++s) {
                     const int c = jc[s];
                     const int slot = jslot[s];
+                    const int kind = jkind[s];
                     unsigned char* slot_row = slot_base + size_t(slot) * P.slot_stride + row_off;
                     if (!mbar_wait(&acc_full[s], accp[s], abort_flag, err, kDevTimeoutEpilogue)) {
                         ok = false;
@@ -995,6 +1137,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const float uf = (float)I.u[c], uim = uf * im;
                     if (!last_chunk) {
                         epi_reduce(tbase, mf, im);
+                    } else if (kind == 2) {
+                        epi_partial(tbase, mf, im, sk_part_at(P, pair, rank, c) + row_off);
                     } else {
                         if (c == 0) {
                             if (!mbar_wait(&slot_empty[slot], sep[slot] ^ 1u, abort_flag, err, kDevTimeoutEpilogue)) {
@@ -1003,9 +1147,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             sep[slot] ^= 1u;
                         }
+                        // a head: this channel's residues of every tail first
+                        for (int tp = pair + G.rem; kind == 1 && tp < G.rem * G.split && ok; tp += G.rem)
+                            ok = sk_wait(P.sk_flags + ((size_t(tp) * 2 + rank) * nch + c) * kEpiWarps + (warp - 2),
+                                         abort_flag, err);
+                        if (!ok) break;
                         unsigned char* dst = slot_row + size_t(c) * kTileM * kTileN;
-                        epi_digits(tbase, mf, im, uf, uim, dst, (2 * jtm[s] + (int)rank) * kTileM + row_local < I.m,
-                                   I.n - jtn[s] * kTileN - half * 128);
+                        const bool row_ok = (2 * jtm[s] + (int)rank) * kTileM + row_local < I.m;
+                        const int col_lim = I.n - jtn[s] * kTileN - half * 128;
+                        if (kind == 1)
+                            epi_digits_sk(tbase, mf, im, uf, uim, dst, row_ok, col_lim, P, pair + G.rem,
+                                          G.rem * G.split, G.rem, rank, c, row_off);
+                        else
+                            epi_digits(tbase, mf, im, uf, uim, dst, row_ok, col_lim);
                     }
                     tc_fence_before();
                     if (last_chunk && c == nch - 1) __threadfence_block();
@@ -1015,16 +1169,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive(&acc_empty[s]);
                         else
                             mbar_arrive_cluster(acc_empty_leader[s]);
-                        if (last_chunk && c == nch - 1) mbar_arrive(&slot_full[slot]);
+                        if (last_chunk && c == nch - 1 && kind != 2) mbar_arrive(&slot_full[slot]);
+                    }
+                    if (last_chunk && kind == 2) {
+                        // this warp's residues of channel c are out: release them to the head
+                        __threadfence();
+                        __syncwarp();
+                        if (lane == 0)
+                            st_release_gpu(P.sk_flags + ((size_t(pair) * 2 + rank) * nch + c) * kEpiWarps + (warp - 2),
+                                           1);
                     }
                 }
             }
         }
-        if (ok && my_tiles > 0) {
-            // the CTA's last tile: take 8 of the 12 row shares of its reconstruction
-            const int ti = my_tiles - 1;
-            int tm, tn;
-            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
+        const int nd = G.digit_tiles();
+        if (ok && nd > 0) {
+            // the CTA's last digit tile: take 8 of the 12 row shares of its reconstruction
+            const int ti = nd - 1;
+            int jl = nseg - 1;
+            if (G.has_tail() && jl == G.ndp) --jl;  // a range that is one tail only: the last round-robin tile
+            int t, hb, he, kind, tm, tn;
+            G.get(jl, t, hb, he, kind);
+            tile_coords(t, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             uint4* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(I, kcw, lane);
             if (mbar_wait(&slot_full[ti & 1], (uint32_t)(ti >> 1) & 1u, abort_flag, err, kDevTimeoutEpilogue))
@@ -1037,19 +1203,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int cw = warp - kFirstCombineWarp;
         unsigned char* slot_base = P.slots + size_t(blockIdx.x) * 2 * P.slot_stride;
         uint32_t sfp[2] = {0u, 0u};
-        if (my_tiles > 0) stage_consts(I, kc, cw * 32 + lane);
-        for (int ti = 0; ti < my_tiles; ++ti) {
+        const int nd = G.digit_tiles();
+        if (nd > 0) stage_consts(I, kc, cw * 32 + lane);
+        for (int j = 0, ti = 0; j < nseg; ++j) {
+            int t, hb, he, kind, tm, tn;
+            G.get(j, t, hb, he, kind);
+            if (kind == 2) continue;
             const int slot = ti & 1;
             if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;
             sfp[slot] ^= 1u;
-            int tm, tn;
-            tile_coords(pair + ti * npairs, P.tiles_m, P.tiles_n, P.raster, tm, tn);
+            tile_coords(t, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             // rows of this CTA: the 128-row block 2 tm + rank
             combine_block<false>(I, kc, (2 * tm + (int)rank) * kTileM, tn * kTileN, slot_base + size_t(slot) * P.slot_stride,
-                          size_t(kTileM) * kTileN, cw, ti == my_tiles - 1 ? kCombineWarps + kEpiWarps : kCombineWarps,
+                          size_t(kTileM) * kTileN, cw, ti == nd - 1 ? kCombineWarps + kEpiWarps : kCombineWarps,
                           lane);
             __syncwarp();
             if (lane == 0) mbar_arrive(&slot_empty[slot]);
+            ++ti;
         }
     }
 

@@ -363,3 +363,52 @@ def test_reconstruction_at_the_channel_boundaries(kernel, p, which, past, monkey
     check_sampled(A, B, C, got, p, alpha, beta, seed=k)
     if k < 1000:
         assert np.array_equal(got, oracle.fgemm(A, B, p, alpha, beta, C))
+
+
+# A shape whose last wave the CTA-pair kernel cuts along the inner dimension on
+# a GB300 (74 resident pairs): 10 x 8 = 80 tiles of 256 x 256, ragged edges, so
+# 6 tiles in the last wave, each in min(74 / 6, chunks, 4) parts.
+STREAM_K_MN = (2523, 2043)
+
+
+@pytest.mark.parametrize("p", [65521, 8388593, 2147483647])
+def test_cut_last_wave_at_the_accumulator_bound(p, monkeypatch):
+    """80 tiles on 74 pairs with four chunks per tile: each last-wave tile is
+    cut into four parts, and the head adds three tails' residues to a full
+    chunk at the accumulator bound (sign-pattern inputs, residues
+    +-(m_c - 1)/2).  Every entry against the closed form, sampled entries
+    against the oracle, and the whole result against the round-robin
+    schedule (FFGPU_STREAMK=0)."""
+    monkeypatch.setenv("FFGPU_KERNEL", "pair")
+    m, n = STREAM_K_MN
+    chunk = ff.fgemm_plan(m, n, 4096, p)["k_chunk"]
+    k = 3 * chunk + 300
+    plan = ff.fgemm_plan(m, n, k, p)
+    assert plan["channels"] % 2 == 0 and plan["mode"] == 2
+    x, used = largest_x_with_half_residues(p, plan["moduli"])
+    rng = W.rng_for("worstcase", 2, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, x, x)
+    alpha, beta = int(rng.integers(1, p)), int(rng.integers(1, p))
+    got = run(A, B, C, p, alpha, beta)
+    assert np.array_equal(got, closed_form(s, t, k, x, x, p, alpha, beta, C))
+    check_sampled(A, B, C, got, p, alpha, beta, seed=p % 1000)
+    monkeypatch.setenv("FFGPU_STREAMK", "0")
+    assert np.array_equal(run(A, B, C, p, alpha, beta), got)
+
+
+@pytest.mark.parametrize("k", [2048, 3000])
+def test_cut_last_wave_uniform_words(k, monkeypatch):
+    """Uniform words (not reduced mod p) at the same shape with two and three
+    chunks per tile (two and three parts): sampled entries against the
+    oracle, Freivalds' test, and the round-robin schedule's result."""
+    monkeypatch.setenv("FFGPU_KERNEL", "pair")
+    p = 2147483647
+    m, n = STREAM_K_MN
+    rng = W.rng_for("square", 12, k)
+    A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    got = run(A, B, C, p, alpha, beta)
+    check_sampled(A, B, C, got, p, alpha, beta, seed=k, count=2048)
+    assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
+    monkeypatch.setenv("FFGPU_STREAMK", "0")
+    assert np.array_equal(run(A, B, C, p, alpha, beta), got)
