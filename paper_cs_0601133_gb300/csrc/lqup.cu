@@ -36,8 +36,11 @@
 // come first in original order) and the leaf is committed; if not, a pivot
 // lies beyond the window, nothing has been written, and the leaf is split.  A
 // single row whose window is zero takes its pivot from the first non-zero
-// column the check found.  The host reads every leaf's outcome (rank, commit
-// or split) before it issues the next step: the calls are host-synchronous.
+// column the check found.  A leaf whose rows are all pivots commits whatever
+// lies beyond the window, so both kernels then write A in place (and the rest
+// kernel reorders rowperm); otherwise they write scratch rows, copied to A on
+// commit.  The host reads every leaf's outcome (rank, commit or split) before
+// it issues the next step: the calls are host-synchronous.
 //
 // Look-ahead.  Where a node's update Z <- Z - G Y takes the tensor-core route
 // and its bottom half has more than one leaf, the columns of the bottom
@@ -131,10 +134,10 @@ __device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, uns
 // products over all pairs at once, on 64 x 64 zero-padded blocks so that every
 // dot product has the level's full length and no bounds.
 //
-// Writes the leaf's new rows on the window (rows points at column c of the
-// scratch rows), E (h x h, original row order), U11^{-1} (r x r, zeros below
-// the diagonal, leading dimension ldu; skipped when Uig is null) and the
-// LeafInfo.
+// Writes the leaf's new rows on the window (over A's window when every row
+// is a pivot, else to the scratch rows: rows points at their column c), E
+// (h x h, original row order), U11^{-1} (r x r, zeros below the diagonal,
+// leading dimension ldu; skipped when Uig is null) and the LeafInfo.
 constexpr int kWinWarps = kWinThreads / 32;
 constexpr int kRowsPerWarp = kLeafRows / kWinWarps;
 constexpr int kExt = kLeafRows;              // columns of the identity extension
@@ -246,7 +249,7 @@ __device__ __forceinline__ void win_update(const WinField<kBin>& F, uint32_t (&v
 
 // The elimination; returns the rank on the window, or -1 if a wait ran out.
 template <bool kBin, int NCW>
-__device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* __restrict__ A, long long lda, int h, int W,
+__device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* A, long long lda, int h, int W,
                              const WinState& S, int* timeout) {
     constexpr int NCA = NCW + kExt / 32;
     constexpr int WA = 32 * NCA;
@@ -259,7 +262,7 @@ __device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* __restrict
 #pragma unroll
         for (int c = 0; c < NCW; ++c) {
             const int q = lane + 32 * c;
-            v[rr][c] = (tt < h && q < W) ? F.to(__ldg(A + (long long)tt * lda + q)) : 0u;
+            v[rr][c] = (tt < h && q < W) ? F.to(A[(long long)tt * lda + q]) : 0u;
         }
 #pragma unroll
         for (int c = NCW; c < NCA; ++c) v[rr][c] = (lane + 32 * (c - NCW) == tt) ? F.one : 0u;
@@ -301,7 +304,7 @@ __device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* __restrict
 }
 
 template <bool kBin>
-__device__ __forceinline__ void window_body(const uint32_t* __restrict__ A, long long lda, int h, int W, int WS,
+__device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, int W, int WS,
                                             uint32_t p, unsigned long long mu, uint32_t two64p,
                                             uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig, long long ldu,
                                             uint32_t* __restrict__ rows, long long ldr,
@@ -505,7 +508,11 @@ __device__ __forceinline__ void window_body(const uint32_t* __restrict__ A, long
             Uig[(long long)i * ldu + q] = Ui[i * kLeafRows + q];
         }
     // the leaf's new rows on the window: multipliers left of the diagonal of
-    // the first r columns, the pivot rows' values on and right of it
+    // the first r columns, the pivot rows' values on and right of it; in place
+    // when every row is a pivot (the leaf then commits: no residual is left to
+    // check), else to the scratch rows
+    uint32_t* const dst = r == h ? A : rows;
+    const long long ldd = r == h ? lda : ldr;
     for (int idx = tid; idx < h * W; idx += blockDim.x) {
         const int i = idx / W, q = idx - i * W;
         const int t = s_newrow[i];
@@ -514,11 +521,11 @@ __device__ __forceinline__ void window_body(const uint32_t* __restrict__ A, long
             v = F.from(Lsm[t * h + q]);
         else
             v = i < r ? F.from(U[t * WA + s_newcol[q]]) : 0u;
-        rows[(long long)i * ldr + q] = v;
+        dst[(long long)i * ldd + q] = v;
     }
 }
 
-__global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint32_t* __restrict__ A, long long lda,
+__global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(uint32_t* A, long long lda,
                                                                   int h, int W, int WS, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
@@ -532,73 +539,99 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(const uint3
 
 // The rest of the leaf's rows.  Blocks [0, nleft): columns [0, c), the rows
 // only reordered.  Blocks from nleft on: kRestCols columns each from c + W
-// on: new row i = E[newrow[i]] times the original columns (independent
-// 128-bit dot products, no barrier between pivots); the non-pivot rows'
-// residuals must be zero, else the leaf fails and the smallest such column is
-// recorded.  A points at (rb, 0), rows at the scratch rows' column 0.
-__global__ void __launch_bounds__(kThreads) lqup_rest_kernel(const uint32_t* __restrict__ A, long long lda, int h,
-                                                             int c, int W, int n, int nleft, uint32_t p,
-                                                             unsigned long long mu, uint32_t two64p,
-                                                             const uint32_t* __restrict__ Eg,
-                                                             uint32_t* __restrict__ rows, long long ldr,
-                                                             LeafInfo* __restrict__ info) {
+// on: new row i = E[newrow[i]] times the original columns, a 64 x 64 x h
+// product per block (each thread 4 rows x 4 columns, exact 96-bit sums); the
+// non-pivot rows' residuals must be zero, else the leaf fails and the
+// smallest such column is recorded.  A points at (rb, 0).  Out of place
+// (inplace = 0) the new rows go to the scratch rows (column 0 at rows, leading
+// dimension ldr); in place (every row of the leaf a pivot, so the leaf
+// commits) they overwrite A's rows (every block reads all its columns before
+// it writes them) and block 0 also applies the row order to rowperm.
+__device__ __forceinline__ void mac96(uint32_t& lo, uint32_t& mid, uint32_t& hi, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(lo), "+r"(mid), "+r"(hi)
+        : "r"(a), "r"(b));
+}
+
+__global__ void __launch_bounds__(kThreads) lqup_rest_kernel(uint32_t* A, long long lda, int h, int c, int W, int n,
+                                                             int nleft, uint32_t p, unsigned long long mu,
+                                                             uint32_t two64p, const uint32_t* __restrict__ Eg,
+                                                             uint32_t* rows, long long ldr, int inplace,
+                                                             int32_t* rowperm, LeafInfo* __restrict__ info) {
     extern __shared__ uint32_t sm[];
     __shared__ int s_newrow[kLeafRows];
+    __shared__ int32_t s_perm[kLeafRows];
     const int tid = threadIdx.x;
     const int r = info->rank;
     for (int x = tid; x < h; x += blockDim.x) s_newrow[x] = info->newrow[x];
     __syncthreads();
+    uint32_t* out = inplace ? A : rows;
+    const long long ldo = inplace ? lda : ldr;
+    if (inplace && blockIdx.x == 0) {
+        for (int x = tid; x < h; x += blockDim.x) s_perm[x] = rowperm[s_newrow[x]];
+        __syncthreads();
+        for (int x = tid; x < h; x += blockDim.x) rowperm[x] = s_perm[x];
+    }
     if ((int)blockIdx.x < nleft) {
+        // one column per thread, every row of it read before any is written
         const int col = blockIdx.x * blockDim.x + tid;
-        if (col < c)
-            for (int i0 = 0; i0 < h; i0 += 16) {  // sixteen loads in flight before their stores
-                uint32_t v[16];
+        if (col < c) {
+            uint32_t v[kLeafRows];
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    v[e] = i0 + e < h ? __ldg(A + (long long)s_newrow[i0 + e] * lda + col) : 0u;
+            for (int e = 0; e < kLeafRows; ++e) v[e] = e < h ? A[(long long)s_newrow[e] * lda + col] : 0u;
 #pragma unroll
-                for (int e = 0; e < 16; ++e)
-                    if (i0 + e < h) rows[(long long)(i0 + e) * ldr + col] = v[e];
-            }
+            for (int e = 0; e < kLeafRows; ++e)
+                if (e < h) out[(long long)e * ldo + col] = v[e];
+        }
         return;
     }
     const int q0 = c + W + (blockIdx.x - nleft) * kRestCols;
     const int nq = min(kRestCols, n - q0);
-    uint32_t* R = sm;                   // [h][kRestCols]
-    uint32_t* Es = R + h * kRestCols;   // [h][h]
-    {
-        // every load of the thread in flight before the stores (h <= 64: at
-        // most 16 of R and 16 of E per thread)
-        constexpr int kPer = kLeafRows * kRestCols / kThreads;
-        uint32_t vr[kPer], ve[kPer];
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            const int idx = e * kThreads + tid;
-            const int i = idx / kRestCols, q = idx % kRestCols;
-            vr[e] = (i < h && q < nq) ? __ldg(A + (long long)i * lda + q0 + q) : 0u;
-            ve[e] = idx < h * h ? __ldg(Eg + idx) : 0u;
-        }
-#pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            const int idx = e * kThreads + tid;
-            if (idx < h * kRestCols) R[idx] = vr[e];
-            if (idx < h * h) Es[idx] = ve[e];
-        }
+    uint32_t* R = sm;                           // [kLeafRows][kRestCols]: the original columns
+    uint32_t* Et = R + kLeafRows * kRestCols;   // [kLeafRows][kLeafRows]: Et[s][i] = E[newrow[i]][s]
+    for (int idx = tid; idx < kLeafRows * kRestCols; idx += blockDim.x) {
+        const int i = idx / kRestCols, q = idx % kRestCols;
+        R[idx] = (i < h && q < nq) ? A[(long long)i * lda + q0 + q] : 0u;
+    }
+    for (int idx = tid; idx < kLeafRows * kLeafRows; idx += blockDim.x) {
+        const int sr = idx / kLeafRows, i = idx % kLeafRows;
+        Et[idx] = (sr < h && i < h) ? __ldg(Eg + s_newrow[i] * h + sr) : 0u;
     }
     __syncthreads();
-    const int q = tid % kRestCols;
-    for (int i = tid / kRestCols; i < h; i += kThreads / kRestCols) {
-        const int t = s_newrow[i];
-        Acc128 acc;
-        const uint32_t* Et = Es + t * h;
-        for (int s = 0; s <= t; ++s) acc.add((unsigned long long)Et[s] * R[s * kRestCols + q]);
-        const uint32_t v = acc.mod(p, mu, two64p);
-        if (q < nq) {
-            if (i >= r && v != 0u) {
-                info->fail = 1;
-                atomicMin(&info->firstnz, q0 + q);
+    const int tx = tid % 16, ty = tid / 16;  // columns 4 tx .. 4 tx + 3, rows 4 ty .. 4 ty + 3
+    uint32_t lo[4][4], mid[4][4], hi[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lo[i][j] = mid[i][j] = hi[i][j] = 0u;
+#pragma unroll 4
+    for (int sr = 0; sr < h; ++sr) {
+        const uint4 ea = *reinterpret_cast<const uint4*>(Et + sr * kLeafRows + 4 * ty);
+        const uint4 rb = *reinterpret_cast<const uint4*>(R + sr * kRestCols + 4 * tx);
+        const uint32_t ev[4] = {ea.x, ea.y, ea.z, ea.w}, rv[4] = {rb.x, rb.y, rb.z, rb.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) mac96(lo[i][j], mid[i][j], hi[i][j], ev[i], rv[j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = 4 * ty + i;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * tx + j;
+            const uint32_t th = mod_u64((unsigned long long)mod_u64(hi[i][j], p, mu) * two64p, p, mu);
+            const uint32_t tl = mod_u64(((unsigned long long)mid[i][j] << 32) | lo[i][j], p, mu);
+            const uint32_t v = th + tl >= p ? th + tl - p : th + tl;
+            if (row < h && q < nq) {
+                if (row >= r && v != 0u) {
+                    info->fail = 1;
+                    atomicMin(&info->firstnz, q0 + q);
+                }
+                out[(long long)row * ldo + q0 + q] = row < r ? v : 0u;
             }
-            rows[(long long)i * ldr + q0 + q] = i < r ? v : 0u;
         }
     }
 }
@@ -881,7 +914,7 @@ ffgpu_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FFGPU_OK : FFGPU
 size_t smem_window(int h, int WS) {
     return (size_t(h) * (WS + kExt) + size_t(h) * h + 2 * size_t(kLeafRows) * kLeafRows + size_t(kTmWords)) * 4;
 }
-size_t smem_rest(int h) { return size_t(h) * kRestCols * 4 + size_t(h) * h * 4; }
+size_t smem_rest(int) { return size_t(kLeafRows) * kRestCols * 4 + size_t(kLeafRows) * kLeafRows * 4; }
 
 ffgpu_status set_attrs() {
     static std::once_flag once;
@@ -923,10 +956,14 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     if ((st = join(x)) != FFGPU_OK) return st;
     const int nleft = (int)((c + kThreads - 1) / kThreads);
     const int nright = w > W ? (int)((w - W + kRestCols - 1) / kRestCols) : 0;
+    // every row a pivot: the window kernel wrote its columns in place, the rest
+    // follows in place (and applies the row order to rowperm)
+    const bool inplace = r == h;
     if (nleft + nright > 0) {
         st = cuda_ok(timed_launch("lqup_rest", x.s, [&] {
             lqup_rest_kernel<<<nleft + nright, kThreads, smem_rest((int)h), x.s>>>(
-                Ab, x.lda, (int)h, (int)c, W, (int)x.n, nleft, x.p, x.mu, x.two64p, x.E, x.rows, x.n, x.info);
+                Ab, x.lda, (int)h, (int)c, W, (int)x.n, nleft, x.p, x.mu, x.two64p, x.E, x.rows, x.n, inplace ? 1 : 0,
+                x.rowperm + rb, x.info);
             return cudaGetLastError();
         }));
         if (st != FFGPU_OK) return st;
@@ -958,14 +995,17 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
         *ok = true;
         return st;
     }
-    if ((st = cuda_ok(cudaMemcpy2DAsync(Ab, x.lda * 4, x.rows, x.n * 4, x.n * 4, h, cudaMemcpyDeviceToDevice,
+    if (!inplace &&
+        (st = cuda_ok(cudaMemcpy2DAsync(Ab, x.lda * 4, x.rows, x.n * 4, x.n * 4, h, cudaMemcpyDeviceToDevice,
                                         x.s))) != FFGPU_OK)
         return st;
-    st = cuda_ok(timed_launch("lqup_rowperm", x.s, [&] {
-        lqup_rowperm_kernel<<<1, kThreads, 0, x.s>>>(x.rowperm + rb, (int)h, x.info);
-        return cudaGetLastError();
-    }));
-    if (st != FFGPU_OK) return st;
+    if (!inplace || nleft + nright == 0) {
+        st = cuda_ok(timed_launch("lqup_rowperm", x.s, [&] {
+            lqup_rowperm_kernel<<<1, kThreads, 0, x.s>>>(x.rowperm + rb, (int)h, x.info);
+            return cudaGetLastError();
+        }));
+        if (st != FFGPU_OK) return st;
+    }
     if (!ident && x.m > h) {
         st = cuda_ok(timed_launch("lqup_colperm", x.s, [&] {
             lqup_colperm_kernel<<<grid_rows(x.m), kThreads, 0, x.s>>>(x.A, x.lda, (int)x.m, (int)rb, (int)(rb + h),
