@@ -8,9 +8,9 @@
 // carry chains), which stays exact for any inputs and any k < 2^32, reduced
 // mod p once, then alpha and beta applied (the delayed reduction of section
 // 3.1 taken to its limit: one reduction per output).  64 x 64 output tiles,
-// 256 threads with 4 x 4 outputs each, k staged through shared memory 32 at a
-// time (32 x 32 tiles with 64 threads for the batched launch's products with a
-// dimension of at most 32).  When the tiles leave SMs idle, k is split (the
+// 256 threads with 4 x 4 outputs each, k staged 32 at a time through two
+// shared-memory buffers (32 x 32 tiles with 64 threads for the batched
+// launch's products with a dimension of at most 32).  When the tiles leave SMs idle, k is split (the
 // rule and its measurements are at small_splits): each split writes its exact
 // 96-bit partial sums to the workspace and a second kernel adds them, reduces
 // mod p and applies alpha and beta (C is then written only after every read
@@ -50,7 +50,19 @@ __device__ __forceinline__ uint32_t finish96(uint32_t lo, uint32_t mid, uint32_t
 // One T x T output tile (rows row0.., columns col0..) over the k-range
 // [kbeg, kend), T * T / 16 threads with 4 x 4 outputs each: with part null
 // it finishes the outputs itself, else it stores its partial sums at part
-// (uint4 per output: lo, mid, hi, 0; m x n).
+// (uint4 per output: lo, mid, hi, 0; m x n).  The k chunks are staged in two
+// shared-memory buffers by asynchronous copies (words outside the matrices
+// arrive as zeros), the next chunk's copies in flight while the current one
+// is multiplied.
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int T>
 __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int row0, int col0,
                                            const uint32_t* __restrict__ A, long long lda,
@@ -59,37 +71,47 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
                                            uint32_t two64p, uint32_t alpha, uint32_t beta) {
     constexpr int NT = T * T / 16;       // threads
     constexpr int PER = T * kSmK / NT;   // staged words per thread and operand (8 for T = 64, 16 for T = 32)
-    __shared__ __align__(16) uint32_t As[kSmK][T];  // As[kk][row]
-    __shared__ __align__(16) uint32_t Bs[kSmK][T];  // Bs[kk][col]
+    __shared__ __align__(16) uint32_t As[2][kSmK][T];  // As[buf][kk][row]
+    __shared__ __align__(16) uint32_t Bs[2][kSmK][T];  // Bs[buf][kk][col]
     const int tid = threadIdx.x, tx = tid % (T / 4), ty = tid / (T / 4);
     uint32_t lo[4][4], mid[4][4], hi[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) lo[i][j] = mid[i][j] = hi[i][j] = 0u;
-    for (int k0 = kbeg; k0 < kend; k0 += kSmK) {
-        {
-            // A: row r, k-run of PER words; B: k row kk, column run of PER words
-            const int r = tid / (kSmK / PER), kk0 = (tid % (kSmK / PER)) * PER, gi = row0 + r;
+    // A: row r, k-run of PER words; B: k row kk, column run of PER words
+    const int ar = tid / (kSmK / PER), akk0 = (tid % (kSmK / PER)) * PER, agi = row0 + ar;
+    const int bkk = tid / (T / PER), bc0 = (tid % (T / PER)) * PER;
+    auto stage = [&](int buf, int k0) {
 #pragma unroll
-            for (int e = 0; e < PER; ++e) {
-                const int gk = k0 + kk0 + e;
-                As[kk0 + e][r] = (gi < m && gk < kend) ? __ldg(A + (long long)gi * lda + gk) : 0u;
-            }
+        for (int e = 0; e < PER; ++e) {
+            const int gk = k0 + akk0 + e;
+            const bool ok = agi < m && gk < kend;
+            cp_async4(&As[buf][akk0 + e][ar], ok ? A + (long long)agi * lda + gk : A, ok);
         }
-        {
-            const int kk = tid / (T / PER), c0 = (tid % (T / PER)) * PER, gk = k0 + kk;
+        const int gk = k0 + bkk;
 #pragma unroll
-            for (int e = 0; e < PER; ++e) {
-                const int gj = col0 + c0 + e;
-                Bs[kk][c0 + e] = (gk < kend && gj < n) ? __ldg(B + (long long)gk * ldb + gj) : 0u;
-            }
+        for (int e = 0; e < PER; ++e) {
+            const int gj = col0 + bc0 + e;
+            const bool ok = gk < kend && gj < n;
+            cp_async4(&Bs[buf][bkk][bc0 + e], ok ? B + (long long)gk * ldb + gj : B, ok);
+        }
+        cp_async_commit();
+    };
+    if (kbeg < kend) stage(0, kbeg);
+    int buf = 0;
+    for (int k0 = kbeg; k0 < kend; k0 += kSmK, buf ^= 1) {
+        if (k0 + kSmK < kend) {
+            stage(buf ^ 1, k0 + kSmK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < kSmK; ++kk) {
-            const uint4 a = *reinterpret_cast<const uint4*>(&As[kk][ty * 4]);
-            const uint4 b = *reinterpret_cast<const uint4*>(&Bs[kk][tx * 4]);
+            const uint4 a = *reinterpret_cast<const uint4*>(&As[buf][kk][ty * 4]);
+            const uint4 b = *reinterpret_cast<const uint4*>(&Bs[buf][kk][tx * 4]);
             const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
