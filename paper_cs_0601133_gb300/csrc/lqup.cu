@@ -96,10 +96,6 @@ struct Acc128 {
     }
 };
 
-__device__ __forceinline__ uint32_t mulm(uint32_t a, uint32_t b, uint32_t p, unsigned long long mu) {
-    return mod_u64((unsigned long long)a * b, p, mu);
-}
-
 // Window factorization of one leaf (one CTA of kWinThreads).  A points at
 // (rb, c); the leaf's tile is h x W (zero padding up to WS, a multiple of 32).
 //
