@@ -342,8 +342,9 @@ bool use_pair_kernel(int64_t m, int grid) {
 
 // Schedule of a CTA-pair launch: np pairs, tiles dealt round-robin, and a
 // cut last wave (split > 1): when the last wave has rem tiles, at most half
-// the pairs, each of them is cut into split = min(pairs / rem, H, 4) parts of
-// its H chunks, so that that wave takes ceil(H / split) chunks instead of H.
+// the pairs, each of them is cut into split = min(pairs / rem, ksteps /
+// kMinPartSteps, 4) parts of its ksteps k-steps, so that that wave takes
+// about ksteps / split k-steps instead of ksteps.
 // A problem with fewer tiles than pairs is one such wave, on rem x split
 // pairs.  An even channel count is required (the kernel's job pairs never
 // mix two segments).  FFGPU_STREAMK=0 keeps the round-robin schedule.
@@ -356,17 +357,23 @@ static int64_t pair_tiles(int64_t m, int64_t n) {
     return ((m + 2 * kTileM - 1) / (2 * kTileM)) * ((n + kTileN - 1) / kTileN);
 }
 
-// T tiles, at most np_max pairs, H chunks per tile, nch channels; cut = false
-// gives the round-robin schedule.
-static PairSched pair_sched(int64_t T, int np_max, int64_t H, int nch, bool cut) {
+// k-steps of a part of a cut tile: one chunk (1024 products).  Shorter parts
+// lose more than they gain: their heads' epilogues wait on the tails'
+// residues in L2 for every channel with little tensor work to overlap it
+// (1024^3 with four parts of 4 k-steps: 161 us against 87.5 round-robin).
+constexpr int64_t kMinPartSteps = 16;
+
+// T tiles, at most np_max pairs, ksteps k-steps per tile, nch channels; cut =
+// false gives the round-robin schedule.
+static PairSched pair_sched(int64_t T, int np_max, int64_t ksteps, int nch, bool cut) {
     PairSched s;
     np_max = std::max(1, np_max);
     s.np = (int)std::max<int64_t>(1, std::min<int64_t>(T, np_max));
     const char* e = std::getenv("FFGPU_STREAMK");
-    if (!cut || (e && std::strcmp(e, "0") == 0) || np_max < 2 || H < 2 || (nch & 1)) return s;
+    if (!cut || (e && std::strcmp(e, "0") == 0) || np_max < 2 || ksteps < 2 * kMinPartSteps || (nch & 1)) return s;
     const int64_t rem = T < np_max ? T : T % np_max;
     if (rem == 0) return s;
-    const int64_t split = std::min<int64_t>(std::min<int64_t>(np_max / rem, H), 4);
+    const int64_t split = std::min<int64_t>(std::min<int64_t>(np_max / rem, ksteps / kMinPartSteps), 4);
     if (split < 2) return s;
     if (T < np_max) s.np = (int)(T * split);
     s.dp = (int)(T - rem);
@@ -410,9 +417,7 @@ static size_t fgemm_ws_bytes_impl(int64_t m, int64_t n, int64_t k, uint32_t p, i
     const int64_t ks = std::min<int64_t>(k, pl.k_slice), kp = round64(ks);
     const int grid = grid_for_tiles(m, n, sms);
     const bool pair = use_pair_kernel(m, grid);
-    const int64_t cs = chunk_steps_for(pl);
-    const PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(sms), (kp / kTileK + cs - 1) / cs, pl.nch, cut)
-                              : PairSched();
+    const PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(sms), kp / kTileK, pl.nch, cut) : PairSched();
     const size_t rns = launch_layout(m, n, kp, pl.nch, grid, pair, ps).total;
     // a small product runs on the CUDA cores, its k-split partial sums in the workspace
     return fgemm_small(m, n, k) ? std::max(rns, small_ws_bytes(m, n, k, sms)) : rns;
@@ -499,13 +504,12 @@ ffgpu_status fgemm_run_rns_src(int64_t m, int64_t n, int64_t k, uint32_t p, uint
         // block or the caller forces the one-CTA kernel; its schedule sets the
         // number of residue slots, so it is chosen before the layout
         const bool pair = use_pair_kernel(m, grid);
-        const int64_t cs = chunk_steps_for(pl);
-        const int64_t H = (kp / kTileK + cs - 1) / cs;
+        const int64_t ksteps = kp / kTileK;
         const int cap = max_grid > 0 ? std::min(sm_count(dev), max_grid) : sm_count(dev);
-        PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(cap), H, pl.nch, true) : PairSched();
+        PairSched ps = pair ? pair_sched(pair_tiles(m, n), pair_limit(cap), ksteps, pl.nch, true) : PairSched();
         LaunchLayout X = launch_layout(m, n, kp, pl.nch, grid, pair, ps);
         if (X.total > ws_bytes && ps.split > 1) {  // no room for a cut last wave: round-robin
-            ps = pair_sched(pair_tiles(m, n), pair_limit(cap), H, pl.nch, false);
+            ps = pair_sched(pair_tiles(m, n), pair_limit(cap), ksteps, pl.nch, false);
             X = launch_layout(m, n, kp, pl.nch, grid, pair, ps);
         }
         if (X.total > ws_bytes) return FFGPU_ERR_NOMEM;

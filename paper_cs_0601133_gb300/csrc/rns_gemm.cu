@@ -782,8 +782,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 //
 // Schedule.  Tiles are dealt round-robin to the pairs.  When the last wave
 // has fewer tiles (rem) than half the pairs, its tiles are instead cut along
-// the inner dimension into sk_split equal parts of their chunks, part j of
-// tile r on pair r + j rem, so that the last wave keeps rem x sk_split pairs
+// the inner dimension into sk_split equal parts of their k-steps (each part
+// taken in chunks of at most chunk_steps), part j of tile r on pair r + j rem, so that the last wave keeps rem x sk_split pairs
 // busy for a fraction of the time.  The parts of a wave run together, at the
 // same offsets of the inner dimension, as the tiles of a full wave do (their
 // operand blocks are shared through L2 the same way).  Parts j > 0 ("tails")
@@ -802,8 +802,8 @@ constexpr int kPairTile = 256;
 // The segments of one pair (the same in every role of both CTAs): its
 // round-robin tiles, then, in a cut last wave, one part of a tile.
 struct PairSegs {
-    int pair, np, H, ndp, split, rem;
-    __device__ PairSegs(const RnsGemmParams& P, int pair_, int np_, int H_) : pair(pair_), np(np_), H(H_) {
+    int pair, np, KS, ndp, split, rem;
+    __device__ PairSegs(const RnsGemmParams& P, int pair_, int np_, int KS_) : pair(pair_), np(np_), KS(KS_) {
         if (P.sk_split > 1) {
             ndp = P.sk_dp / np;
             split = P.sk_split;
@@ -816,19 +816,19 @@ struct PairSegs {
     }
     __device__ bool in_split() const { return split > 1 && pair < rem * split; }
     __device__ int count() const { return ndp + (in_split() ? 1 : 0); }
-    // segment j: tile t, chunks [hb, he), kind 0 whole, 1 head, 2 tail
-    __device__ void get(int j, int& t, int& hb, int& he, int& kind) const {
+    // segment j: tile t, k-steps [sb, se), kind 0 whole, 1 head, 2 tail
+    __device__ void get(int j, int& t, int& sb, int& se, int& kind) const {
         if (j < ndp) {
             t = pair + j * np;
-            hb = 0;
-            he = H;
+            sb = 0;
+            se = KS;
             kind = 0;
             return;
         }
         const int part = pair / rem;
         t = ndp * np + pair % rem;
-        hb = part * H / split;
-        he = (part + 1) * H / split;
+        sb = part * KS / split;
+        se = (part + 1) * KS / split;
         kind = part == 0 ? 1 : 2;
     }
     __device__ bool has_tail() const { return in_split() && pair >= rem; }  // the last segment
@@ -960,8 +960,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int pair = (int)blockIdx.x >> 1, npairs = (int)gridDim.x >> 1;
     const int nch = I.nch;
     const int CS = I.chunk_steps;
-    const int H = (I.ksteps + CS - 1) / CS;
-    const PairSegs G(P, pair, npairs, H);
+    const PairSegs G(P, pair, npairs, I.ksteps);
     const int nseg = G.count();
     const int J = nseg * nch;  // jobs: (segment, channel); a job pair never mixes two chunk ranges
 
@@ -999,19 +998,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                int jc[2], jrA[2], jrB[2], hb = 0, he = H;
+                int jc[2], jrA[2], jrB[2], sb = 0, se = I.ksteps;
                 for (int s = 0; s < nj; ++s) {
                     const int j = (2 * pi + s) / nch;
                     int t, kind, tm, tn;
-                    G.get(j, t, hb, he, kind);
+                    G.get(j, t, sb, se, kind);
                     tile_coords(t, P.tiles_m, P.tiles_n, P.raster, tm, tn);
                     jc[s] = (2 * pi + s) % nch;
                     jrA[s] = tm * kPairTile + (int)rank * 128;
                     jrB[s] = tn * kPairTile + (int)rank * 128;
                 }
-                for (int h = hb; h < he && ok; ++h) {
-                    const int k0 = h * CS;
-                    const int steps = min(CS, I.ksteps - k0);
+                const int nh = (se - sb + CS - 1) / CS;
+                for (int h = 0; h < nh && ok; ++h) {
+                    const int k0 = sb + h * CS;
+                    const int steps = min(CS, se - k0);
                     for (int s = 0; s < nj && ok; ++s) {
                         const int c = jc[s];
                         const int rowA = jrA[s];
@@ -1053,10 +1053,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool any = false;
             for (int pi = 0; 2 * pi < J && ok; ++pi) {
                 const int nj = min(2, J - 2 * pi);
-                int t, kind, hb, he;
-                G.get((2 * pi) / nch, t, hb, he, kind);
-                for (int h = hb; h < he && ok; ++h) {
-                    const int steps = min(CS, I.ksteps - h * CS);
+                int t, kind, sb, se;
+                G.get((2 * pi) / nch, t, sb, se, kind);
+                const int nh = (se - sb + CS - 1) / CS;
+                for (int h = 0; h < nh && ok; ++h) {
+                    const int steps = min(CS, se - (sb + h * CS));
                     for (int s = 0; s < nj && ok; ++s) {
                         if (!mbar_wait(&acc_empty[s], accp[s] ^ 1u, abort_flag, err, kDevTimeoutMma)) {
                             ok = false;
@@ -1074,7 +1075,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t b0 = smem_addr(sB + stage * kPBBytes);
 #pragma unroll
                             for (int kk = 0; kk < kTileK / 16; ++kk) {
-                                const uint32_t acc = (h > hb || st > 0 || kk > 0) ? 1u : 0u;
+                                const uint32_t acc = (h > 0 || st > 0 || kk > 0) ? 1u : 0u;
                                 tc_mma_bf16_pair(dt, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
                                                  acc);
                             }
@@ -1109,17 +1110,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool ok = true;
         for (int pi = 0; 2 * pi < J && ok; ++pi) {
             const int nj = min(2, J - 2 * pi);
-            int jc[2], jslot[2], jtm[2], jtn[2], jkind[2], hb = 0, he = H;
+            int jc[2], jslot[2], jtm[2], jtn[2], jkind[2], sb = 0, se = I.ksteps;
             for (int s = 0; s < nj; ++s) {
                 const int j = (2 * pi + s) / nch;
                 int t;
-                G.get(j, t, hb, he, jkind[s]);
+                G.get(j, t, sb, se, jkind[s]);
                 tile_coords(t, P.tiles_m, P.tiles_n, P.raster, jtm[s], jtn[s]);
                 jc[s] = (2 * pi + s) % nch;
                 jslot[s] = G.digit_ord(j) & 1;
             }
-            for (int h = hb; h < he && ok; ++h) {
-                const bool last_chunk = (h == he - 1);
+            const int nh = (se - sb + CS - 1) / CS;
+            for (int h = 0; h < nh && ok; ++h) {
+                const bool last_chunk = (h == nh - 1);
                 for (int s = 0; s < nj; ++s) {
                     const int c = jc[s];
                     const int slot = jslot[s];
@@ -1188,8 +1190,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int ti = nd - 1;
             int jl = nseg - 1;
             if (G.has_tail() && jl == G.ndp) --jl;  // a range that is one tail only: the last round-robin tile
-            int t, hb, he, kind, tm, tn;
-            G.get(jl, t, hb, he, kind);
+            int t, sb, se, kind, tm, tn;
+            G.get(jl, t, sb, se, kind);
             tile_coords(t, P.tiles_m, P.tiles_n, P.raster, tm, tn);
             uint4* kcw = kc + (1 + (warp - 2)) * kMaxChannels;
             stage_consts_warp(I, kcw, lane);
@@ -1206,8 +1208,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nd = G.digit_tiles();
         if (nd > 0) stage_consts(I, kc, cw * 32 + lane);
         for (int j = 0, ti = 0; j < nseg; ++j) {
-            int t, hb, he, kind, tm, tn;
-            G.get(j, t, hb, he, kind);
+            int t, sb, se, kind, tm, tn;
+            G.get(j, t, sb, se, kind);
             if (kind == 2) continue;
             const int slot = ti & 1;
             if (!mbar_wait(&slot_full[slot], sfp[slot], abort_flag, err, kDevTimeoutEpilogue)) break;

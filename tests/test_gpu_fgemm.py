@@ -412,3 +412,41 @@ def test_cut_last_wave_uniform_words(k, monkeypatch):
     assert oracle.freivalds(A, B, C, got, p, alpha, beta, trials=2)
     monkeypatch.setenv("FFGPU_STREAMK", "0")
     assert np.array_equal(run(A, B, C, p, alpha, beta), got)
+
+
+@pytest.mark.parametrize("p", [65521, 2147483647])
+def test_cut_small_problem_at_the_accumulator_bound(p, monkeypatch):
+    """Fewer tiles than resident pairs (1000 x 1000: 16 pair tiles), so the
+    whole problem is one wave cut into four parts of about 17 k-steps: each
+    part's first chunk is a full one at the accumulator bound (sign-pattern
+    inputs, residues +-(m_c - 1)/2), and the head adds three tails' residues
+    to it.  Every entry against the closed form, sampled entries against the
+    oracle, the whole result against the round-robin schedule."""
+    monkeypatch.setenv("FFGPU_KERNEL", "pair")
+    m = n = 1000
+    chunk = ff.fgemm_plan(m, n, 4096, p)["k_chunk"]
+    k = 4 * chunk + 300
+    plan = ff.fgemm_plan(m, n, k, p)
+    assert plan["channels"] % 2 == 0 and plan["mode"] == 2
+    x, used = largest_x_with_half_residues(p, plan["moduli"])
+    rng = W.rng_for("worstcase", 3, p)
+    A, B, C, s, t = W.sign_pattern_problem(rng, m, n, k, p, x, x)
+    alpha, beta = int(rng.integers(1, p)), int(rng.integers(1, p))
+    got = run(A, B, C, p, alpha, beta)
+    assert np.array_equal(got, closed_form(s, t, k, x, x, p, alpha, beta, C))
+    check_sampled(A, B, C, got, p, alpha, beta, seed=p % 997)
+    monkeypatch.setenv("FFGPU_STREAMK", "0")
+    assert np.array_equal(run(A, B, C, p, alpha, beta), got)
+
+
+@pytest.mark.parametrize("m,k,n", [(1000, 2048, 1000), (700, 3000, 1100), (520, 2047, 300), (300, 4100, 1500)])
+def test_cut_small_problems_uniform_words(m, k, n, monkeypatch):
+    """Problems with fewer tiles than pairs, cut into two to four parts of at
+    least a chunk of k-steps each (parts not aligned to chunks, ragged k and
+    ragged tiles), against the oracle element by element."""
+    monkeypatch.setenv("FFGPU_KERNEL", "pair")
+    p = 2147483647
+    rng = W.rng_for("square", 13, m, k, n)
+    A, B, C = W.uniform_words(rng, (m, k)), W.uniform_words(rng, (k, n)), W.uniform_words(rng, (m, n))
+    alpha, beta = int(rng.integers(0, p)), int(rng.integers(0, p))
+    check(A, B, C, p, alpha, beta)
