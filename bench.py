@@ -59,6 +59,16 @@ def parse():
     return ap.parse_args()
 
 
+def workload_config(n, p, alpha, beta, world):
+    """The workload as both arms name it (the same object in the reference
+    arm's line): problem, inputs, the L2 note, the parallelism."""
+    inputs = 3 * n * n * 4
+    l2 = ("inputs %d MiB > 129 MB L2: no flush between steps" % (inputs >> 20) if inputs > 129e6 else
+          "inputs %d MiB fit the 129 MB L2 (a step re-reads them from L2)" % (inputs >> 20))
+    return {"workload": workload_name(n, p), "n": n, "p": p, "alpha": alpha, "beta": beta, "l2": l2,
+            "parallelism": "replicas x%d" % world}
+
+
 def workload_name(n, p):
     return "fgemm m=n=k=%d p=%d alpha,beta uniform in [0,p), uniform residues" % (n, p)
 
@@ -234,7 +244,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tstep * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": workload_name(args.n, args.p), "n": args.n, "p": args.p},
+        "config": workload_config(args.n, args.p, alpha, beta, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "GOPS", "cores": oracle.num_threads(),
                          "kind": "oracle",
                          "sample": "each step: %d of %d rows of C with the full inner dimension" % (rows, args.n)},
@@ -390,12 +400,8 @@ def run_own(args):
             "metric": METRIC, "value": value, "unit": "GOPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": workload_name(n, p), "n": n, "p": p, "alpha": alpha, "beta": beta,
-                       "channels": plan["channels"], "moduli": plan["moduli"],
-                       "l2": ("inputs %d MiB > 129 MB L2: no flush between steps" % (3 * n * n * 4 >> 20))
-                             if 3 * n * n * 4 > 129e6 else
-                             "inputs %d MiB fit the 129 MB L2 (a step re-reads them from L2)" % (3 * n * n * 4 >> 20),
-                       "parallelism": "replicas x%d" % world, "plan": plan_used},
+            "config": workload_config(n, p, alpha, beta, world),
+            "plan": {"channels": plan["channels"], "moduli": plan["moduli"], "tuned": plan_used},
             "roofline": roofline,
             "cpu_baseline": base,
             "e2e": e2e,
