@@ -49,6 +49,7 @@
 // first leaf's window kernel runs while the rest of the update does; every
 // later launch makes the caller's stream wait for the side stream first.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstring>
 #include <map>
@@ -299,12 +300,25 @@ __device__ int win_eliminate(const WinField<kBin>& F, const uint32_t* A, long lo
     return k;
 }
 
+// The leaf's outcome (rank, whether the window's columns keep their order, a
+// wait that ran out) straight into the host's mapped mailbox, then the
+// sequence number that tells the host the words are there (the host polls it
+// instead of copying the record back and synchronising the stream).
+__device__ __forceinline__ void post_outcome(int* mbox, int seq, int rank, int ident, int timeout) {
+    volatile int* m = mbox;
+    m[0] = rank;
+    m[1] = ident;
+    m[2] = timeout;
+    __threadfence_system();
+    m[3] = seq;
+}
+
 template <bool kBin>
 __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, int W, int WS,
                                             uint32_t p, unsigned long long mu, uint32_t two64p,
                                             uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig, long long ldu,
                                             uint32_t* __restrict__ rows, long long ldr,
-                                            LeafInfo* __restrict__ info) {
+                                            LeafInfo* __restrict__ info, int* mbox, int seq) {
     extern __shared__ uint32_t sm[];
     const int WA = WS + kExt;
     uint32_t* U = sm;                          // [h][WA]
@@ -350,6 +364,7 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
             info->fail = 0;
             info->ident = 1;
             info->firstnz = INT_MAX;
+            post_outcome(mbox, seq, 0, 1, 1);
         }
         return;
     }
@@ -488,6 +503,7 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
         info->fail = 0;
         info->ident = ident;
         info->firstnz = INT_MAX;
+        post_outcome(mbox, seq, r, ident, 0);
     }
     for (int x = tid; x < h; x += blockDim.x) {
         info->newrow[x] = s_newrow[x];
@@ -526,11 +542,12 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(uint32_t* A
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
                                                                   long long ldu, uint32_t* __restrict__ rows,
-                                                                  long long ldr, LeafInfo* __restrict__ info) {
+                                                                  long long ldr, LeafInfo* __restrict__ info,
+                                                                  int* mbox, int seq) {
     if (p == 2u)
-        window_body<true>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info);
+        window_body<true>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info, mbox, seq);
     else
-        window_body<false>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info);
+        window_body<false>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info, mbox, seq);
 }
 
 // The rest of the leaf's rows.  Blocks [0, nleft): columns [0, c), the rows
@@ -785,6 +802,48 @@ int* pinned_words() {
     return buf;
 }
 
+// The window kernel's mailbox in mapped pinned memory (one per host thread):
+// words rank, ident, timeout, then the sequence number of the leaf that wrote
+// them; dev is the same memory as the kernel addresses it.
+struct Mailbox {
+    int* host = nullptr;
+    int* dev = nullptr;
+    int seq = 0;
+};
+
+Mailbox* mailbox() {
+    thread_local Mailbox mb;
+    if (!mb.host) {
+        int* h = nullptr;
+        if (cudaHostAlloc(&h, 64, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) return nullptr;
+        int* d = nullptr;
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaFreeHost(h);
+            return nullptr;
+        }
+        std::memset(h, 0, 64);
+        mb.host = h;
+        mb.dev = d;
+    }
+    return &mb;
+}
+
+// Polls the mailbox for leaf seq.  Nothing else is queued on s behind the
+// window kernel, so once the stream is idle the words must be there; the poll
+// is also bounded in time.
+ffgpu_status wait_outcome(const Mailbox& mb, int seq, cudaStream_t s) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (unsigned it = 1;; ++it) {
+        if (__atomic_load_n(&mb.host[3], __ATOMIC_ACQUIRE) == seq) return FFGPU_OK;
+        if ((it & 255u) == 0) {
+            const cudaError_t e = cudaStreamQuery(s);
+            if (e == cudaSuccess) return __atomic_load_n(&mb.host[3], __ATOMIC_ACQUIRE) == seq ? FFGPU_OK : FFGPU_ERR_CUDA;
+            if (e != cudaErrorNotReady) return FFGPU_ERR_CUDA;
+            if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(60)) return FFGPU_ERR_TIMEOUT;
+        }
+    }
+}
+
 // Split of h rows: on a leaf boundary above the leaf size, in halves below it.
 int64_t split_rows(int64_t h) {
     if (h <= kLeafRows) return h / 2;
@@ -858,6 +917,7 @@ struct Ctx {
     cudaStream_t s;
     int win;
     int* host;
+    Mailbox* mbox;
     int sms;
     // look-ahead (null s2: off): the update of a bottom half's rows below its
     // first leaf runs on s2, with its own workspace, while that leaf is
@@ -934,9 +994,11 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     // the kernel's register layouts: 64, 96 or 256 window columns (p = 2: 256)
     const int WS = x.p == 2 ? kMaxWin : W <= 64 ? 64 : W <= 96 ? 96 : kMaxWin;
     uint32_t* Ab = x.A + rb * x.lda;
+    const int seq = ++x.mbox->seq;
     ffgpu_status st = cuda_ok(timed_launch("lqup_window", x.s, [&] {
         lqup_window_kernel<<<1, kWinThreads, smem_window((int)h, WS), x.s>>>(
-            Ab + c, x.lda, (int)h, W, WS, x.p, x.mu, x.two64p, x.E, Uo, ldu, x.rows + c, x.n, x.info);
+            Ab + c, x.lda, (int)h, W, WS, x.p, x.mu, x.two64p, x.E, Uo, ldu, x.rows + c, x.n, x.info, x.mbox->dev,
+            seq);
         return cudaGetLastError();
     }));
     if (st != FFGPU_OK) return st;
@@ -944,11 +1006,10 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     // non-zero, so the rest of the leaf needs no second round trip.  (A
     // pending side-stream update runs meanwhile: the window kernel reads and
     // writes only this leaf's rows and the leaf's scratch.)
-    if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 5 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) != FFGPU_OK)
-        return st;
-    if ((st = cuda_ok(cudaStreamSynchronize(x.s))) != FFGPU_OK) return st;
-    if (x.host[4]) return FFGPU_ERR_TIMEOUT;
-    const int r = x.host[0];
+    if ((st = wait_outcome(*x.mbox, seq, x.s)) != FFGPU_OK) return st;
+    if (x.mbox->host[2]) return FFGPU_ERR_TIMEOUT;
+    const int r = x.mbox->host[0];
+    const int ident0 = x.mbox->host[1];
     if ((st = join(x)) != FFGPU_OK) return st;
     const int nleft = (int)((c + kThreads - 1) / kThreads);
     const int nright = w > W ? (int)((w - W + kRestCols - 1) / kRestCols) : 0;
@@ -964,7 +1025,7 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
         }));
         if (st != FFGPU_OK) return st;
     }
-    int fail = 0, ident = x.host[2], firstnz = INT_MAX;
+    int fail = 0, ident = ident0, firstnz = INT_MAX;
     if (r < h && nright > 0) {
         // non-pivot rows: their residuals beyond the window decide
         if ((st = cuda_ok(cudaMemcpyAsync(x.host, x.info, 4 * sizeof(int), cudaMemcpyDeviceToHost, x.s))) !=
@@ -1202,6 +1263,8 @@ ffgpu_status lqup_run(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda
     x.win = window_for(p);
     x.host = pinned_words();
     if (!x.host) return FFGPU_ERR_NOMEM;
+    x.mbox = mailbox();
+    if (!x.mbox) return FFGPU_ERR_NOMEM;
     x.sms = sms;
     x.pending = false;
     x.s2 = nullptr;
