@@ -126,15 +126,14 @@ struct Acc128 {
 // over a warp, one extended-Euclid inverse) gives the true multipliers
 // l_t'k = a d_t / (P d_t') (prefix products of the inverse pivots per row),
 // the true U rows and E (each stored row times 1 / d_t).  The inverse of the
-// pivot block U11 (r x r, upper triangular) is formed by doubling:
-// [[A, C], [0, D]]^{-1} has off-diagonal block -A^{-1} C D^{-1}, each level two
-// products over all pairs at once, on 64 x 64 zero-padded blocks so that every
-// dot product has the level's full length and no bounds.
+// pivot block U11 (r x r, upper triangular) is left to the rest kernel's last
+// CTA (u11_inverse), which runs beside the rest of the rows.
 //
 // Writes the leaf's new rows on the window (over A's window when every row
 // is a pivot, else to the scratch rows: rows points at their column c), E
-// (h x h, original row order), U11^{-1} (r x r, zeros below the diagonal,
-// leading dimension ldu; skipped when Uig is null) and the LeafInfo.
+// (h x h, original row order), the LeafInfo and, when the caller asks for
+// the inverse of the pivot block (Uig not null), U11 and the inverse of its
+// diagonal to Usc.
 constexpr int kWinWarps = kWinThreads / 32;
 constexpr int kRowsPerWarp = kLeafRows / kWinWarps;
 constexpr int kExt = kLeafRows;              // columns of the identity extension
@@ -316,16 +315,13 @@ __device__ __forceinline__ void post_outcome(int* mbox, int seq, int rank, int i
 template <bool kBin>
 __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, int W, int WS,
                                             uint32_t p, unsigned long long mu, uint32_t two64p,
-                                            uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig, long long ldu,
+                                            uint32_t* __restrict__ Eg, const uint32_t* Uig, uint32_t* __restrict__ Usc,
                                             uint32_t* __restrict__ rows, long long ldr,
                                             LeafInfo* __restrict__ info, int* mbox, int seq) {
     extern __shared__ uint32_t sm[];
     const int WA = WS + kExt;
     uint32_t* U = sm;                          // [h][WA]
     uint32_t* Lsm = U + h * WA;                // [h][h]
-    uint32_t* Us = Lsm + h * h;                // [64][64]: U11 (true values, plain form)
-    uint32_t* Ui = Us + kLeafRows * kLeafRows; // [64][64]: U11^{-1}
-    uint32_t* Tm = Ui + kLeafRows * kLeafRows; // [kTmWords]: doubling products
     __shared__ uint64_t s_bar[kLeafRows];
     __shared__ uint32_t s_Pv[kLeafRows], s_dv[kLeafRows], s_P[kLeafRows], s_invP[kLeafRows];
     __shared__ int s_jp[kLeafRows], s_pre[kLeafRows], s_prow[kLeafRows], s_pcol[kLeafRows];
@@ -337,7 +333,6 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
     const WinField<kBin> F(p, two64p, mu);
 
     for (int idx = tid; idx < h * h; idx += blockDim.x) Lsm[idx] = 0u;
-    for (int idx = tid; idx < kLeafRows * kLeafRows; idx += blockDim.x) Us[idx] = Ui[idx] = 0u;
     for (int x = tid; x < h; x += blockDim.x) {
         s_rowpiv[x] = -1;
         mbar_init(&s_bar[x], 32);
@@ -424,49 +419,16 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
         for (int q = lane; q < WA; q += 32) U[t * WA + q] = F.mul(U[t * WA + q], invd);
     }
     __syncthreads();
-    // U11 and the diagonal of its inverse (plain form, zero outside r x r)
-    for (int idx = tid; idx < r * r; idx += blockDim.x) {
-        const int i = idx / r, q = idx - i * r;
-        if (q > i) Us[i * kLeafRows + q] = F.from(U[s_prow[i] * WA + s_pcol[q]]);
-        else if (q == i) {
-            Us[i * kLeafRows + i] = F.from(U[s_prow[i] * WA + s_pcol[i]]);
-            Ui[i * kLeafRows + i] = F.from(F.mul(s_dv[s_prow[i]], s_invP[i]));
+    // U11 (plain form, on and above the diagonal) and the diagonal of its
+    // inverse, for the rest kernel's last CTA, which forms U11^{-1} by
+    // doubling while the other CTAs compute the rest of the rows
+    if (Uig) {
+        for (int idx = tid; idx < r * r; idx += blockDim.x) {
+            const int i = idx / r, q = idx - i * r;
+            if (q >= i) Usc[i * kLeafRows + q] = F.from(U[s_prow[i] * WA + s_pcol[q]]);
         }
-    }
-    __syncthreads();
-    // doubling for U11^{-1}: level s pairs the blocks [b0, b0 + s) and
-    // [b0 + s, b0 + 2 s), b0 = 2 s pr (b0 + 2 s <= 64 at every level)
-    for (int ls = 0; (1 << ls) < r; ++ls) {
-        const int s = 1 << ls;
-        const int np = (r - s + 2 * s - 1) / (2 * s);
-        const int nout = np << (2 * ls);
-        // Tm = C D^{-1} (s x s per pair)
-        for (int idx = tid; idx < nout; idx += blockDim.x) {
-            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
-            const int i = rem >> ls, jj = rem & (s - 1);
-            const int b0 = 2 * s * pr;
-            const uint32_t* crow = Us + (b0 + i) * kLeafRows + b0 + s;
-            const uint32_t* dcol = Ui + (b0 + s) * kLeafRows + b0 + s + jj;
-            Acc128 acc;
-#pragma unroll 8
-            for (int l = 0; l < s; ++l) acc.add((unsigned long long)crow[l] * dcol[l * kLeafRows]);
-            Tm[idx] = acc.mod(p, mu, two64p);
-        }
-        __syncthreads();
-        // (U11^{-1})12 = -A^{-1} Tm
-        for (int idx = tid; idx < nout; idx += blockDim.x) {
-            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
-            const int i = rem >> ls, jj = rem & (s - 1);
-            const int b0 = 2 * s * pr;
-            const uint32_t* arow = Ui + (b0 + i) * kLeafRows + b0;
-            const uint32_t* tcol = Tm + (pr << (2 * ls)) + jj;
-            Acc128 acc;
-#pragma unroll 8
-            for (int l = 0; l < s; ++l) acc.add((unsigned long long)arow[l] * tcol[l << ls]);
-            const uint32_t v = acc.mod(p, mu, two64p);
-            Ui[(b0 + i) * kLeafRows + b0 + s + jj] = v ? p - v : 0u;
-        }
-        __syncthreads();
+        for (int i = tid; i < r; i += blockDim.x)
+            Usc[kLeafRows * kLeafRows + i] = F.from(F.mul(s_dv[s_prow[i]], s_invP[i]));
     }
 
     // stable partitions: pivots first (in pivot order), then the rest ascending
@@ -514,11 +476,6 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
         const int t = idx / h, q = idx - t * h;
         Eg[idx] = F.from(U[t * WA + WS + q]);
     }
-    if (Uig)
-        for (int idx = tid; idx < r * r; idx += blockDim.x) {
-            const int i = idx / r, q = idx - i * r;
-            Uig[(long long)i * ldu + q] = Ui[i * kLeafRows + q];
-        }
     // the leaf's new rows on the window: multipliers left of the diagonal of
     // the first r columns, the pivot rows' values on and right of it; in place
     // when every row is a pivot (the leaf then commits: no residual is left to
@@ -540,14 +497,73 @@ __device__ __forceinline__ void window_body(uint32_t* A, long long lda, int h, i
 __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(uint32_t* A, long long lda,
                                                                   int h, int W, int WS, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
-                                                                  uint32_t* __restrict__ Eg, uint32_t* __restrict__ Uig,
-                                                                  long long ldu, uint32_t* __restrict__ rows,
+                                                                  uint32_t* __restrict__ Eg, const uint32_t* Uig,
+                                                                  uint32_t* __restrict__ Usc, uint32_t* __restrict__ rows,
                                                                   long long ldr, LeafInfo* __restrict__ info,
                                                                   int* mbox, int seq) {
     if (p == 2u)
-        window_body<true>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info, mbox, seq);
+        window_body<true>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, Usc, rows, ldr, info, mbox, seq);
     else
-        window_body<false>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, ldu, rows, ldr, info, mbox, seq);
+        window_body<false>(A, lda, h, W, WS, p, mu, two64p, Eg, Uig, Usc, rows, ldr, info, mbox, seq);
+}
+
+// U11^{-1} (r x r, upper triangular, plain form) from U11 and the inverse of
+// its diagonal in Usc (written by the window kernel), into Uig (leading
+// dimension ldu, zeros below the diagonal), by one CTA.  Doubling:
+// [[A, C], [0, D]]^{-1} has off-diagonal block -A^{-1} C D^{-1}; level s pairs
+// the blocks [b0, b0 + s) and [b0 + s, b0 + 2 s), b0 = 2 s pr, each level two
+// products over all pairs at once, on 64 x 64 zero-padded blocks so that every
+// dot product has the level's full length and no bounds (b0 + 2 s <= 64 at
+// every level).  sm holds 2 x 64 x 64 + kTmWords words.
+__device__ void u11_inverse(int r, const uint32_t* __restrict__ Usc, uint32_t* __restrict__ Uig, long long ldu,
+                            uint32_t p, unsigned long long mu, uint32_t two64p, uint32_t* sm) {
+    uint32_t* Us = sm;                          // [64][64]: U11
+    uint32_t* Ui = Us + kLeafRows * kLeafRows;  // [64][64]: U11^{-1}
+    uint32_t* Tm = Ui + kLeafRows * kLeafRows;  // [kTmWords]: one level's products
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < kLeafRows * kLeafRows; idx += blockDim.x) {
+        const int i = idx / kLeafRows, q = idx % kLeafRows;
+        const bool in = i < r && q < r;
+        Us[idx] = in && q >= i ? __ldg(Usc + idx) : 0u;
+        Ui[idx] = in && q == i ? __ldg(Usc + kLeafRows * kLeafRows + i) : 0u;
+    }
+    __syncthreads();
+    for (int ls = 0; (1 << ls) < r; ++ls) {
+        const int s = 1 << ls;
+        const int np = (r - s + 2 * s - 1) / (2 * s);
+        const int nout = np << (2 * ls);
+        // Tm = C D^{-1} (s x s per pair)
+        for (int idx = tid; idx < nout; idx += blockDim.x) {
+            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
+            const int i = rem >> ls, jj = rem & (s - 1);
+            const int b0 = 2 * s * pr;
+            const uint32_t* crow = Us + (b0 + i) * kLeafRows + b0 + s;
+            const uint32_t* dcol = Ui + (b0 + s) * kLeafRows + b0 + s + jj;
+            Acc128 acc;
+#pragma unroll 8
+            for (int l = 0; l < s; ++l) acc.add((unsigned long long)crow[l] * dcol[l * kLeafRows]);
+            Tm[idx] = acc.mod(p, mu, two64p);
+        }
+        __syncthreads();
+        // (U11^{-1})12 = -A^{-1} Tm
+        for (int idx = tid; idx < nout; idx += blockDim.x) {
+            const int pr = idx >> (2 * ls), rem = idx & ((s << ls) - 1);
+            const int i = rem >> ls, jj = rem & (s - 1);
+            const int b0 = 2 * s * pr;
+            const uint32_t* arow = Ui + (b0 + i) * kLeafRows + b0;
+            const uint32_t* tcol = Tm + (pr << (2 * ls)) + jj;
+            Acc128 acc;
+#pragma unroll 8
+            for (int l = 0; l < s; ++l) acc.add((unsigned long long)arow[l] * tcol[l << ls]);
+            const uint32_t v = acc.mod(p, mu, two64p);
+            Ui[(b0 + i) * kLeafRows + b0 + s + jj] = v ? p - v : 0u;
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < r * r; idx += blockDim.x) {
+        const int i = idx / r, q = idx - i * r;
+        Uig[(long long)i * ldu + q] = Ui[i * kLeafRows + q];
+    }
 }
 
 // The rest of the leaf's rows.  Blocks [0, nleft): columns [0, c), the rows
@@ -559,7 +575,8 @@ __global__ void __launch_bounds__(kWinThreads, 1) lqup_window_kernel(uint32_t* A
 // (inplace = 0) the new rows go to the scratch rows (column 0 at rows, leading
 // dimension ldr); in place (every row of the leaf a pivot, so the leaf
 // commits) they overwrite A's rows (every block reads all its columns before
-// it writes them) and block 0 also applies the row order to rowperm.
+// it writes them) and block 0 also applies the row order to rowperm.  With
+// dbl set, one more block (the last) forms U11^{-1} into Uig meanwhile.
 __device__ __forceinline__ void mac96(uint32_t& lo, uint32_t& mid, uint32_t& hi, uint32_t a, uint32_t b) {
     asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
         "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
@@ -572,10 +589,16 @@ __global__ void __launch_bounds__(kThreads) lqup_rest_kernel(uint32_t* A, long l
                                                              int nleft, uint32_t p, unsigned long long mu,
                                                              uint32_t two64p, const uint32_t* __restrict__ Eg,
                                                              uint32_t* rows, long long ldr, int inplace,
-                                                             int32_t* rowperm, LeafInfo* __restrict__ info) {
+                                                             int32_t* rowperm, LeafInfo* __restrict__ info,
+                                                             const uint32_t* __restrict__ Usc, uint32_t* Uig,
+                                                             long long ldu, int dbl) {
     extern __shared__ uint32_t sm[];
     __shared__ int s_newrow[kLeafRows];
     __shared__ int32_t s_perm[kLeafRows];
+    if (dbl && blockIdx.x == gridDim.x - 1) {
+        u11_inverse(info->rank, Usc, Uig, ldu, p, mu, two64p, sm);
+        return;
+    }
     const int tid = threadIdx.x;
     const int r = info->rank;
     for (int x = tid; x < h; x += blockDim.x) s_newrow[x] = info->newrow[x];
@@ -857,7 +880,7 @@ int64_t split_rows(int64_t h) {
 int window_for(uint32_t p) { return p > 65536 ? kLeafRows : p > 64 ? kLeafRows + 32 : kMaxWin; }
 
 struct Layout {
-    size_t rows, e, usp, t1, g, info, words, rest;  // byte offsets; rest = products' workspace
+    size_t rows, e, usp, t1, g, info, usc, words, rest;  // byte offsets; rest = products' workspace
     size_t prod;                             // bytes the products need
     size_t side;                             // the look-ahead products' workspace (prod bytes)
 };
@@ -888,7 +911,8 @@ Layout layout(int64_t m, int64_t n, uint32_t p, int sms) {
     Y.t1 = Y.usp + align256(cap * cap * 4);
     Y.g = Y.t1 + align256(cap * cap * 4);
     Y.info = Y.g + align256(size_t(kGWords) * 4);
-    Y.words = Y.info + align256(sizeof(LeafInfo));
+    Y.usc = Y.info + align256(sizeof(LeafInfo));
+    Y.words = Y.usc + align256((size_t(kLeafRows) * kLeafRows + kLeafRows) * 4);
     Y.rest = Y.words + 256;
     Y.prod = 0;
     products_bound(m, n, p, sms, Y.prod);
@@ -911,6 +935,7 @@ struct Ctx {
     uint32_t* T1;   // scratch for Y' U_b^{-1}
     uint32_t* G;    // scratch for a small product G = X U_a^{-1} that cannot be formed in place
     LeafInfo* info;
+    uint32_t* Usc;  // a leaf's U11 and the inverse of its diagonal, for the rest kernel's last block
     void* ws;
     size_t ws_bytes;
     int* err;
@@ -968,9 +993,13 @@ const SideRes* side_resources() {
 ffgpu_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? FFGPU_OK : FFGPU_ERR_CUDA; }
 
 size_t smem_window(int h, int WS) {
-    return (size_t(h) * (WS + kExt) + size_t(h) * h + 2 * size_t(kLeafRows) * kLeafRows + size_t(kTmWords)) * 4;
+    return (size_t(h) * (WS + kExt) + size_t(h) * h) * 4;
 }
-size_t smem_rest(int) { return size_t(kLeafRows) * kRestCols * 4 + size_t(kLeafRows) * kLeafRows * 4; }
+size_t smem_rest(int) {
+    // the rows' blocks: R and Et; the U11 block: U11, its inverse, one level's products
+    return std::max(size_t(kLeafRows) * kRestCols * 4 + size_t(kLeafRows) * kLeafRows * 4,
+                    (2 * size_t(kLeafRows) * kLeafRows + size_t(kTmWords)) * 4);
+}
 
 ffgpu_status set_attrs() {
     static std::once_flag once;
@@ -997,8 +1026,8 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     const int seq = ++x.mbox->seq;
     ffgpu_status st = cuda_ok(timed_launch("lqup_window", x.s, [&] {
         lqup_window_kernel<<<1, kWinThreads, smem_window((int)h, WS), x.s>>>(
-            Ab + c, x.lda, (int)h, W, WS, x.p, x.mu, x.two64p, x.E, Uo, ldu, x.rows + c, x.n, x.info, x.mbox->dev,
-            seq);
+            Ab + c, x.lda, (int)h, W, WS, x.p, x.mu, x.two64p, x.E, Uo, x.Usc, x.rows + c, x.n, x.info,
+            x.mbox->dev, seq);
         return cudaGetLastError();
     }));
     if (st != FFGPU_OK) return st;
@@ -1016,11 +1045,13 @@ ffgpu_status leaf(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank,
     // every row a pivot: the window kernel wrote its columns in place, the rest
     // follows in place (and applies the row order to rowperm)
     const bool inplace = r == h;
-    if (nleft + nright > 0) {
+    // one more block forms the inverse of the pivot block when it is asked for
+    const int dbl = Uo ? 1 : 0;
+    if (nleft + nright + dbl > 0) {
         st = cuda_ok(timed_launch("lqup_rest", x.s, [&] {
-            lqup_rest_kernel<<<nleft + nright, kThreads, smem_rest((int)h), x.s>>>(
+            lqup_rest_kernel<<<nleft + nright + dbl, kThreads, smem_rest((int)h), x.s>>>(
                 Ab, x.lda, (int)h, (int)c, W, (int)x.n, nleft, x.p, x.mu, x.two64p, x.E, x.rows, x.n, inplace ? 1 : 0,
-                x.rowperm + rb, x.info);
+                x.rowperm + rb, x.info, x.Usc, Uo, ldu, dbl);
             return cudaGetLastError();
         }));
         if (st != FFGPU_OK) return st;
@@ -1258,6 +1289,7 @@ ffgpu_status lqup_run(int64_t m, int64_t n, uint32_t p, uint32_t* A, int64_t lda
     x.T1 = reinterpret_cast<uint32_t*>(w + Y.t1);
     x.G = reinterpret_cast<uint32_t*>(w + Y.g);
     x.info = reinterpret_cast<LeafInfo*>(w + Y.info);
+    x.Usc = reinterpret_cast<uint32_t*>(w + Y.usc);
     x.err = err;
     x.s = s;
     x.win = window_for(p);
