@@ -875,9 +875,10 @@ int64_t split_rows(int64_t h) {
 }
 
 // Window width: wide enough for a leaf's pivots plus the columns that small
-// fields skip (a zero Schur entry has probability 1/p: above 2^16 a 64-row
-// leaf meets one with probability below 10^-3, and then only splits).
-int window_for(uint32_t p) { return p > 65536 ? kLeafRows : p > 64 ? kLeafRows + 32 : kMaxWin; }
+// fields skip (a zero Schur entry has probability 1/p: above 2^10 a 64-row
+// leaf of uniform entries meets one with probability about 1/p < 10^-3, and
+// then only splits, while 96 columns cost every leaf an eighth more time).
+int window_for(uint32_t p) { return p > 1024 ? kLeafRows : p > 64 ? kLeafRows + 32 : kMaxWin; }
 
 struct Layout {
     size_t rows, e, usp, t1, g, info, usc, words, rest;  // byte offsets; rest = products' workspace
