@@ -6,10 +6,11 @@
 // solve the second half.  The recursion stops at diagonal blocks of L rows,
 // L between 128 and 1024 (two leaves up to 2048 rows, more beyond: the rule
 // and its measurements are at leaf_size), whose inverses are computed up
-// front: one kernel inverts every 128 x 128 diagonal block (one CTA per block,
-// eight lanes per column of the inverse, substitution mod p; non-unit
-// diagonals inverted by the extended Euclidean algorithm of section 2.1.1; a
-// non-invertible diagonal entry is recorded in the device error word), then
+// front: one kernel inverts every 128 x 128 diagonal block (one CTA per block
+// in shared memory: 16 x 16 blocks by substitution mod p, then doubling on
+// them, see trsm_invert_blocks; non-unit diagonals inverted by the extended
+// Euclidean algorithm of section 2.1.1; a non-invertible diagonal entry is
+// recorded in the device error word), then
 // each doubling level s -> 2s forms the off-diagonal block of every pair
 // [[A, 0], [C, D]] (lower; upper by symmetry) as -D^{-1} (C A^{-1}) with two
 // batched products over all pairs at once (one grouped launch each).  A leaf
@@ -46,98 +47,200 @@ int64_t leaf_size(int64_t sz) {
     return L;
 }
 
-// Exact sum of products as a 128-bit value (hi, lo); reduced once.
-struct Acc128 {
-    unsigned long long lo = 0, hi = 0;
-    __device__ __forceinline__ void add(unsigned long long v) {
-        lo += v;
-        hi += (lo < v) ? 1ull : 0ull;
-    }
-    __device__ __forceinline__ uint32_t mod(uint32_t p, unsigned long long mu, uint32_t two64p) const {
-        const unsigned long long a = (unsigned long long)mod_u64(hi, p, mu) * two64p;
-        return mod_u64((unsigned long long)mod_u64(a, p, mu) + mod_u64(lo, p, mu), p, mu);
-    }
-};
+// Exact multiply-add into a 96-bit sum (lo, mid, hi): below 2^68 for the at
+// most 64 products of residues < 2^31 that one entry of a block product sums.
+__device__ __forceinline__ void inv_mac96(uint32_t& lo, uint32_t& mid, uint32_t& hi, uint32_t a, uint32_t b) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(lo), "+r"(mid), "+r"(hi)
+        : "r"(a), "r"(b));
+}
+
+// (hi 2^64 + mid 2^32 + lo) mod p.
+__device__ __forceinline__ uint32_t inv_mod96(uint32_t lo, uint32_t mid, uint32_t hi, uint32_t p,
+                                              unsigned long long mu, uint32_t two64p) {
+    const uint32_t th = mod_u64((unsigned long long)mod_u64(hi, p, mu) * two64p, p, mu);
+    const uint32_t tl = mod_u64(((unsigned long long)mid << 32) | lo, p, mu);
+    return th + tl >= p ? th + tl - p : th + tl;
+}
 
 // Inverse of diagonal block b of T (rows/cols [b kBlk, b kBlk + tb)), written
 // densely into the leaf-sized inverse that contains it (kBlk x kBlk, zeros
-// outside the triangle).  Column j of the inverse solves T x = e_j by forward
-// (lower) or back (upper) substitution mod p, independently of the other
-// columns: a CTA takes kInvCols columns of one block (kBlk / kInvCols CTAs
-// per block, so that the sequential chains of many columns run on many SMs),
-// eight lanes per column; each step's dot product is split over the eight
-// lanes (exact 128-bit partial sums, reduced once, combined by shuffles), so
-// the chain is one short step per row, and it starts at the first row where
-// one of the CTA's columns has a non-zero entry.
-constexpr int kInvCols = 32;
-constexpr int kInvThreads = 8 * kInvCols;
-constexpr int kBX = kBlk + 1;  // padded column stride of the inverse in shared memory
+// outside the triangle and beyond tb).  One CTA per block, everything in
+// shared memory: the block of T (reduced mod p; a ragged block padded with
+// the identity, whose inverse it leaves unchanged), then the inverses of its
+// eight 16 x 16 diagonal blocks by substitution (one warp per block, one lane
+// per column, the column in registers: each entry is d_i (delta_ij - the dot
+// product with the entries above it), d_i the inverse of the diagonal
+// entry), then doubling on pairs of s-blocks, s = 16, 32, 64: the
+// off-diagonal block of [[A, 0], [C, D]]^{-1} is -D^{-1} (C A^{-1}) (lower;
+// -A^{-1} (C D^{-1}) for [[A, C], [0, D]]), two block products per level over
+// all pairs at once, exact 96-bit sums reduced once per entry.  A
+// non-invertible diagonal entry of a non-unit triangle is recorded in the
+// device error word.
+constexpr int kInvThreads = 1024;  // the kernel assumes blockDim.x == kInvThreads
+constexpr int kInvSub = 16;          // diagonal blocks inverted by substitution
+constexpr int kBS = kBlk + 1;        // padded row stride of the blocks in shared memory
+constexpr size_t kInvSmemWords = size_t(2) * kBlk * kBS + size_t(kBlk) * kBlk / 4 + kBlk;
+
+// One level's block products over all pairs: out_q = P_q Q_q (s x s, inner
+// dimension s), negated when asked.  P_q and Q_q are s x s blocks of
+// the shared arrays at the pair's offsets; out_q is written at its own.
+struct InvBlk {
+    const uint32_t* base;
+    int stride;
+    int r0, c0;    // the pair-0 block's corner
+    int dr, dc;    // added per pair
+};
+
+__device__ __forceinline__ void inv_add96(uint32_t& lo, uint32_t& mid, uint32_t& hi, unsigned long long v) {
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(lo), "+r"(mid), "+r"(hi)
+        : "r"((uint32_t)v), "r"((uint32_t)(v >> 32)));
+}
+
+// A thread takes four entries of one row of out_q, columns cc + e s/4 (so that
+// the lanes of a warp read consecutive words of Q_q), and sums their products
+// four at a time in 64-bit words (4 (p - 1)^2 < 2^64), folded into 96 bits.
+__device__ __forceinline__ void inv_level_product(int s, int npairs, InvBlk P, InvBlk Q, uint32_t* out,
+                                                  int ostride, int or0, int oc0, int odr, int odc, bool negate,
+                                                  uint32_t p, unsigned long long mu, uint32_t two64p) {
+    const int sq = s / 4, per_pair = s * sq;
+    for (int o = threadIdx.x; o < npairs * per_pair; o += blockDim.x) {
+        const int q = o / per_pair, rem = o - q * per_pair, r = rem / sq, cc = rem - r * sq;
+        const uint32_t* pr = P.base + (P.r0 + q * P.dr + r) * P.stride + P.c0 + q * P.dc;
+        const uint32_t* qc = Q.base + (Q.r0 + q * Q.dr) * Q.stride + Q.c0 + q * Q.dc + cc;
+        uint32_t lo[4] = {0u, 0u, 0u, 0u}, mid[4] = {0u, 0u, 0u, 0u}, hi[4] = {0u, 0u, 0u, 0u};
+        for (int l0 = 0; l0 < s; l0 += 4) {
+            unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+#pragma unroll
+            for (int l = l0; l < l0 + 4; ++l) {
+                const unsigned long long a = pr[l];
+                const uint32_t* qr = qc + l * Q.stride;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] += a * qr[e * sq];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) inv_add96(lo[e], mid[e], hi[e], acc[e]);
+        }
+        uint32_t* orow = out + (or0 + q * odr + r) * ostride + oc0 + q * odc + cc;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            uint32_t v = inv_mod96(lo[e], mid[e], hi[e], p, mu, two64p);
+            if (negate && v != 0u) v = p - v;
+            orow[e * sq] = v;
+        }
+    }
+}
+
+// Column j of the inverse of one kInvSub x kInvSub triangular block Tg (row
+// stride kBS, inverse diagonal dg), by substitution: rows top to bottom
+// (lower) or bottom to top (upper).  Entries outside the column's triangle
+// stay zero, so every sum may run over all earlier (later) rows.
+template <bool kUpper>
+__device__ __forceinline__ void inv_sub_column(const uint32_t* Tg, const uint32_t* dg, int j, uint32_t (&x)[kInvSub],
+                                               uint32_t p, unsigned long long mu, uint32_t two64p) {
+#pragma unroll
+    for (int i = 0; i < kInvSub; ++i) x[i] = 0u;
+#pragma unroll
+    for (int t = 0; t < kInvSub; ++t) {
+        const int i = kUpper ? kInvSub - 1 - t : t;
+        uint32_t lo = 0u, mid = 0u, hi = 0u;
+#pragma unroll
+        for (int l = kUpper ? i + 1 : 0; l < (kUpper ? kInvSub : i); ++l) inv_mac96(lo, mid, hi, Tg[i * kBS + l], x[l]);
+        if (kUpper ? i <= j : i >= j) {
+            const uint32_t a = inv_mod96(lo, mid, hi, p, mu, two64p);
+            const uint32_t rhs = i == j ? 1u : 0u;
+            const uint32_t v = rhs >= a ? rhs - a : rhs + (p - a);
+            x[i] = mod_u64((unsigned long long)v * dg[i], p, mu);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kInvThreads) trsm_invert_blocks(const uint32_t* __restrict__ T, long long ldt,
                                                                   int size, int upper, int unit, uint32_t p,
                                                                   unsigned long long mu, uint32_t two64p,
                                                                   uint32_t* __restrict__ Inv, int leaf, int* err) {
     extern __shared__ uint32_t sm[];
-    // this CTA's columns, column-major with a padded stride: entry (i, q kInvCols + jl) of the inverse at
-    // sX[jl*kBX + i], so that the eight lanes of a column read consecutive words (distinct banks) in the
-    // dot products below and the final copy, which walks the columns, spreads over the banks too
-    uint32_t* sX = sm;
-    uint32_t* sT = sm + kInvCols * kBX;          // [kBlk][kBlk]: the block of T
-    uint32_t* sD = sT + kBlk * kBlk;             // [kBlk] inverse diagonal
-    const int b = blockIdx.x / (kBlk / kInvCols), q = blockIdx.x % (kBlk / kInvCols);
-    const int base = b * kBlk;
-    const int tb = min(kBlk, size - base);
+    uint32_t* sT = sm;                      // [kBlk][kBS]: the block of T
+    uint32_t* sX = sT + kBlk * kBS;         // [kBlk][kBS]: its inverse
+    uint32_t* sTmp = sX + kBlk * kBS;       // a level's C A^{-1} (C D^{-1}) blocks, s x s each
+    uint32_t* sD = sTmp + kBlk * kBlk / 4;  // [kBlk]: inverse diagonal
+    const int b = blockIdx.x, base = b * kBlk, tb = min(kBlk, size - base);
     const uint32_t* Tb = T + (long long)base * ldt + base;
-    for (int idx = threadIdx.x; idx < tb * kBlk; idx += blockDim.x) {
-        const int r = idx / kBlk, c = idx % kBlk;
-        sT[idx] = c < tb ? __ldg(Tb + (long long)r * ldt + c) : 0u;
+    // the block's words, sixteen loads in flight per thread at a time
+    constexpr int kLd = kBlk * kBlk / kInvThreads, kBatch = 16;
+    static_assert(kLd % kBatch == 0, "whole batches of loads");
+#pragma unroll 1
+    for (int u0 = 0; u0 < kLd; u0 += kBatch) {
+        uint32_t v[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = threadIdx.x + (u0 + u) * kInvThreads, r = idx / kBlk, c = idx - r * kBlk;
+            v[u] = (r < tb && c < tb) ? __ldg(Tb + (long long)r * ldt + c) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int idx = threadIdx.x + (u0 + u) * kInvThreads, r = idx / kBlk, c = idx - r * kBlk;
+            sT[r * kBS + c] = (r < tb && c < tb) ? mod_u64(v[u], p, mu) : (r == c ? 1u : 0u);
+            sX[r * kBS + c] = 0u;
+        }
     }
-    for (int i = threadIdx.x; i < tb; i += blockDim.x) {
-        if (unit) {
-            sD[i] = 1u;
-        } else {
-            const uint32_t d = inv_mod_dev(mod_u64(__ldg(Tb + (long long)i * ldt + i), p, mu), p);
+    for (int i = threadIdx.x; i < kBlk; i += blockDim.x) {
+        uint32_t d = 1u;
+        if (!unit && i < tb) {
+            d = inv_mod_dev(mod_u64(__ldg(Tb + (long long)i * ldt + i), p, mu), p);
             if (d == 0) atomicCAS(err, 0, (int)kDevSingular);
-            sD[i] = d;
         }
-    }
-    for (int idx = threadIdx.x; idx < kInvCols * kBX; idx += blockDim.x) sX[idx] = 0u;
-    __syncthreads();
-    const int jl = threadIdx.x >> 3, gl = threadIdx.x & 7;
-    const int j = q * kInvCols + jl;
-    const bool col = j < tb;
-    // rows above (lower) / below (upper) the CTA's first column are zero in all its columns
-    const int s0 = upper ? max(0, tb - (q + 1) * kInvCols) : q * kInvCols;
-    uint32_t* Xj = sX + jl * kBX;
-    for (int s = s0; s < tb; ++s) {  // same trip count in every lane (shuffles below)
-        const int i = upper ? tb - 1 - s : s;
-        const bool act = col && (upper ? i <= j : i >= j);
-        Acc128 acc;
-        if (act) {
-            // any 32-bit word times a residue < 2^31 stays below 2^63
-            const uint32_t* Ti = sT + i * kBlk;
-            const int lo = upper ? i + 1 : j, hi = upper ? j + 1 : i;
-            for (int l = lo + gl; l < hi; l += 8) acc.add((unsigned long long)Ti[l] * Xj[l]);
-        }
-        uint32_t v = act ? acc.mod(p, mu, two64p) : 0u;
-        for (int o = 4; o > 0; o >>= 1) {
-            const uint32_t y = __shfl_xor_sync(0xffffffffu, v, o);
-            v += y;
-            v = v >= p ? v - p : v;
-        }
-        if (act && gl == 0) {
-            const uint32_t rhs = (i == j) ? 1u : 0u;
-            const uint32_t t = rhs >= v ? rhs - v : rhs + (p - v);
-            Xj[i] = mod_u64((unsigned long long)t * sD[i], p, mu);
-        }
-        __syncwarp();
+        sD[i] = d;
     }
     __syncthreads();
-    // this CTA's columns of the dense kBlk x kBlk block (zero padding beyond tb)
+    {
+        // the kInvSub x kInvSub diagonal blocks: warp w takes block w, lane j its column j
+        const int w = threadIdx.x >> 5, j = threadIdx.x & 31;
+        if (w < kBlk / kInvSub && j < kInvSub) {
+            const int g = w * kInvSub;
+            const uint32_t* Tg = sT + g * kBS + g;
+            uint32_t x[kInvSub];
+            if (upper)
+                inv_sub_column<true>(Tg, sD + g, j, x, p, mu, two64p);
+            else
+                inv_sub_column<false>(Tg, sD + g, j, x, p, mu, two64p);
+#pragma unroll
+            for (int i = 0; i < kInvSub; ++i) sX[(g + i) * kBS + g + j] = x[i];
+        }
+    }
+    __syncthreads();
+    for (int s = kInvSub; s < kBlk; s *= 2) {
+        const int np = kBlk / (2 * s), s2 = 2 * s;
+        if (!upper) {
+            // tmp_q = C_q A_q^{-1}: C_q = T[b, a], A_q^{-1} = X[a, a]
+            inv_level_product(s, np, InvBlk{sT, kBS, s, 0, s2, s2}, InvBlk{sX, kBS, 0, 0, s2, s2}, sTmp, s, 0, 0, s, 0,
+                              false, p, mu, two64p);
+            __syncthreads();
+            // X[b, a] = -D_q^{-1} tmp_q, D_q^{-1} = X[b, b]
+            inv_level_product(s, np, InvBlk{sX, kBS, s, s, s2, s2}, InvBlk{sTmp, s, 0, 0, s, 0}, sX, kBS, s, 0, s2, s2,
+                              true, p, mu, two64p);
+        } else {
+            // tmp_q = C_q D_q^{-1}: C_q = T[a, b], D_q^{-1} = X[b, b]
+            inv_level_product(s, np, InvBlk{sT, kBS, 0, s, s2, s2}, InvBlk{sX, kBS, s, s, s2, s2}, sTmp, s, 0, 0, s, 0,
+                              false, p, mu, two64p);
+            __syncthreads();
+            // X[a, b] = -A_q^{-1} tmp_q, A_q^{-1} = X[a, a]
+            inv_level_product(s, np, InvBlk{sX, kBS, 0, 0, s2, s2}, InvBlk{sTmp, s, 0, 0, s, 0}, sX, kBS, 0, s, s2, s2,
+                              true, p, mu, two64p);
+        }
+        __syncthreads();
+    }
+    // the dense kBlk x kBlk block (zeros beyond tb) into its leaf's inverse
     const int per = leaf / kBlk;
     uint32_t* out = Inv + (size_t)(b / per) * leaf * leaf + (size_t)(b % per) * kBlk * (leaf + 1);
-    for (int idx = threadIdx.x; idx < kBlk * kInvCols; idx += blockDim.x) {
-        const int r = idx / kInvCols, cl = idx % kInvCols, c = q * kInvCols + cl;
-        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[cl * kBX + r] : 0u;
+    for (int idx = threadIdx.x; idx < kBlk * kBlk; idx += blockDim.x) {
+        const int r = idx / kBlk, c = idx - r * kBlk;
+        out[(size_t)r * leaf + c] = (r < tb && c < tb) ? sX[r * kBS + c] : 0u;
     }
 }
 
@@ -489,7 +592,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
     }
     // leaf inverses: zero (the other triangle), 128-blocks by substitution, then doubling
     if (cudaMemsetAsync(inv, 0, size_t(Y.nl) * Y.L * Y.L * 4, s) != cudaSuccess) return FFGPU_ERR_CUDA;
-    const size_t smem = (size_t(kInvCols) * kBX + size_t(kBlk) * kBlk + kBlk) * 4;
+    const size_t smem = kInvSmemWords * 4;
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(trsm_invert_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -497,7 +600,7 @@ ffgpu_status ftrsm_run(int side, int uplo, int diag, int algo, int64_t m, int64_
             return FFGPU_ERR_CUDA;
         attr_set = true;
     }
-    const int nb = (int)((sz + kBlk - 1) / kBlk) * (kBlk / kInvCols);  // CTAs: column groups of every block
+    const int nb = (int)((sz + kBlk - 1) / kBlk);  // one CTA per block
     if (timed_launch("trsm_invert_blocks", s, [&] {
             trsm_invert_blocks<<<nb, kInvThreads, smem, s>>>(T, ldt, (int)sz, uplo, diag, p, mu, two64p, inv, (int)Y.L,
                                                       err);
