@@ -453,9 +453,10 @@ void set_batched_small_macs(int64_t macs) { g_batch_small_macs.store(macs < 0 ? 
 
 namespace {
 
-// Two launches by tile size: products with a dimension of at most 32 on
-// 32 x 32 tiles (less padding), the others on 64 x 64 tiles.  Tables: per size
-// the job records, then the tile -> job map.
+// Two launches by tile size: products with a dimension of at most 32, or
+// whose output pads less on 32 x 32 tiles (small_on_32), on 32 x 32 tiles, the
+// others on 64 x 64 tiles.  Tables: per size the job records, then the tile ->
+// job map.
 struct SmallGroup {
     std::vector<const ffgpu_fgemm_desc*> d;
     std::vector<const ffgpu_fgemm_desc*> by[2];  // [0]: 64 x 64 tiles, [1]: 32 x 32 tiles
@@ -465,10 +466,24 @@ struct SmallGroup {
 
 constexpr int kSmallTile[2] = {64, 32};
 
+// 32 x 32 tiles for a product with a dimension of at most 32, or whose output
+// padded to 32 x 32 tiles, weighted by kSmall32Cost (a 32 x 32 tile stages
+// twice the words per multiply-add of a 64 x 64 one), is smaller than padded
+// to 64 x 64 tiles.  Measured on the 131,072-product multi-modular batch
+// (ms for the whole batch, weights 1.0 / 1.25 / 1.5 / the first rule alone):
+// 215.0 / 214.8 / 217.4 / 216.7.
+constexpr double kSmall32Cost = 1.25;
+bool small_on_32(int64_t m, int64_t n) {
+    if (std::min(m, n) <= 32) return true;
+    const double p32 = double((m + 31) / 32 * 32) * double((n + 31) / 32 * 32);
+    const double p64 = double((m + 63) / 64 * 64) * double((n + 63) / 64 * 64);
+    return p32 * kSmall32Cost < p64;
+}
+
 void layout_small(SmallGroup& G) {
     G.by[0].clear();
     G.by[1].clear();
-    for (const ffgpu_fgemm_desc* d : G.d) G.by[std::min(d->m, d->n) <= 32 ? 1 : 0].push_back(d);
+    for (const ffgpu_fgemm_desc* d : G.d) G.by[small_on_32(d->m, d->n) ? 1 : 0].push_back(d);
     size_t off = 0;
     for (int g = 0; g < 2; ++g) {
         G.tiles[g] = 0;

@@ -63,7 +63,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int T>
+template <int T, bool kTrimK>
 __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int row0, int col0,
                                            const uint32_t* __restrict__ A, long long lda,
                                            const uint32_t* __restrict__ B, long long ldb, uint32_t* C, long long ldc,
@@ -108,8 +108,7 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
             cp_async_wait<0>();
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kSmK; ++kk) {
+        auto step = [&](int kk) {
             const uint4 a = *reinterpret_cast<const uint4*>(&As[buf][kk][ty * 4]);
             const uint4 b = *reinterpret_cast<const uint4*>(&Bs[buf][kk][tx * 4]);
             const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
@@ -117,6 +116,15 @@ __device__ __forceinline__ void small_tile(int m, int n, int kbeg, int kend, int
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mac96(lo[i][j], mid[i][j], hi[i][j], av[i], bv[j]);
+        };
+        if (!kTrimK || kend - k0 >= kSmK) {
+#pragma unroll 4
+            for (int kk = 0; kk < kSmK; ++kk) step(kk);
+        } else {
+            // kTrimK: the last, partial chunk takes only its words (the rest
+            // are zeros), which pays where most products have a ragged k
+#pragma unroll 4
+            for (int kk = 0; kk < kend - k0; ++kk) step(kk);
         }
         __syncthreads();
     }
@@ -148,7 +156,7 @@ __global__ void __launch_bounds__(kSmThreads) small_gemm_kernel(int m, int n, in
                                                                 uint32_t p, unsigned long long mu, uint32_t two64p,
                                                                 uint32_t alpha, uint32_t beta) {
     const int kbeg = blockIdx.z * kps, kend = min(k, kbeg + kps);
-    small_tile<kSmT>(m, n, kbeg, kend, blockIdx.y * kSmT, blockIdx.x * kSmT, A, lda, B, ldb, C, ldc,
+    small_tile<kSmT, false>(m, n, kbeg, kend, blockIdx.y * kSmT, blockIdx.x * kSmT, A, lda, B, ldb, C, ldc,
                      part ? part + (long long)blockIdx.z * m * n : nullptr, p, mu, two64p, alpha, beta);
 }
 
@@ -162,7 +170,7 @@ __global__ void __launch_bounds__(T * T / 16) small_grouped_kernel(const SmallJo
     const SmallJob& J = jobs[tile_job[t]];
     const int local = t - J.tile0;
     const int tr = local / J.tiles_n, tc = local - tr * J.tiles_n;
-    small_tile<T>(J.m, J.n, 0, J.k, tr * T, tc * T, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, nullptr, J.p, J.mu,
+    small_tile<T, true>(J.m, J.n, 0, J.k, tr * T, tc * T, J.A, J.lda, J.B, J.ldb, J.C, J.ldc, nullptr, J.p, J.mu,
                   J.two64p, J.alpha, J.beta);
 }
 
