@@ -55,6 +55,29 @@ def test_mixed_shapes_and_moduli():
         assert np.array_equal(got, oracle.fgemm(A, B, p, al, be, C)), (A.shape, B.shape, p)
 
 
+def test_tile_classes_and_ragged_inner_dimensions():
+    """Small products on both tile sizes of the grouped CUDA-core launch (32 x
+    32 tiles for a dimension of at most 32 or where they pad less, e.g. 90 x
+    90 or 129 x 65; 64 x 64 tiles for 64 x 64 or 100 x 64) with inner
+    dimensions that end inside a 32-long chunk (1, 5, 31, 33, 63, 100), words
+    not reduced mod p: every entry against the oracle."""
+    rng = W.rng_for("multimodular", 101)
+    shapes = [(33, 33), (40, 700), (90, 90), (65, 130), (96, 96), (100, 64), (31, 500), (64, 64), (129, 65)]
+    ks = [1, 5, 31, 33, 63, 100]
+    primes = [251, 65521, 2147483647]
+    problems = []
+    for i, (m, n) in enumerate(shapes):
+        for j, k in enumerate(ks):
+            p = primes[(i + j) % len(primes)]
+            A = W.uniform_words(rng, (m, k))
+            B = W.uniform_words(rng, (k, n))
+            C = W.uniform_words(rng, (m, n))
+            problems.append((A, B, C, p, int(rng.integers(0, 2**32)), int(rng.integers(0, 2**32))))
+    outs = run_batch(problems)
+    for (A, B, C, p, al, be), got in zip(problems, outs):
+        assert np.array_equal(got, oracle.fgemm(A, B, p, al, be, C)), (A.shape, B.shape, p)
+
+
 def test_multimodular_instances_subset():
     shapes, primes = W.multimodular_instances(count=24, nprimes=32)
     use = primes[::8]  # 4 of the 32 primes
