@@ -814,6 +814,110 @@ __global__ void __launch_bounds__(kThreads) row_scatter_kernel(const uint32_t* _
     }
 }
 
+// Products of the recursion's smallest blocks (every dimension at most
+// kTiny), one launch in place of a k-split product and its reduction kernel
+// (two launches each on the pivot chain), spread over a few CTAs.  Stage 1
+// forms T = P1 Q1 (m x n, inner dimension k1); with P2 given, stage 2 forms
+// P2 T (m2 x n, inner dimension m).  The result times alpha goes to C.
+// Without P2 the CTAs split the rows (CTA j: rows [j kTinyPart, ...)), so C
+// may be P1 itself: each CTA reads and writes only its own rows.  With P2
+// they split the columns (CTA j: columns [j kTinyPart, ...)), and C must not
+// overlap the operands.  With zr > 0 the first CTA also sets the zr x zc
+// block at Z to zero.  Each entry's products of residues are summed four at
+// a time in 64 bits (4 (p - 1)^2 < 2^64) and folded into 96 bits before one
+// reduction.
+constexpr int kTiny = 64;
+constexpr int kTinyPart = 8;
+constexpr int kTinyThreads = 512;
+
+__device__ __forceinline__ void tiny_add96(uint32_t& lo, uint32_t& mid, uint32_t& hi, unsigned long long v) {
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(lo), "+r"(mid), "+r"(hi)
+        : "r"((uint32_t)v), "r"((uint32_t)(v >> 32)));
+}
+
+// out (m x n, row stride n) = A (m x k, row stride k) B (k x n, row stride n)
+// mod p; out is none of A, B.
+__device__ void tiny_mm(uint32_t* out, const uint32_t* A, const uint32_t* B, int m, int n, int k, uint32_t p,
+                        unsigned long long mu, uint32_t two64p) {
+    for (int o = threadIdx.x; o < m * n; o += blockDim.x) {
+        const int r = o / n, c = o - r * n;
+        const uint32_t* a = A + r * k;
+        const uint32_t* b = B + c;
+        uint32_t lo = 0u, mid = 0u, hi = 0u;
+        int l = 0;
+        for (; l + 4 <= k; l += 4) {
+            unsigned long long acc = (unsigned long long)a[l] * b[l * n];
+            acc += (unsigned long long)a[l + 1] * b[(l + 1) * n];
+            acc += (unsigned long long)a[l + 2] * b[(l + 2) * n];
+            acc += (unsigned long long)a[l + 3] * b[(l + 3) * n];
+            tiny_add96(lo, mid, hi, acc);
+        }
+        unsigned long long acc = 0ull;
+        for (; l < k; ++l) acc += (unsigned long long)a[l] * b[l * n];
+        tiny_add96(lo, mid, hi, acc);
+        const uint32_t th = mod_u64((unsigned long long)mod_u64(hi, p, mu) * two64p, p, mu);
+        const uint32_t tl = mod_u64(((unsigned long long)mid << 32) | lo, p, mu);
+        out[o] = th + tl >= p ? th + tl - p : th + tl;
+    }
+}
+
+// rows x cols block of a row-major matrix (leading dimension ld) into shared
+// memory (row stride cols), reduced mod p
+__device__ __forceinline__ void tiny_load(uint32_t* dst, const uint32_t* src, long long ld, int rows, int cols,
+                                          uint32_t p, unsigned long long mu) {
+    for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) {
+        const int r = i / cols, c = i - r * cols;
+        dst[i] = mod_u64(src[(long long)r * ld + c], p, mu);
+    }
+}
+
+__global__ void __launch_bounds__(kTinyThreads) lqup_tiny_kernel(int m, int n, int k1, const uint32_t* P1,
+                                                                 long long ld1, const uint32_t* Q1, long long ldq1,
+                                                                 int m2, const uint32_t* P2, long long ld2,
+                                                                 uint32_t alpha, uint32_t* C, long long ldc,
+                                                                 uint32_t* Z, long long ldz, int zr, int zc,
+                                                                 uint32_t p, unsigned long long mu, uint32_t two64p) {
+    __shared__ uint32_t sA[kTiny * kTiny], sB[kTiny * kTiny], sT[kTiny * kTiny];
+    const int part = blockIdx.x * kTinyPart;
+    const uint32_t* R = sT;
+    int rows, cols, r0 = 0, c0 = 0;
+    if (P2 == nullptr) {  // rows [part, part + rows) of P1 Q1
+        r0 = part;
+        rows = min(kTinyPart, m - part);
+        cols = n;
+        tiny_load(sA, P1 + (long long)r0 * ld1, ld1, rows, k1, p, mu);
+        tiny_load(sB, Q1, ldq1, k1, n, p, mu);
+        __syncthreads();
+        tiny_mm(sT, sA, sB, rows, n, k1, p, mu, two64p);
+    } else {  // columns [part, part + cols) of P2 (P1 Q1)
+        c0 = part;
+        cols = min(kTinyPart, n - part);
+        tiny_load(sA, P1, ld1, m, k1, p, mu);
+        tiny_load(sB, Q1 + c0, ldq1, k1, cols, p, mu);
+        __syncthreads();
+        tiny_mm(sT, sA, sB, m, cols, k1, p, mu, two64p);
+        __syncthreads();  // stage 1 has read sA and sB
+        tiny_load(sA, P2, ld2, m2, m, p, mu);
+        __syncthreads();
+        tiny_mm(sB, sA, sT, m2, cols, m, p, mu, two64p);
+        R = sB;
+        rows = m2;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows * cols; i += blockDim.x) {
+        const int r = i / cols, c = i - r * cols;
+        C[(long long)(r0 + r) * ldc + c0 + c] = alpha == 1u ? R[i] : mod_u64((unsigned long long)R[i] * alpha, p, mu);
+    }
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < zr * zc; i += blockDim.x) {
+            const int r = i / zc, c = i - r * zc;
+            Z[(long long)r * ldz + c] = 0u;
+        }
+}
+
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 int grid_rows(int64_t rows) { return (int)std::max<int64_t>(1, std::min<int64_t>(rows, 152 * 16)); }
@@ -1158,6 +1262,17 @@ ffgpu_status rec(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank, 
         if (fgemm_ws_bytes(m, n, k, x.p, sms) > x.ws_bytes) return FFGPU_ERR_NOMEM;
         return fgemm_run(m, n, k, x.p, alpha, Ap, la, Bp, lb, beta, Cp, lc, x.ws, x.ws_bytes, x.err, x.s, 0, false);
     };
+    // one-CTA products of blocks of at most kTiny (see lqup_tiny_kernel)
+    auto tiny = [&](int m, int n, int k1, const uint32_t* P1, int64_t ld1, const uint32_t* Q1, int64_t ldq1, int m2,
+                    const uint32_t* P2, int64_t ld2, uint32_t alpha, uint32_t* Cp, int64_t ldc, uint32_t* Zp,
+                    int64_t ldz, int zr, int zc) -> ffgpu_status {
+        return cuda_ok(timed_launch("lqup_tiny", x.s, [&] {
+            const int parts = ((P2 ? n : m) + kTinyPart - 1) / kTinyPart;
+            lqup_tiny_kernel<<<parts, kTinyThreads, 0, x.s>>>(m, n, k1, P1, ld1, Q1, ldq1, m2, P2, ld2, alpha, Cp, ldc,
+                                                              Zp, ldz, zr, zc, x.p, x.mu, x.two64p);
+            return cudaGetLastError();
+        }));
+    };
     if (r1 > 0) {
         uint32_t* top = x.A + rb * x.lda + c;
         uint32_t* bot = x.A + (rb + h1) * x.lda + c;
@@ -1165,7 +1280,11 @@ ffgpu_status rec(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank, 
         // writes (the tensor-core route converts its operands first; the
         // CUDA-core kernel does when one column tile covers G), else through
         // a scratch (a small product: h2 r1 <= 2^27 / r1 < kGWords)
-        if (fgemm_small(h2, r1, r1) ? r1 <= 64 : fgemm_single_pass(x.p, r1)) {
+        if (h2 <= kTiny && r1 <= kTiny) {
+            if ((st = tiny((int)h2, (int)r1, (int)r1, bot, x.lda, Ua, lda_u, 0, nullptr, 0, 1, bot, x.lda, nullptr, 0,
+                           0, 0)) != FFGPU_OK)
+                return st;
+        } else if (fgemm_small(h2, r1, r1) ? r1 <= 64 : fgemm_single_pass(x.p, r1)) {
             if ((st = product(h2, r1, r1, 1, bot, x.lda, Ua, lda_u, 0, bot, x.lda)) != FFGPU_OK) return st;
         } else {
             if (!fgemm_small(h2, r1, r1) || h2 * r1 > kGWords) return FFGPU_ERR_INVALID;
@@ -1208,7 +1327,13 @@ ffgpu_status rec(const Ctx& x, int64_t rb, int64_t h, int64_t c, int64_t* rank, 
         if ((st = reverse_rows(x, rb + h1, rb + h1 + r2)) != FFGPU_OK) return st;
         if ((st = reverse_rows(x, rb + r1, rb + h1 + r2)) != FFGPU_OK) return st;
     }
-    if (Uo && r1 > 0 && r2 > 0) {
+    if (Uo && r1 > 0 && r2 > 0 && r1 <= kTiny && r2 <= kTiny) {
+        // [[U_a^{-1}, -U_a^{-1} Y' U_b^{-1}], [0, U_b^{-1}]] in one launch
+        const uint32_t* Yp = x.A + rb * x.lda + c + r1;
+        if ((st = tiny((int)r1, (int)r2, (int)r2, Yp, x.lda, Ub, ldu, (int)r1, Uo, ldu, x.p - 1, Uo + r1, ldu,
+                       Uo + r1 * ldu, ldu, (int)r2, (int)r1)) != FFGPU_OK)
+            return st;
+    } else if (Uo && r1 > 0 && r2 > 0) {
         // [[U_a^{-1}, -U_a^{-1} Y' U_b^{-1}], [0, U_b^{-1}]]
         if (cudaMemset2DAsync(Uo + r1 * ldu, ldu * 4, 0, r1 * 4, r2, x.s) != cudaSuccess) return FFGPU_ERR_CUDA;
         const uint32_t* Yp = x.A + rb * x.lda + c + r1;
